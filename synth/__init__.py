@@ -177,8 +177,9 @@ def make_elts(seed: int, n_elts: int, nnz: int, catalogue: int, mu: float, sigma
 
 
 def percentile_terms(losses: List[np.ndarray], lo: float = 20.0, hi: float = 95.0):
-    """Per-ELT retention/limit at the lo-th/hi-th percentile of that ELT's losses
-    (NumPy's default linear interpolation)."""
+    """Per-ELT retention R = P_lo and limit L = P_hi, the lo-th and hi-th percentiles of that
+    ELT's losses (NumPy's default linear interpolation); L is the limit amount, so the cover
+    pays min(max(x - P_lo, 0), P_hi)."""
     r = np.array([np.percentile(x, lo) if x.size else 0.0 for x in losses], dtype=np.float64)
     l = np.array([np.percentile(x, hi) if x.size else 0.0 for x in losses], dtype=np.float64)
     return r, l
