@@ -1,0 +1,381 @@
+"""Benchmark of the Aggregate Risk Analysis hot path on GB300.
+
+One step = one pass of the whole path over the paper-scale workload: the per-layer fold of
+per-ELT and occurrence terms, the YET stream (trial sums, aggregate terms, YLT write) and
+PML(100), PML(250), TVaR(0.99) of the YLT, with the metrics read back to the host.
+
+Workload (paper scale): 1 layer of 15 ELTs x 20,000 events over a 2,000,000-event catalogue
+(FP32 lognormal(11, 2) losses), YET of 1,000,000 trials x 1,000 events (4 GB of event IDs,
+larger than L2, so no cache flush is needed between steps).  Synthetic, seeded.
+
+Metric: event-ELT lookups per second, counted as logical (occurrence, ELT) pairs,
+sum_t n_t x |ELTs of the layer| per step.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank runs its own replica on its own GPU (trials are independent; no
+data-path collective), and value is the aggregate over ranks (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_TRIALS = 1_000_000
+EVENTS_PER_TRIAL = 1000
+N_ELTS = 15
+CATALOGUE = 2_000_000
+RPS = [100.0, 250.0]
+LEVELS = [0.99]
+WORKLOAD = "paper_scale: 1 layer x 15 ELTs (20k events each, 2M catalogue, FP32 losses), 1e6 trials x 1000 events"
+METRIC = "event-ELT lookups/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--flags", type=int, default=0, help="ARA_RUN_* flags (measurement variants)")
+    ap.add_argument("--trials", type=int, default=N_TRIALS)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample time")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# Distributed plumbing (one process per GPU under torchrun)
+# ------------------------------------------------------------------------------------------
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+# Clocks during the timed region
+# ------------------------------------------------------------------------------------------
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(REASONS, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# Inputs
+# ------------------------------------------------------------------------------------------
+def make_inputs(seed: int, n_trials: int, pinned: bool):
+    import torch
+    import synth
+    pf = synth.paper_scale_portfolio(0)
+    ids = torch.empty(n_trials * EVENTS_PER_TRIAL, dtype=torch.int32, pin_memory=pinned)
+    yet = synth.paper_scale_yet(seed, n_trials=n_trials, ids_out=ids.numpy())
+    off = torch.from_numpy(yet.offsets)
+    if pinned:
+        off = off.pin_memory()
+    return pf, yet, ids, off
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic_per_launch():
+    """DRAM bytes per launch of the YET-stream kernel from the committed ncu summary, scaled
+    to the benchmark's launch (null when absent or stale)."""
+    path = os.path.join(ROOT, "profiles", "ylt_stream_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        if t.get("kernel_source_sha") != kernel_source_sha():
+            return None
+        return float(t["dram_bytes_per_event"])
+    except Exception:
+        return None
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1606_04473_gb300", "csrc", "ara_ylt.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ------------------------------------------------------------------------------------------
+def oracle_sample_rate(pf, yet_fn, target_s: float):
+    """Time the oracle (all host cores) on the first K trials, K sized for ~target_s."""
+    import oracle
+    import synth
+    calib = 2000
+    y = yet_fn(calib)
+    oracle.ylt(pf, y)  # warm (builds the direct-access tables once per call; part of the work)
+    t0 = time.perf_counter()
+    oracle.ylt(pf, y)
+    dt = time.perf_counter() - t0
+    k = int(max(calib, min(200_000, calib * target_s / max(dt, 1e-3))))
+    y = yet_fn(k)
+    t0 = time.perf_counter()
+    oracle.ylt(pf, y)
+    dt = time.perf_counter() - t0
+    lookups = k * EVENTS_PER_TRIAL * N_ELTS
+    return {"value": lookups / dt, "unit": "lookups/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"first {k} trials of the paper-scale YET ({k * EVENTS_PER_TRIAL} occurrences x "
+                      f"{N_ELTS} ELTs), FP64 C oracle, {dt:.1f} s", "trials": k}
+
+
+def run_reference(args, rank, ws):
+    """Reference arm: the FP64 CPU oracle, timed on the host cores, each step a bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    pf = synth.paper_scale_portfolio(0)
+    base = oracle_sample_rate(pf, lambda k: synth.paper_scale_yet(0, n_trials=k), 2.0)
+    k = base["trials"]
+    yet = synth.paper_scale_yet(0, n_trials=k)
+    for _ in range(args.warmup):
+        oracle.ylt(pf, yet)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y = oracle.ylt(pf, yet)
+        oracle.risk_metrics(y, RPS, LEVELS)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = k * EVENTS_PER_TRIAL * N_ELTS / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "lookups/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_trials": k},
+            "cpu_baseline": {"value": value, "unit": "lookups/s", "cores": oracle.threads(),
+                             "kind": "oracle",
+                             "sample": f"first {k} trials of the paper-scale YET per step"},
+            "e2e": {"value": value, "unit": "lookups/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# Our arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args, rank, ws, local):
+    import torch
+    import paper_1606_04473_gb300 as ara
+    import synth
+
+    n_trials = args.trials
+    pf, yet, ids_h, off_h = make_inputs(seed=rank, n_trials=n_trials, pinned=True)
+    g = ara.Portfolio.from_tables(pf)
+    off = off_h.cuda()
+    ids = ids_h.cuda()
+    ylt = torch.empty((1, n_trials), dtype=torch.float64, device="cuda")
+    n_events = n_trials * EVENTS_PER_TRIAL
+    lookups_per_step = n_events * N_ELTS
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g.run_ylt(off, ids, out=ylt, flags=args.flags)
+        return ara.risk_metrics(ylt, RPS, LEVELS)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    g.check()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs) ----
+    ara.timing_reset()
+    ara.timing_enable(True)
+    n0 = ara.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            pml, tvar = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = (ara.launch_count() - n0)
+    ara.timing_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    ylt_ms, ylt_n = ara.timing_read(ara.ARA_K_YLT)
+    fold_ms, fold_n = ara.timing_read(ara.ARA_K_FOLD)
+    sel_ms, sel_n = ara.timing_read(ara.ARA_K_SELECT)
+    g.check()
+    ms_max = max_over_ranks(ms, ws)
+    value = lookups_per_step * ws / (ms_max / 1e3)
+
+    # ---- end to end through the host-memory entry point (H2D + D2H inside the timed region) ----
+    e2e_steps = args.e2e_steps or max(3, min(args.steps, 10))
+    ylt_h = torch.empty((1, n_trials), dtype=torch.float64, pin_memory=True)
+    ids_np, off_np, ylt_np = ids_h.numpy(), off_h.numpy(), ylt_h.numpy()
+    for _ in range(2):
+        g.run_ylt_host(off_np, ids_np, out=ylt_np, return_periods=RPS, tvar_levels=LEVELS, flags=args.flags)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.run_ylt_host(off_np, ids_np, out=ylt_np, return_periods=RPS, tvar_levels=LEVELS, flags=args.flags)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
+    barrier(ws)
+    h2d = ids_h.numel() * 4 + off_h.numel() * 8
+    d2h = n_trials * 8 + 8 * (len(RPS) + len(LEVELS))
+
+    # ---- roofline of the dominant kernel (the YET stream) ----
+    peak, peak_kind = measured_peaks()
+    alg_bytes = 4 * n_events + 8 * (n_trials + 1) + 8 * n_trials + 8 * CATALOGUE
+    per_launch_ms = ylt_ms / max(ylt_n, 1)
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    tpe = ncu_traffic_per_launch()
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": (tpe * n_events if tpe else None),
+            "peak_source": peak_kind, "kernel": "k_ylt_folded",
+            "alg_bytes_per_launch": alg_bytes, "ms_per_launch": round(per_launch_ms, 4),
+            "frac_8byte_events": round((alg_bytes + 4 * n_events) / (per_launch_ms / 1e3) / 1e9 / peak, 4)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample_rate(pf, lambda k: synth.paper_scale_yet(rank, n_trials=k), args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "lookups/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_max,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded SplitMix64 YET, lognormal ELT losses)",
+                "config": {"workload": WORKLOAD, "n_trials": n_trials, "events_per_trial": EVENTS_PER_TRIAL,
+                           "n_elts": N_ELTS, "catalogue": CATALOGUE, "flags": args.flags,
+                           "layout": "folded per-event table + smem hit bitmap",
+                           "accumulation": "exact 128-bit fixed-point trial sums, FP64 terms",
+                           "l2": "inputs larger than L2 (4 GB of event IDs per step), no flush",
+                           "parallelism": f"replicas x{ws}"},
+                "lookups_per_step": lookups_per_step,
+                "kernel_ms": {"fold": round(fold_ms / max(fold_n, 1), 4),
+                              "ylt_stream": round(per_launch_ms, 4),
+                              "select": round(sel_ms / max(sel_n, 1), 4)},
+                "roofline": roof,
+                "cpu_baseline": cpu,
+                "e2e": {"value": lookups_per_step * ws / e2e_s, "unit": "lookups/s",
+                        "ms_per_step": e2e_s * 1e3, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "api": "ara_run_ylt_host (pinned host YET)"},
+                "gpu_launches": launches,
+                "clocks": clk.summary(),
+                "results": {"pml100": float(pml[0, 0]), "pml250": float(pml[0, 1]),
+                            "tvar99": float(tvar[0, 0])}}
+        print(json.dumps(line), flush=True)
+    g.close()
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, ws)
+        else:
+            run_ours(args, rank, ws, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

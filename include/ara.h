@@ -1,0 +1,213 @@
+/*
+ * ara.h -- C ABI of the GB300 (sm_103a) Aggregate Risk Analysis library (libara.so).
+ *
+ * Aggregate Risk Analysis (paper Section IV) streams every trial of a pre-simulated Year
+ * Event Table (YET, Eq. 1) through the Event Loss Tables (ELTs, Eq. 2) of a layer (Eq. 3),
+ * applies financial terms and writes one Year Loss Table (YLT) entry per trial; PML and
+ * TVaR are taken from the YLT (Section IV-A).
+ *
+ * Financial terms.  Every term pair (retention R, limit L) is applied as the clamp
+ *     C(x; R, L) = min(max(x - R, 0), L)
+ * (Section IV-B prints this formula with the 0 of max() lost).  Per layer:
+ *     a_j(e) = C(x_j(e); R_j, L_j)          x_j(e): loss of event e in ELT j, 0 if absent
+ *     o(e)   = C(sum_j a_j(e); OccR, OccL)  occurrence terms, one occurrence at a time
+ *     S_t    = sum over the events e of trial t of o(e)
+ *     y_t    = C(S_t; AggR, AggL)           aggregate terms -> YLT entry
+ * (Algorithm 3 and the two paragraphs after it).
+ *
+ * Conventions
+ *   - Every call returns an ara_status (0 = ARA_OK, negative = error) unless noted.
+ *   - "d_" pointers are device memory of the portfolio's device, "h_" pointers host memory.
+ *     The library never frees or retains caller memory beyond the call (asynchronous calls
+ *     read it until the stream reaches them).
+ *   - Streams are cudaStream_t handles passed as void*; NULL is the legacy default stream.
+ *   - Argument errors are detected on the host before anything is launched (ARA_EINVAL).
+ *     Data errors that only the device can see (an event ID outside the catalogue, trial
+ *     offsets that decrease or leave [0, n_events]) are recorded by the kernels, the offending
+ *     trial counts as empty, and the next ara_check() on the portfolio returns ARA_EDATA.
+ *   - The library is thread-compatible: one portfolio must not run on two streams at once
+ *     (its fold workspace is shared); distinct portfolios are independent.
+ */
+#ifndef ARA_H
+#define ARA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ARA_API __attribute__((visibility("default")))
+#else
+#define ARA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ara_status;
+#define ARA_OK        0
+#define ARA_EINVAL   (-1)   /* invalid argument or input table */
+#define ARA_ENOMEM   (-2)   /* device or host allocation failed */
+#define ARA_ECUDA    (-3)   /* a CUDA runtime call failed (no device, launch failure, ...) */
+#define ARA_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
+#define ARA_EBUSY    (-5)   /* resource in use */
+#define ARA_EDATA    (-6)   /* device-side data check failed in an earlier asynchronous run */
+
+typedef struct ara_portfolio ara_portfolio;
+
+/* ---------------------------------------------------------------------------------------
+ * Portfolio: ELTs (Eq. 2) with their terms I = (R_j, L_j), and layers (Eq. 3) with their
+ * terms T = (OccR, OccL, AggR, AggL)  [Section IV-A, Section IV-B].
+ * --------------------------------------------------------------------------------------- */
+
+/* flags of ara_create_portfolio */
+#define ARA_LOSSES_F32   1  /* keep ELT losses in FP32 on the device (each loss must be exactly
+                               representable in FP32, else ARA_EINVAL); default FP64 */
+#define ARA_DENSE_TABLES 2  /* also build catalogue-indexed direct-access tables
+                               [n_elts][catalogue] (Section IV-B), used by ARA_RUN_PER_ELT */
+
+/*
+ * Copy a portfolio to the current CUDA device.  Synchronous.
+ *   catalogue_size           number of events in the global event catalogue; event IDs are
+ *                            0 .. catalogue_size-1  (1 <= catalogue_size <= 2^31 - 1)
+ *   n_elts                   number of ELTs (>= 0)
+ *   elt_record_offsets       host [n_elts + 1], non-decreasing, [0] = 0: ELT j owns records
+ *                            elt_record_offsets[j] .. elt_record_offsets[j+1]-1
+ *   record_event_ids         host [total records]: event IDs, unique within an ELT, any order
+ *   record_losses            host [total records]: finite losses >= 0
+ *   elt_ret, elt_lim         host [n_elts]: per-ELT retention (finite, >= 0) and limit (>= 0,
+ *                            +INFINITY allowed)
+ *   n_layers                 number of layers (>= 0)
+ *   layer_elt_offsets        host [n_layers + 1], non-decreasing, [0] = 0
+ *   layer_elt_ids            host [layer_elt_offsets[n_layers]]: ELTs of each layer, in order
+ *   occ_ret, occ_lim,        host [n_layers]: occurrence and aggregate retentions (finite,
+ *   agg_ret, agg_lim         >= 0) and limits (>= 0, +INFINITY allowed)
+ *   flags                    ARA_LOSSES_F32 | ARA_DENSE_TABLES
+ *   out                      receives the handle (owned by the library until destroyed)
+ * Errors: ARA_EINVAL (any rule above broken; nothing allocated), ARA_ENOMEM, ARA_ECUDA.
+ */
+ARA_API ara_status ara_create_portfolio(int64_t catalogue_size, int32_t n_elts,
+                                const int64_t* elt_record_offsets,
+                                const int32_t* record_event_ids, const double* record_losses,
+                                const double* elt_ret, const double* elt_lim, int32_t n_layers,
+                                const int32_t* layer_elt_offsets, const int32_t* layer_elt_ids,
+                                const double* occ_ret, const double* occ_lim,
+                                const double* agg_ret, const double* agg_lim, int32_t flags,
+                                ara_portfolio** out);
+
+/* Release every device and host resource of the portfolio (synchronises its device). */
+ARA_API void ara_destroy_portfolio(ara_portfolio* pf);
+
+/* ---------------------------------------------------------------------------------------
+ * YLT: Algorithm 1 (for each layer) around Algorithm 3 (for each trial, event, ELT).
+ * --------------------------------------------------------------------------------------- */
+
+/* flags of ara_run_ylt / ara_run_ylt_host */
+#define ARA_RUN_FOLDED    0   /* default: per-ELT and occurrence terms folded once per layer
+                                 into a per-event table (occurrence terms depend on nothing but
+                                 the event, Section IV-B), then one gather per hit occurrence */
+#define ARA_RUN_PER_ELT   1   /* Algorithm 3 literally: every ELT of the layer looked up for
+                                 every occurrence (needs ARA_DENSE_TABLES) */
+#define ARA_RUN_NO_FILTER 2   /* folded, without the shared-memory hit filter (measurement) */
+#define ARA_RUN_F64_SUM   4   /* folded, trial sums in FP64 instead of exact fixed point
+                                 (measurement) */
+
+/*
+ * YLT of n_trials trials for the selected layers.  Asynchronous on `stream`.
+ *   d_trial_offsets  device [n_trials + 1] int64: trial t owns events
+ *                    d_trial_offsets[t] .. d_trial_offsets[t+1]-1 of d_event_ids
+ *                    (0 <= offsets non-decreasing <= n_events, else ARA_EDATA later)
+ *   n_events         number of elements of d_event_ids
+ *   d_event_ids      device [n_events] int32, 4-byte aligned: each trial's event IDs in time
+ *                    order (Eq. 1)
+ *   d_timestamps     device [n_events] float or NULL: accepted for the YET's shape, not read
+ *                    (no term of Section IV-B depends on the time of an occurrence)
+ *   n_layer_sel      number of layers to run; layer_sel host [n_layer_sel] layer indices,
+ *                    or (n_layer_sel = 0, layer_sel = NULL) for all layers in order
+ *   d_ylt            device [n_layer_sel][n_trials] double, row-major: the YLT
+ *   d_regimes        device [n_layer_sel][n_trials] uint8 or NULL: the aggregate clamp's
+ *                    regime per trial (0: S <= AggR or kink, 1: AggR < S < AggR + AggL,
+ *                    2: S > AggR + AggL), recorded for ara_adjoint
+ *   flags            ARA_RUN_* (one of FOLDED / PER_ELT, optionally NO_FILTER, F64_SUM)
+ * Errors: ARA_EINVAL, ARA_ECUDA; data errors via ara_check().
+ */
+ARA_API ara_status ara_run_ylt(ara_portfolio* pf, int64_t n_trials, const int64_t* d_trial_offsets,
+                       int64_t n_events, const int32_t* d_event_ids, const float* d_timestamps,
+                       int32_t n_layer_sel, const int32_t* layer_sel, double* d_ylt,
+                       uint8_t* d_regimes, int32_t flags, void* stream);
+
+/*
+ * The whole analysis from host memory: Algorithm 1 with the transfer of Algorithm 2 and the
+ * kernels of Algorithm 3, then the YLT and (optionally) its PML / TVaR back on the host.
+ * The YET is copied in chunks on an internal copy stream while earlier chunks are processed
+ * on `stream`, so host-to-device traffic overlaps the kernels (pinned host memory gives full
+ * link bandwidth); the YLT stays on the device for the risk metrics and is copied back.
+ * Synchronous: returns when every output is written.
+ *   h_trial_offsets host [n_trials + 1], [0] = 0, non-decreasing (validated: ARA_EINVAL)
+ *   h_event_ids     host [h_trial_offsets[n_trials]]
+ *   h_ylt           host [n_layer_sel][n_trials] or NULL (then only the metrics are returned)
+ *   n_rp, return_periods, n_tvar, tvar_levels, h_pml, h_tvar: as in ara_risk_metrics, or
+ *                   n_rp = n_tvar = 0 for no metrics
+ * Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA, ARA_EDATA (event ID outside the catalogue).
+ */
+ARA_API ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials,
+                                    const int64_t* h_trial_offsets, const int32_t* h_event_ids,
+                                    int32_t n_layer_sel, const int32_t* layer_sel, double* h_ylt,
+                                    int32_t n_rp, const double* return_periods, int32_t n_tvar,
+                                    const double* tvar_levels, double* h_pml, double* h_tvar,
+                                    int32_t flags, void* stream);
+
+/* Synchronise `stream`, then report (and clear) device-side data errors recorded by earlier
+ * asynchronous runs of this portfolio: ARA_OK or ARA_EDATA. */
+ARA_API ara_status ara_check(ara_portfolio* pf, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Risk metrics of Section IV-A (PML, TVaR), read as empirical order statistics of the YLT:
+ *   PML(RP)  = the k-th largest year loss, k = ceil(N / RP)
+ *   TVaR(p)  = mean of the m largest year losses, m = ceil(N (1 - p))
+ * N/RP and N(1-p) within 1e-9 (relative) of an integer are taken as that integer, so that
+ * decimal levels such as p = 0.99 give m = N/100 exactly.
+ * --------------------------------------------------------------------------------------- */
+
+/*
+ * Risk metrics of n_layers YLT rows.  Synchronous (results are host values).
+ *   d_ylt         device [n_layers][n_trials] double
+ *   return_periods host [n_rp], each >= 1 with 1 <= ceil(N/RP) <= N
+ *   tvar_levels   host [n_tvar], each in [0, 1) with ceil(N(1-p)) >= 1
+ *   h_pml         host [n_layers][n_rp];  h_tvar host [n_layers][n_tvar]
+ * n_rp + n_tvar <= 16, n_trials >= 1.  Allocates its scratch with the stream-ordered
+ * allocator (cudaMallocAsync) on `stream`.
+ * Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA.
+ */
+ARA_API ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, int32_t n_layers,
+                            int32_t n_rp, const double* return_periods, int32_t n_tvar,
+                            const double* tvar_levels, double* h_pml, double* h_tvar,
+                            void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Introspection for measurement.
+ * --------------------------------------------------------------------------------------- */
+
+/* Kernels launched by this library in this process so far. */
+ARA_API int64_t ara_launch_count(void);
+
+/* kernel classes for timing */
+#define ARA_K_FOLD    0   /* per-layer fold of per-ELT and occurrence terms */
+#define ARA_K_YLT     1   /* the YET stream: trial sums, aggregate terms, YLT write */
+#define ARA_K_SELECT  2   /* PML / TVaR selection (all of its launches) */
+#define ARA_K_ADJOINT 3   /* adjoint kernels */
+#define ARA_K_COUNT   4
+
+/* When enabled, CUDA events are recorded on the launching stream around every launch of
+ * each kernel class.  ara_timing_read synchronises those events and returns the summed
+ * device time (ms) and the number of launches since the last reset. */
+ARA_API void ara_timing_enable(int32_t on);
+ARA_API void ara_timing_reset(void);
+ARA_API ara_status ara_timing_read(int32_t kernel_class, double* total_ms, int64_t* launches);
+
+/* Static description of a status code. */
+ARA_API const char* ara_status_string(ara_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARA_H */

@@ -1,0 +1,239 @@
+"""Aggregate Risk Analysis on GB300 (sm_103a): Python binding of libara.so.
+
+This module only marshals arguments to the C ABI declared in include/ara.h; every step of
+the computation runs in the library's CUDA kernels.  PyTorch provides device memory and
+streams.  There is no CPU fallback: if libara.so is missing or cannot be loaded, every
+call raises.
+
+Paper mapping (arXiv 1606.04473, Section IV):
+  Portfolio          ELTs (Eq. 2) with terms I, layers (Eq. 3) with terms T
+  Portfolio.run_ylt  Algorithm 1 around Algorithm 3 for a YET already on the device
+  Portfolio.run_ylt_host  the same with the transfer of Algorithm 2 overlapped
+  risk_metrics       PML and TVaR of the YLT (named in Section IV-A)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libara.so")
+
+ARA_OK, ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA, ARA_ETIMEOUT, ARA_EBUSY, ARA_EDATA = 0, -1, -2, -3, -4, -5, -6
+ARA_LOSSES_F32, ARA_DENSE_TABLES = 1, 2
+ARA_RUN_FOLDED, ARA_RUN_PER_ELT, ARA_RUN_NO_FILTER, ARA_RUN_F64_SUM = 0, 1, 2, 4
+ARA_K_FOLD, ARA_K_YLT, ARA_K_SELECT, ARA_K_ADJOINT = 0, 1, 2, 3
+
+_lib = None
+
+
+class AraError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libara.so (raises if it has not been built: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libara.so not found at {LIB_PATH}; build it with "
+                           "paper_1606_04473_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.ara_create_portfolio.argtypes = [i64, i32, P, P, P, P, P, i32, P, P, P, P, P, P, i32,
+                                       ctypes.POINTER(P)]
+    L.ara_destroy_portfolio.argtypes = [P]
+    L.ara_destroy_portfolio.restype = None
+    L.ara_run_ylt.argtypes = [P, i64, P, i64, P, P, i32, P, P, P, i32, P]
+    L.ara_run_ylt_host.argtypes = [P, i64, P, P, i32, P, P, i32, P, i32, P, P, P, i32, P]
+    L.ara_check.argtypes = [P, P]
+    L.ara_risk_metrics.argtypes = [P, i64, i32, i32, P, i32, P, P, P, P]
+    L.ara_launch_count.restype = i64
+    L.ara_timing_enable.argtypes = [i32]
+    L.ara_timing_enable.restype = None
+    L.ara_timing_reset.restype = None
+    L.ara_timing_read.argtypes = [i32, ctypes.POINTER(d), ctypes.POINTER(i64)]
+    L.ara_status_string.argtypes = [i32]
+    L.ara_status_string.restype = ctypes.c_char_p
+    for fn in ["ara_create_portfolio", "ara_run_ylt", "ara_run_ylt_host", "ara_check",
+               "ara_risk_metrics", "ara_timing_read"]:
+        getattr(L, fn).restype = i32
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().ara_status_string(int(s)).decode()
+    except Exception:
+        return "unknown"
+
+
+def _check(st: int, what: str):
+    if st != ARA_OK:
+        raise AraError(st, what)
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream):
+    """cudaStream_t of a torch.cuda.Stream (or the current stream when None)."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Portfolio:
+    """A portfolio resident on the current CUDA device (ara_create_portfolio)."""
+
+    def __init__(self, catalogue: int, elt_ids: Sequence[np.ndarray], elt_losses: Sequence[np.ndarray],
+                 elt_ret, elt_lim, layer_elts: Sequence[Sequence[int]], occ_ret, occ_lim,
+                 agg_ret, agg_lim, losses_f32: bool = False, dense_tables: bool = False):
+        L = lib()
+        n_elts = len(elt_ids)
+        off = np.zeros(n_elts + 1, dtype=np.int64)
+        off[1:] = np.cumsum([len(x) for x in elt_ids])
+        ids = np.ascontiguousarray(np.concatenate(elt_ids) if n_elts else np.zeros(0), dtype=np.int32)
+        loss = np.ascontiguousarray(np.concatenate(elt_losses) if n_elts else np.zeros(0), dtype=np.float64)
+        loff = np.zeros(len(layer_elts) + 1, dtype=np.int32)
+        loff[1:] = np.cumsum([len(l) for l in layer_elts])
+        lel = np.ascontiguousarray([j for l in layer_elts for j in l], dtype=np.int32)
+        f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+        self._keep = [off, ids, loss, loff, lel]
+        er, el, orr, ol, ar, al = (f(elt_ret), f(elt_lim), f(occ_ret), f(occ_lim), f(agg_ret), f(agg_lim))
+        flags = (ARA_LOSSES_F32 if losses_f32 else 0) | (ARA_DENSE_TABLES if dense_tables else 0)
+        h = ctypes.c_void_p()
+        st = L.ara_create_portfolio(int(catalogue), n_elts, _np_ptr(off), _np_ptr(ids), _np_ptr(loss),
+                                    _np_ptr(er), _np_ptr(el), len(layer_elts), _np_ptr(loff),
+                                    _np_ptr(lel), _np_ptr(orr), _np_ptr(ol), _np_ptr(ar), _np_ptr(al),
+                                    flags, ctypes.byref(h))
+        _check(st, "ara_create_portfolio")
+        self._h = h
+        self.catalogue = int(catalogue)
+        self.n_layers = len(layer_elts)
+        self.n_elts = n_elts
+
+    @classmethod
+    def from_tables(cls, pf, dense_tables: bool = False) -> "Portfolio":
+        """From an object with the fields of the paper's tables (catalogue, elt_ids, elt_losses,
+        elt_ret, elt_lim, layer_elts, occ_ret, occ_lim, agg_ret, agg_lim, losses_f32)."""
+        return cls(pf.catalogue, pf.elt_ids, pf.elt_losses, pf.elt_ret, pf.elt_lim, pf.layer_elts,
+                   pf.occ_ret, pf.occ_lim, pf.agg_ret, pf.agg_lim,
+                   losses_f32=bool(getattr(pf, "losses_f32", False)), dense_tables=dense_tables)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ara_destroy_portfolio(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sel(self, layers):
+        if layers is None:
+            return 0, None, self.n_layers, None
+        sel = np.ascontiguousarray(np.asarray(layers, dtype=np.int32).reshape(-1))
+        return sel.size, _np_ptr(sel), sel.size, sel
+
+    def run_ylt(self, offsets, event_ids, layers=None, out=None, regimes=None, flags: int = 0,
+                stream=None, timestamps=None):
+        """YLT [n_layers_selected, n_trials] (float64, on the device) of a device-resident YET.
+        Asynchronous on `stream`; call check() to surface device-side data errors."""
+        import torch
+        n_trials = offsets.numel() - 1
+        n_sel, sel_p, n_out, _sel = self._sel(layers)
+        if out is None:
+            out = torch.empty((n_out, n_trials), dtype=torch.float64, device=offsets.device)
+        st = lib().ara_run_ylt(self._h, n_trials, _dev_ptr(offsets, torch.int64, "offsets"),
+                               event_ids.numel(), _dev_ptr(event_ids, torch.int32, "event_ids"),
+                               None if timestamps is None else _dev_ptr(timestamps, torch.float32, "timestamps"),
+                               n_sel, sel_p, _dev_ptr(out, torch.float64, "out"),
+                               None if regimes is None else _dev_ptr(regimes, torch.uint8, "regimes"),
+                               int(flags), _stream_handle(stream))
+        _check(st, "ara_run_ylt")
+        return out
+
+    def run_ylt_host(self, offsets: np.ndarray, event_ids: np.ndarray, layers=None, out=None,
+                     return_periods: Sequence[float] = (), tvar_levels: Sequence[float] = (),
+                     want_ylt: bool = True, flags: int = 0, stream=None):
+        """The whole analysis from host memory (synchronous): YLT [n_layers_selected, n_trials]
+        on the host, plus (PML, TVaR) when return periods / levels are given.  Pinned host
+        arrays (e.g. from torch pin_memory) transfer at full link bandwidth."""
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        event_ids = np.ascontiguousarray(event_ids, dtype=np.int32)
+        n_trials = offsets.size - 1
+        n_sel, sel_p, n_out, _sel = self._sel(layers)
+        if want_ylt and out is None:
+            out = np.empty((n_out, n_trials), dtype=np.float64)
+        if out is not None:
+            assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == (n_out, n_trials)
+        rp = np.ascontiguousarray(return_periods, dtype=np.float64)
+        lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
+        pml = np.zeros((n_out, rp.size))
+        tvar = np.zeros((n_out, lv.size))
+        st = lib().ara_run_ylt_host(self._h, n_trials, _np_ptr(offsets), _np_ptr(event_ids), n_sel,
+                                    sel_p, _np_ptr(out), rp.size, _np_ptr(rp), lv.size, _np_ptr(lv),
+                                    _np_ptr(pml), _np_ptr(tvar), int(flags), _stream_handle(stream))
+        _check(st, "ara_run_ylt_host")
+        if rp.size or lv.size:
+            return out, pml, tvar
+        return out
+
+    def check(self, stream=None):
+        _check(lib().ara_check(self._h, _stream_handle(stream)), "ara_check")
+
+
+def risk_metrics(ylt, return_periods: Sequence[float] = (), tvar_levels: Sequence[float] = (),
+                 stream=None):
+    """(PML [n_layers, n_rp], TVaR [n_layers, n_tvar]) of a device YLT [n_layers, n_trials]."""
+    import torch
+    ylt2 = ylt if ylt.dim() == 2 else ylt.reshape(1, -1)
+    nl, n = ylt2.shape
+    rp = np.ascontiguousarray(return_periods, dtype=np.float64)
+    lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
+    pml = np.zeros((nl, rp.size))
+    tvar = np.zeros((nl, lv.size))
+    st = lib().ara_risk_metrics(_dev_ptr(ylt2, torch.float64, "ylt"), n, nl, rp.size, _np_ptr(rp),
+                                lv.size, _np_ptr(lv), _np_ptr(pml), _np_ptr(tvar), _stream_handle(stream))
+    _check(st, "ara_risk_metrics")
+    return pml, tvar
+
+
+def launch_count() -> int:
+    return int(lib().ara_launch_count())
+
+
+def timing_enable(on: bool = True):
+    lib().ara_timing_enable(1 if on else 0)
+
+
+def timing_reset():
+    lib().ara_timing_reset()
+
+
+def timing_read(kernel_class: int):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().ara_timing_read(int(kernel_class), ctypes.byref(ms), ctypes.byref(n)), "ara_timing_read")
+    return ms.value, n.value

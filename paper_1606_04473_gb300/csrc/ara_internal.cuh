@@ -1,0 +1,134 @@
+// Internal declarations shared by the translation units of libara.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "../../include/ara.h"
+
+namespace ara {
+
+// ------------------------------------------------------------------------------------------
+// Error plumbing
+// ------------------------------------------------------------------------------------------
+#define ARA_TRY(expr)                                              \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) {                                       \
+      ::ara::note_cuda_error(_e, #expr, __FILE__, __LINE__);       \
+      return _e == cudaErrorMemoryAllocation ? ARA_ENOMEM : ARA_ECUDA; \
+    }                                                              \
+  } while (0)
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Device-side data error bits (atomicOr into the portfolio's error word).
+enum : uint32_t { DERR_EVENT_RANGE = 1u, DERR_OFFSETS = 2u };
+
+// ------------------------------------------------------------------------------------------
+// Launch accounting and per-class event timing
+// ------------------------------------------------------------------------------------------
+extern std::atomic<int64_t> g_launches;
+void timing_begin(int kclass, cudaStream_t s);
+void timing_end(int kclass, cudaStream_t s);
+
+// RAII helper: events around every launch of a kernel class (when timing is enabled) and
+// one count per launch.
+struct LaunchScope {
+  int kclass;
+  cudaStream_t s;
+  LaunchScope(int k, cudaStream_t st, int n_launches = 1) : kclass(k), s(st) {
+    g_launches.fetch_add(n_launches);
+    timing_begin(k, s);
+  }
+  ~LaunchScope() { timing_end(kclass, s); }
+};
+
+// ------------------------------------------------------------------------------------------
+// Per-layer constants of the folded path
+// ------------------------------------------------------------------------------------------
+// Occurrence losses o(e) are kept as unsigned fixed point q(e) = round(o(e) * 2^frac_bits),
+// q(e) <= 2^61, and trial sums are exact 128-bit integer sums of q.  The aggregate terms are
+// applied to the exact sum in the same fixed point; only the final year loss is converted to
+// double.
+struct LayerConst {
+  double occ_ret, occ_lim, agg_ret, agg_lim;   // layer terms T (FP64)
+  double scale;                                // 2^frac_bits
+  double inv_scale;                            // 2^-frac_bits
+  uint64_t agg_ret_lo, agg_ret_hi;             // round(AggR * scale) as u128 (saturated)
+  uint64_t agg_lim_lo, agg_lim_hi;             // round(AggL * scale) as u128 (saturated)
+  int32_t elt_begin, elt_end;                  // slice of layer_elt_ids
+  int32_t frac_bits;
+  int32_t pad;
+};
+
+struct Portfolio {
+  int device = 0;
+  int n_sms = 0;
+  int64_t catalogue = 0;
+  int32_t n_elts = 0, n_layers = 0, flags = 0;
+  int64_t n_records = 0;
+  // host copies
+  std::vector<int64_t> rec_off;
+  std::vector<double> elt_ret, elt_lim, elt_max_loss;
+  std::vector<int32_t> layer_off, layer_elts;
+  std::vector<LayerConst> layers;
+  // device tables
+  int64_t* d_rec_off = nullptr;     // [n_elts + 1]
+  int32_t* d_rec_ids = nullptr;     // [n_records], sorted by event ID within each ELT
+  double* d_rec_loss = nullptr;     // [n_records] (FP64 storage) or nullptr
+  float* d_rec_loss32 = nullptr;    // [n_records] (FP32 storage) or nullptr
+  double* d_elt_ret = nullptr;      // [n_elts]
+  double* d_elt_lim = nullptr;      // [n_elts]
+  int32_t* d_layer_elts = nullptr;  // [layer_off[n_layers]]
+  LayerConst* d_layers = nullptr;   // [n_layers]
+  void* d_dense = nullptr;          // [n_elts][catalogue] float or double (ARA_DENSE_TABLES)
+  // per-layer fold workspace
+  uint64_t* d_q = nullptr;          // [n_layers][catalogue]: q(e) (or o(e) bits for F64_SUM)
+  uint32_t* d_bits = nullptr;       // [n_layers][bm_words]: bit e set iff q(e) != 0
+  int64_t bm_words = 0;             // words per layer (padded to a multiple of 4)
+  uint32_t* d_err = nullptr;        // device error word
+  // host-input pipeline resources (grown on demand)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+  int32_t* d_stage_ids[2] = {nullptr, nullptr};
+  int64_t* d_stage_off[2] = {nullptr, nullptr};
+  int64_t stage_events = 0, stage_trials = 0;
+  double* d_ylt_full = nullptr;     // [n_sel][n_trials] YLT of the host pipeline
+  int64_t ylt_full_elems = 0;
+};
+
+// ------------------------------------------------------------------------------------------
+// Kernel entry points (host-side launchers), implemented in ara_ylt.cu / ara_select.cu
+// ------------------------------------------------------------------------------------------
+struct YltArgs {
+  int64_t n_trials;
+  const int64_t* offsets;   // [n_trials + 1]
+  int64_t id_base;          // subtracted from every offset (host pipeline chunks)
+  int64_t n_events;         // valid range of (offset - id_base)
+  const int32_t* ids;
+  int32_t n_sel;
+  const int32_t* sel;       // host [n_sel] layer indices
+  double* ylt;              // row i (layer sel[i]) at ylt + i * row_stride
+  uint8_t* regimes;         // row i at regimes + i * row_stride, or nullptr
+  int64_t row_stride;       // elements between the rows of consecutive selected layers
+  int32_t flags;
+};
+
+ara_status launch_fold(Portfolio& pf, int32_t n_sel, const int32_t* sel_host, int32_t flags,
+                       cudaStream_t s);
+ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s);
+ara_status build_dense(Portfolio& pf, cudaStream_t s);
+// Host check of risk-metric arguments (ranks within [1, n]); ARA_OK or ARA_EINVAL.
+ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t n_tvar,
+                            const double* levels);
+// PML / TVaR of n_layers device YLT rows into host arrays (synchronises s); scratch from the
+// stream-ordered allocator.
+ara_status risk_metrics_device(const double* d_ylt, int64_t n, int32_t n_layers, int32_t n_rp,
+                               const double* rps, int32_t n_tvar, const double* levels,
+                               double* h_pml, double* h_tvar, cudaStream_t s);
+
+}  // namespace ara

@@ -1,0 +1,323 @@
+// PML and TVaR (Section IV-A names both as metrics derived from the YLT) as empirical order
+// statistics: PML(RP) is the ceil(N/RP)-th largest year loss, TVaR(p) the mean of the
+// ceil(N(1-p)) largest.  Both come from an exact radix select on order-preserving 64-bit keys
+// of the FP64 year losses (8 passes of 8 bits), followed by one pass summing the tail above
+// the selected key.  Every block of a pass adds its shared-memory histogram into the pass's
+// global histogram; the last block to finish (ticket counter, no waiting) advances the
+// selection state.  Results are bit-exact copies of YLT entries (PML) and a deterministic
+// FP64 sum (TVaR).
+
+#include <cmath>
+#include <vector>
+
+#include "ara_internal.cuh"
+
+namespace ara {
+
+constexpr int SEL_BITS = 8;
+constexpr int SEL_BINS = 1 << SEL_BITS;
+constexpr int SEL_PASSES = 64 / SEL_BITS;
+constexpr int SEL_MAX_T = 16;
+constexpr int SEL_THREADS = 256;
+
+struct SelTargets {
+  int32_t n_t;                 // targets per layer
+  int32_t n_rp;                // targets [0, n_rp) are PML ranks, the rest TVaR counts
+  int64_t rank[SEL_MAX_T];     // 1-based rank from the top
+};
+
+struct SelState {
+  uint64_t prefix;             // key bits fixed so far
+  int64_t k;                   // rank still to find among keys matching the prefix
+};
+
+// Scratch layout (one allocation, zero-filled before the first pass):
+//   hist   [SEL_PASSES][n_layers][n_t][SEL_BINS]  uint32
+//   ticket [SEL_PASSES + 1][n_layers]             uint32
+//   state  [n_layers][n_t]                        SelState
+//   psum   [n_layers][n_t][blocks]                double
+//   pcnt   [n_layers][n_t][blocks]                int64
+//   out    [n_layers][n_t]                        double
+struct SelScratch {
+  uint32_t* hist;
+  uint32_t* ticket;
+  SelState* state;
+  double* psum;
+  int64_t* pcnt;
+  double* out;
+};
+
+size_t select_scratch_bytes(int32_t n_layers, int32_t n_t, int32_t blocks) {
+  size_t b = 0;
+  auto take = [&](size_t n) { b = (b + 255) / 256 * 256 + n; };
+  take(sizeof(uint32_t) * SEL_PASSES * n_layers * n_t * SEL_BINS);
+  take(sizeof(uint32_t) * (SEL_PASSES + 1) * n_layers);
+  take(sizeof(SelState) * n_layers * n_t);
+  take(sizeof(double) * n_layers * n_t * blocks);
+  take(sizeof(int64_t) * n_layers * n_t * blocks);
+  take(sizeof(double) * n_layers * n_t);
+  return (b + 255) / 256 * 256;
+}
+
+static SelScratch carve(void* base, int32_t n_layers, int32_t n_t, int32_t blocks) {
+  size_t b = 0;
+  char* p = (char*)base;
+  auto take = [&](size_t n) {
+    b = (b + 255) / 256 * 256;
+    void* r = p + b;
+    b += n;
+    return r;
+  };
+  SelScratch s;
+  s.hist = (uint32_t*)take(sizeof(uint32_t) * SEL_PASSES * n_layers * n_t * SEL_BINS);
+  s.ticket = (uint32_t*)take(sizeof(uint32_t) * (SEL_PASSES + 1) * n_layers);
+  s.state = (SelState*)take(sizeof(SelState) * n_layers * n_t);
+  s.psum = (double*)take(sizeof(double) * n_layers * n_t * blocks);
+  s.pcnt = (int64_t*)take(sizeof(int64_t) * n_layers * n_t * blocks);
+  s.out = (double*)take(sizeof(double) * n_layers * n_t);
+  return s;
+}
+
+// Order-preserving map of an IEEE double to an unsigned 64-bit key (total order).
+__device__ __forceinline__ uint64_t key_of(double y) {
+  const uint64_t b = (uint64_t)__double_as_longlong(y);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double value_of(uint64_t k) {
+  const uint64_t b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+__global__ void __launch_bounds__(SEL_THREADS)
+k_select_pass(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScratch sc, int pass) {
+  __shared__ uint32_t h[SEL_MAX_T * SEL_BINS];
+  __shared__ uint64_t pre[SEL_MAX_T];
+  __shared__ bool last;
+  const int layer = blockIdx.y, nt = tg.n_t;
+  for (int i = threadIdx.x; i < nt * SEL_BINS; i += blockDim.x) h[i] = 0;
+  if (threadIdx.x < nt) pre[threadIdx.x] = pass == 0 ? 0ull : sc.state[layer * nt + threadIdx.x].prefix;
+  __syncthreads();
+  const int shift = 64 - SEL_BITS * (pass + 1);
+  const double* row = ylt + (int64_t)layer * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = key_of(row[i]);
+    const uint32_t d = (uint32_t)(key >> shift) & (SEL_BINS - 1);
+    for (int t = 0; t < nt; ++t)
+      if (pass == 0 || (key >> (shift + SEL_BITS)) == (pre[t] >> (shift + SEL_BITS)))
+        atomicAdd(&h[t * SEL_BINS + d], 1u);
+  }
+  __syncthreads();
+  uint32_t* gh = sc.hist + ((int64_t)pass * gridDim.y + layer) * nt * SEL_BINS;
+  for (int i = threadIdx.x; i < nt * SEL_BINS; i += blockDim.x)
+    if (h[i]) atomicAdd(&gh[i], h[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    last = atomicAdd(&sc.ticket[pass * gridDim.y + layer], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // Last block: pick the digit of every target, scanning bins from the top (one warp each).
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = warp; t < nt; t += blockDim.x / 32) {
+    SelState st = pass == 0 ? SelState{0ull, tg.rank[t]} : sc.state[layer * nt + t];
+    // lane l owns bins [SEL_BINS - 8(l+1), SEL_BINS - 8l) (descending order overall)
+    uint32_t c[SEL_BINS / 32];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int u = 0; u < SEL_BINS / 32; ++u) {
+      c[u] = __ldcg(&gh[t * SEL_BINS + (SEL_BINS - 1 - (lane * (SEL_BINS / 32) + u))]);
+      mine += c[u];
+    }
+    uint32_t incl = mine;  // inclusive prefix over lanes (from the top bins down)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const uint32_t excl = incl - mine;
+    const bool here = (int64_t)excl < st.k && st.k <= (int64_t)incl;
+    if (here) {
+      int64_t before = excl;
+      int u = 0;
+      for (; u < SEL_BINS / 32; ++u) {
+        if (before + c[u] >= st.k) break;
+        before += c[u];
+      }
+      const uint32_t bin = SEL_BINS - 1 - (lane * (SEL_BINS / 32) + u);
+      st.k -= before;
+      st.prefix |= (uint64_t)bin << shift;
+      sc.state[layer * nt + t] = st;
+    }
+  }
+}
+
+// Tail pass: for every target, the selected key; for TVaR targets the sum and count of the
+// values strictly above it.  The last block combines block partials in block order.
+__global__ void __launch_bounds__(SEL_THREADS)
+k_select_tail(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScratch sc) {
+  __shared__ double ssum[SEL_THREADS / 32][SEL_MAX_T];
+  __shared__ int64_t scnt[SEL_THREADS / 32][SEL_MAX_T];
+  __shared__ uint64_t thr[SEL_MAX_T];
+  __shared__ bool last;
+  const int layer = blockIdx.y, nt = tg.n_t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x < nt) thr[threadIdx.x] = sc.state[layer * nt + threadIdx.x].prefix;
+  __syncthreads();
+  const double* row = ylt + (int64_t)layer * n;
+  for (int t = tg.n_rp; t < nt; ++t) {
+    double s = 0.0;
+    int64_t c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const double y = row[i];
+      if (key_of(y) > thr[t]) { s = __dadd_rn(s, y); ++c; }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
+      c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) { ssum[warp][t] = s; scnt[warp][t] = c; }
+  }
+  __syncthreads();
+  if (threadIdx.x < nt && threadIdx.x >= tg.n_rp) {
+    double s = 0.0;
+    int64_t c = 0;
+    for (int w = 0; w < SEL_THREADS / 32; ++w) { s = __dadd_rn(s, ssum[w][threadIdx.x]); c += scnt[w][threadIdx.x]; }
+    const int64_t slot = ((int64_t)layer * nt + threadIdx.x) * gridDim.x + blockIdx.x;
+    sc.psum[slot] = s;
+    sc.pcnt[slot] = c;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    last = atomicAdd(&sc.ticket[SEL_PASSES * gridDim.y + layer], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < nt) {
+    const int t = threadIdx.x;
+    const double v = value_of(thr[t]);
+    double r = v;
+    if (t >= tg.n_rp) {
+      double s = 0.0;
+      int64_t c = 0;
+      const int64_t base = ((int64_t)layer * nt + t) * gridDim.x;
+      for (unsigned b = 0; b < gridDim.x; ++b) { s = __dadd_rn(s, __ldcg(&sc.psum[base + b])); c += __ldcg(&sc.pcnt[base + b]); }
+      const int64_t m = tg.rank[t];
+      r = (s + (double)(m - c) * v) / (double)m;
+    }
+    sc.out[layer * nt + t] = r;
+  }
+}
+
+// ceil(x), taking x within 1e-9 (relative) of an integer as that integer.
+static int64_t ceil_snap(double x) {
+  const double r = std::nearbyint(x);
+  if (std::fabs(x - r) <= 1e-9 * std::fmax(1.0, std::fabs(x))) return (int64_t)r;
+  return (int64_t)std::ceil(x);
+}
+
+ara_status select_targets(int64_t n, int32_t n_rp, const double* rps, int32_t n_tvar,
+                          const double* levels, SelTargets& tg) {
+  if (n < 1 || n_rp < 0 || n_tvar < 0 || n_rp + n_tvar < 1 || n_rp + n_tvar > SEL_MAX_T)
+    return ARA_EINVAL;
+  if ((n_rp > 0 && !rps) || (n_tvar > 0 && !levels)) return ARA_EINVAL;
+  tg.n_t = n_rp + n_tvar;
+  tg.n_rp = n_rp;
+  for (int i = 0; i < n_rp; ++i) {
+    if (!(rps[i] >= 1.0) || !std::isfinite(rps[i])) return ARA_EINVAL;
+    const int64_t k = ceil_snap((double)n / rps[i]);
+    if (k < 1 || k > n) return ARA_EINVAL;
+    tg.rank[i] = k;
+  }
+  for (int i = 0; i < n_tvar; ++i) {
+    if (!(levels[i] >= 0.0 && levels[i] < 1.0)) return ARA_EINVAL;
+    const int64_t m = ceil_snap((double)n * (1.0 - levels[i]));
+    if (m < 1 || m > n) return ARA_EINVAL;
+    tg.rank[n_rp + i] = m;
+  }
+  return ARA_OK;
+}
+
+ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t n_tvar,
+                            const double* levels) {
+  SelTargets tg;
+  return select_targets(n, n_rp, rps, n_tvar, levels, tg);
+}
+
+int32_t select_blocks(int64_t n, int n_sms, int32_t n_layers) {
+  int64_t b = (n + SEL_THREADS * 8 - 1) / (SEL_THREADS * 8);
+  const int64_t cap = std::max<int64_t>(1, 2 * (int64_t)n_sms / std::max(1, n_layers) + 1);
+  return (int32_t)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// Launch the whole selection into `scratch` (zero-filled here); results land in scratch.out.
+ara_status launch_select(const double* d_ylt, int64_t n, int32_t n_layers, const SelTargets& tg,
+                         void* scratch, size_t scratch_bytes, int32_t blocks, cudaStream_t s,
+                         double** d_out) {
+  SelScratch sc = carve(scratch, n_layers, tg.n_t, blocks);
+  ARA_TRY(cudaMemsetAsync(scratch, 0, scratch_bytes, s));
+  {
+    LaunchScope ls(ARA_K_SELECT, s, SEL_PASSES + 1);
+    dim3 grid(blocks, n_layers);
+    for (int p = 0; p < SEL_PASSES; ++p) k_select_pass<<<grid, SEL_THREADS, 0, s>>>(d_ylt, n, tg, sc, p);
+    k_select_tail<<<grid, SEL_THREADS, 0, s>>>(d_ylt, n, tg, sc);
+    ARA_TRY(cudaGetLastError());
+  }
+  *d_out = sc.out;
+  return ARA_OK;
+}
+
+}  // namespace ara
+
+using namespace ara;
+
+namespace ara {
+
+ara_status risk_metrics_device(const double* d_ylt, int64_t n_trials, int32_t n_layers,
+                               int32_t n_rp, const double* rps, int32_t n_tvar,
+                               const double* levels, double* h_pml, double* h_tvar,
+                               cudaStream_t s) {
+  SelTargets tg;
+  if (!d_ylt || n_layers < 1) return ARA_EINVAL;
+  if ((n_rp > 0 && !h_pml) || (n_tvar > 0 && !h_tvar)) return ARA_EINVAL;
+  if ((uintptr_t)d_ylt & 7) return ARA_EINVAL;
+  ara_status st = select_targets(n_trials, n_rp, rps, n_tvar, levels, tg);
+  if (st != ARA_OK) return st;
+  int dev = 0, sms = 0;
+  ARA_TRY(cudaGetDevice(&dev));
+  ARA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int32_t blocks = select_blocks(n_trials, sms, n_layers);
+  const size_t bytes = select_scratch_bytes(n_layers, tg.n_t, blocks);
+  void* scratch = nullptr;
+  ARA_TRY(cudaMallocAsync(&scratch, bytes, s));
+  double* d_out = nullptr;
+  st = launch_select(d_ylt, n_trials, n_layers, tg, scratch, bytes, blocks, s, &d_out);
+  std::vector<double> out((size_t)n_layers * tg.n_t);
+  if (st == ARA_OK) {
+    cudaError_t e = cudaMemcpyAsync(out.data(), d_out, sizeof(double) * out.size(),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = ARA_ECUDA;
+  }
+  cudaFreeAsync(scratch, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && st == ARA_OK) st = ARA_ECUDA;
+  if (st != ARA_OK) return st;
+  for (int32_t l = 0; l < n_layers; ++l) {
+    for (int i = 0; i < n_rp; ++i) h_pml[(size_t)l * n_rp + i] = out[(size_t)l * tg.n_t + i];
+    for (int i = 0; i < n_tvar; ++i) h_tvar[(size_t)l * n_tvar + i] = out[(size_t)l * tg.n_t + n_rp + i];
+  }
+  return ARA_OK;
+}
+
+}  // namespace ara
+
+extern "C" ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, int32_t n_layers,
+                                       int32_t n_rp, const double* rps, int32_t n_tvar,
+                                       const double* levels, double* h_pml, double* h_tvar,
+                                       void* stream) {
+  return risk_metrics_device(d_ylt, n_trials, n_layers, n_rp, rps, n_tvar, levels, h_pml, h_tvar,
+                             (cudaStream_t)stream);
+}

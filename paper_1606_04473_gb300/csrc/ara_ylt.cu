@@ -1,0 +1,523 @@
+// YLT kernels: the per-layer fold of per-ELT and occurrence terms, and the YET stream.
+//
+// Section IV-B (Algorithm 3): for every trial, for every event, for every ELT of the layer,
+// look the event up, apply the ELT terms, combine across the ELTs, apply the occurrence terms,
+// add to the trial's aggregate loss; then apply the aggregate terms.  Occurrence terms act on
+// each occurrence independently of the trial, so the occurrence loss o(e) is a function of
+// the event alone.  The folded path computes o(e) once per catalogue event and layer
+// (k_fold), then streams the YET with one table gather per occurrence whose o(e) is non-zero
+// (k_ylt_folded).  k_ylt_per_elt keeps the literal per-occurrence, per-ELT lookups.
+
+#include <cstdio>
+
+#include "ara_internal.cuh"
+
+namespace ara {
+
+constexpr int FOLD_TILE = 2048;
+constexpr int FOLD_THREADS = 256;
+constexpr int YLT_THREADS = 1024;
+constexpr int MAX_SEL = 256;
+constexpr unsigned FULL = 0xffffffffu;
+
+struct SelList {
+  int32_t n;
+  int32_t idx[MAX_SEL];
+};
+
+// Retention/limit clamp C(x; R, L) = min(max(x - R, 0), L), evaluated in the same order of
+// IEEE operations as the FP64 reference so that results agree bit for bit.
+__device__ __forceinline__ double clamp_terms(double x, double R, double L) {
+  double ex = __dsub_rn(x, R);
+  if (ex < 0.0) ex = 0.0;
+  if (ex > L) ex = L;
+  return ex;
+}
+
+__device__ __forceinline__ int64_t lower_bound_ids(const int32_t* __restrict__ ids, int64_t lo,
+                                                   int64_t hi, int64_t v) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)ids[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------------------------------
+// Fold: o(e) = C(sum_j C(x_j(e); R_j, L_j); OccR, OccL) for every catalogue event e of one
+// tile, for the layer sel.idx[blockIdx.y].  The ELT sum runs in the layer's ELT order (one
+// pass per ELT, separated by barriers), the order of the FP64 reference.  Output: the fixed
+// point q(e) = round(o(e) * 2^frac_bits) (or the FP64 bits of o(e) when f64_table), and the
+// hit bitmap (bit e set iff the stored value is non-zero).
+// ------------------------------------------------------------------------------------------
+template <typename LossT>
+__global__ void __launch_bounds__(FOLD_THREADS)
+k_fold(int64_t catalogue, const int64_t* __restrict__ rec_off, const int32_t* __restrict__ rec_ids,
+       const LossT* __restrict__ rec_loss, const double* __restrict__ elt_ret,
+       const double* __restrict__ elt_lim, const int32_t* __restrict__ layer_elts,
+       const LayerConst* __restrict__ layers, SelList sel, uint64_t* __restrict__ q_out,
+       uint32_t* __restrict__ bits_out, int64_t bm_words, int f64_table) {
+  __shared__ double s[FOLD_TILE];
+  __shared__ int32_t list[FOLD_TILE];
+  __shared__ int32_t n_list;
+  __shared__ int64_t rng[2];
+  const int layer = sel.idx[blockIdx.y];
+  const LayerConst lc = layers[layer];
+  const int64_t t0 = (int64_t)blockIdx.x * FOLD_TILE;
+  const int64_t t1 = min(t0 + (int64_t)FOLD_TILE, catalogue);
+  for (int i = threadIdx.x; i < FOLD_TILE; i += blockDim.x) s[i] = 0.0;
+  if (threadIdx.x == 0) n_list = 0;
+  for (int k = lc.elt_begin; k < lc.elt_end; ++k) {
+    const int j = layer_elts[k];
+    if (threadIdx.x == 0) {
+      int64_t a = lower_bound_ids(rec_ids, rec_off[j], rec_off[j + 1], t0);
+      rng[0] = a;
+      rng[1] = lower_bound_ids(rec_ids, a, rec_off[j + 1], t1);
+    }
+    __syncthreads();
+    const double R = elt_ret[j], L = elt_lim[j];
+    for (int64_t r = rng[0] + threadIdx.x; r < rng[1]; r += blockDim.x) {
+      const int e = (int)(rec_ids[r] - t0);
+      s[e] = __dadd_rn(s[e], clamp_terms((double)rec_loss[r], R, L));  // IDs unique per ELT
+    }
+    __syncthreads();
+  }
+  // Compact the touched events so the FP64 occurrence clamp runs on full warps only.
+  for (int i = threadIdx.x; i < (int)(t1 - t0); i += blockDim.x)
+    if (s[i] != 0.0) list[atomicAdd(&n_list, 1)] = i;
+  __syncthreads();
+  uint64_t* sq = reinterpret_cast<uint64_t*>(s);  // in place: untouched entries are +0.0 == 0
+  for (int p = threadIdx.x; p < n_list; p += blockDim.x) {
+    const int i = list[p];
+    const double o = clamp_terms(s[i], lc.occ_ret, lc.occ_lim);
+    sq[i] = f64_table ? (uint64_t)__double_as_longlong(o) : __double2ull_rn(__dmul_rn(o, lc.scale));
+  }
+  __syncthreads();
+  uint64_t* qo = q_out + (int64_t)layer * catalogue;
+  uint32_t* bo = bits_out + (int64_t)layer * bm_words;
+  for (int i = threadIdx.x; i < FOLD_TILE; i += blockDim.x) {  // FOLD_TILE % blockDim == 0
+    const int64_t e = t0 + i;
+    const uint64_t q = e < t1 ? sq[i] : 0ull;
+    if (e < t1) qo[e] = q;
+    const unsigned b = __ballot_sync(FULL, q != 0ull);
+    if ((threadIdx.x & 31) == 0) {
+      const int64_t w = (t0 + (i & ~31)) >> 5;
+      if (w < bm_words) bo[w] = b;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Stream helpers
+// ------------------------------------------------------------------------------------------
+struct U128 {
+  uint64_t lo, hi;
+};
+
+__device__ __forceinline__ void add_u64(U128& a, uint64_t v) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(a.lo), "+l"(a.hi) : "l"(v));
+}
+__device__ __forceinline__ void add_u128(U128& a, uint64_t lo, uint64_t hi) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(lo), "l"(hi));
+}
+__device__ __forceinline__ bool le_u128(uint64_t alo, uint64_t ahi, uint64_t blo, uint64_t bhi) {
+  return ahi < bhi || (ahi == bhi && alo <= blo);
+}
+
+template <typename Acc> struct AccOps;
+template <> struct AccOps<U128> {
+  static __device__ __forceinline__ U128 zero() { return U128{0ull, 0ull}; }
+  static __device__ __forceinline__ void add(U128& a, uint64_t v) { add_u64(a, v); }
+  static __device__ __forceinline__ U128 warp_sum(U128 a) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const uint64_t l = __shfl_xor_sync(FULL, a.lo, o), h = __shfl_xor_sync(FULL, a.hi, o);
+      add_u128(a, l, h);
+    }
+    return a;
+  }
+  static __device__ __forceinline__ U128 shfl(U128 a, int src) {
+    return U128{__shfl_sync(FULL, a.lo, src), __shfl_sync(FULL, a.hi, src)};
+  }
+  // Aggregate terms on the exact fixed-point sum; only the result is rounded to double.
+  static __device__ __forceinline__ double finish(U128 S, const LayerConst& lc, uint8_t& reg) {
+    if (le_u128(S.lo, S.hi, lc.agg_ret_lo, lc.agg_ret_hi)) { reg = 0; return 0.0; }
+    U128 d = S;
+    asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;" : "+l"(d.lo), "+l"(d.hi)
+        : "l"(lc.agg_ret_lo), "l"(lc.agg_ret_hi));
+    if (le_u128(lc.agg_lim_lo, lc.agg_lim_hi, d.lo, d.hi)) {
+      reg = (d.lo == lc.agg_lim_lo && d.hi == lc.agg_lim_hi) ? 0 : 2;
+      return lc.agg_lim;
+    }
+    reg = 1;
+    const double v = __dadd_rn(__dmul_rn(__ull2double_rn(d.hi), 18446744073709551616.0),
+                               __ull2double_rn(d.lo));
+    return __dmul_rn(v, lc.inv_scale);
+  }
+};
+template <> struct AccOps<double> {
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ void add(double& a, uint64_t v) {
+    a = __dadd_rn(a, __longlong_as_double((long long)v));
+  }
+  static __device__ __forceinline__ double warp_sum(double a) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) a = __dadd_rn(a, __shfl_xor_sync(FULL, a, o));
+    return a;
+  }
+  static __device__ __forceinline__ double shfl(double a, int src) { return __shfl_sync(FULL, a, src); }
+  static __device__ __forceinline__ double finish(double S, const LayerConst& lc, uint8_t& reg) {
+    const double ex = __dsub_rn(S, lc.agg_ret);
+    reg = (ex > 0.0 && ex < lc.agg_lim) ? 1 : (ex > lc.agg_lim ? 2 : 0);
+    return clamp_terms(S, lc.agg_ret, lc.agg_lim);
+  }
+};
+
+// Coarse hit bitmap word cw: coarse bit i is the OR of the exact bits of events
+// [(32 cw + i) << shift, (32 cw + i + 1) << shift).
+__device__ __forceinline__ uint32_t coarsen_word(const uint32_t* __restrict__ src, int64_t cw,
+                                                 int shift, int64_t n_words) {
+  if (shift == 0) return cw < n_words ? src[cw] : 0u;
+  uint32_t out = 0;
+  if (shift <= 4) {
+    const int G = 1 << shift, per = 32 >> shift;
+    for (int w = 0; w < G; ++w) {
+      const int64_t ew = (cw << shift) + w;
+      const uint32_t x = ew < n_words ? src[ew] : 0u;
+      for (int b = 0; b < per; ++b)
+        out |= (((x >> (b * G)) & ((1u << G) - 1u)) ? 1u : 0u) << (w * per + b);
+    }
+  } else {
+    const int64_t wpb = (int64_t)1 << (shift - 5);  // exact words per coarse bit
+    for (int b = 0; b < 32; ++b) {
+      const int64_t w0 = (cw * 32 + b) * wpb;
+      uint32_t any = 0;
+      for (int64_t w = w0; w < w0 + wpb && w < n_words; ++w) any |= src[w];
+      out |= (any ? 1u : 0u) << b;
+    }
+  }
+  return out;
+}
+
+struct StreamParams {
+  int64_t n_trials;
+  const int64_t* offsets;
+  int64_t id_base;
+  int64_t n_events;
+  const int32_t* ids;
+  int32_t mis;             // (address of ids >> 2) & 3: element index of the 16-byte frame
+  int32_t shift;           // bitmap coarsening
+  int64_t catalogue;
+  const uint64_t* q;       // this layer's table
+  const uint32_t* bits;    // this layer's exact bitmap
+  int64_t bm_words;
+  int64_t smem_words;
+  const LayerConst* layer;
+  double* ylt;             // this layer's YLT row
+  uint8_t* regimes;        // this layer's regime row or nullptr
+  uint32_t* err;
+};
+
+// One event ID: range check, hit filter, gather, accumulate.
+template <bool FILTER, typename Acc>
+__device__ __forceinline__ void consume(int e, bool valid, const StreamParams& p,
+                                        const uint32_t* bm, const uint64_t* __restrict__ q,
+                                        Acc& acc, bool& bad) {
+  if (!valid) return;
+  if ((unsigned)e >= (unsigned)p.catalogue) { bad = true; return; }
+  if (FILTER) {
+    const uint32_t b = (uint32_t)e >> p.shift;
+    if (!((bm[b >> 5] >> (b & 31)) & 1u)) return;
+  }
+  AccOps<Acc>::add(acc, __ldg(q + e));
+}
+
+// ------------------------------------------------------------------------------------------
+// Folded YET stream.  A warp owns groups of 32 consecutive trials; for each trial the warp
+// reads the trial's event IDs with coalesced 16-byte streaming loads (scalar loads for the
+// unaligned head and tail), tests each ID against the layer's hit bitmap held in shared
+// memory, gathers q(e) from the L2-resident table only on hits, and sums exactly.  Lane k
+// keeps trial k's sum; the aggregate terms of all 32 trials run at once at the end.
+// ------------------------------------------------------------------------------------------
+template <bool FILTER, typename Acc, int U>
+__global__ void __launch_bounds__(YLT_THREADS, 1) k_ylt_folded(StreamParams p) {
+  extern __shared__ uint32_t bm[];
+  if (FILTER) {
+    for (int64_t cw = threadIdx.x; cw < p.smem_words; cw += blockDim.x)
+      bm[cw] = coarsen_word(p.bits, cw, p.shift, p.bm_words);
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const LayerConst lc = *p.layer;
+  const uint64_t* __restrict__ q = p.q;
+  const int4* __restrict__ base4 = reinterpret_cast<const int4*>(p.ids - p.mis);
+  const int64_t n_groups = (p.n_trials + 31) >> 5;
+  bool bad_id = false, bad_off = false;
+
+  for (int64_t g = warp; g < n_groups; g += nwarps) {
+    const int64_t t0 = g << 5;
+    const int nt = (int)min((int64_t)32, p.n_trials - t0);
+    const int64_t my_off = (lane <= nt) ? __ldg(p.offsets + t0 + lane) - p.id_base : 0;
+    const int64_t last_off = (nt == 32) ? __ldg(p.offsets + t0 + 32) - p.id_base : 0;
+    Acc mine = AccOps<Acc>::zero();
+    for (int k = 0; k < nt; ++k) {
+      int64_t beg = __shfl_sync(FULL, my_off, k);
+      int64_t end = (k + 1 < 32) ? __shfl_sync(FULL, my_off, k + 1) : last_off;
+      if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; beg = end = 0; }
+      Acc acc = AccOps<Acc>::zero();
+      const int64_t pb = beg + p.mis, pe = end + p.mis;
+      const int64_t vb = (pb + 3) >> 2, ve = pe >> 2;
+      {  // scalar edges: the unaligned head and tail (all of a trial with no full vector)
+        int64_t pos = -1;
+        if (vb >= ve) {
+          if (lane < pe - pb) pos = pb + lane;
+        } else {
+          const int nh = (int)(4 * vb - pb), ntl = (int)(pe - 4 * ve);
+          if (lane < nh) pos = pb + lane;
+          else if (lane >= 4 && lane < 4 + ntl) pos = 4 * ve + (lane - 4);
+        }
+        const int e = pos >= 0 ? __ldg(p.ids + (pos - p.mis)) : 0;
+        consume<FILTER>(e, pos >= 0, p, bm, q, acc, bad_id);
+      }
+      for (int64_t v = vb + lane; v < ve; v += 32 * U) {
+        int4 x[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          ok[u] = v + 32 * u < ve;
+          x[u] = ok[u] ? __ldcs(base4 + v + 32 * u) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          consume<FILTER>(x[u].x, ok[u], p, bm, q, acc, bad_id);
+          consume<FILTER>(x[u].y, ok[u], p, bm, q, acc, bad_id);
+          consume<FILTER>(x[u].z, ok[u], p, bm, q, acc, bad_id);
+          consume<FILTER>(x[u].w, ok[u], p, bm, q, acc, bad_id);
+        }
+      }
+      acc = AccOps<Acc>::warp_sum(acc);
+      if (lane == k) mine = acc;
+    }
+    if (lane < nt) {
+      uint8_t reg;
+      const double y = AccOps<Acc>::finish(mine, lc, reg);
+      p.ylt[t0 + lane] = y;
+      if (p.regimes) p.regimes[t0 + lane] = reg;
+    }
+  }
+  if (bad_id) atomicOr(p.err, DERR_EVENT_RANGE);
+  if (bad_off) atomicOr(p.err, DERR_OFFSETS);
+}
+
+// ------------------------------------------------------------------------------------------
+// Literal Algorithm 3: for every occurrence, every ELT of the layer is looked up in its
+// direct-access table.  Lanes are split into segments of W (a power of two >= the ELT count,
+// capped at 32); segment s handles one event, lane j of the segment the layer's j-th ELT.
+// The segment then sums the per-ELT results in the layer's ELT order (shuffles), applies the
+// occurrence terms, and adds the same fixed point q as the folded path, so both paths give
+// identical YLTs.
+// ------------------------------------------------------------------------------------------
+template <typename LossT>
+__global__ void __launch_bounds__(256)
+k_ylt_per_elt(StreamParams p, const LossT* __restrict__ dense, const int32_t* __restrict__ layer_elts,
+              const double* __restrict__ elt_ret, const double* __restrict__ elt_lim) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const LayerConst lc = *p.layer;
+  const int n_le = lc.elt_end - lc.elt_begin;
+  int W = 1;
+  while (W < n_le && W < 32) W <<= 1;
+  const int E = 32 / W;                       // events per warp step
+  const int seg = lane / W, jl = lane % W;
+  const int n_chunks = (n_le + 31) / 32;      // ELT chunks when n_le > 32 (then W = 32, E = 1)
+  const int64_t n_groups = (p.n_trials + 31) >> 5;
+  bool bad_id = false, bad_off = false;
+  for (int64_t g = warp; g < n_groups; g += nwarps) {
+    const int64_t t0 = g << 5;
+    const int nt = (int)min((int64_t)32, p.n_trials - t0);
+    const int64_t my_off = (lane <= nt) ? __ldg(p.offsets + t0 + lane) - p.id_base : 0;
+    const int64_t last_off = (nt == 32) ? __ldg(p.offsets + t0 + 32) - p.id_base : 0;
+    U128 mine = U128{0ull, 0ull};
+    for (int k = 0; k < nt; ++k) {
+      int64_t beg = __shfl_sync(FULL, my_off, k);
+      int64_t end = (k + 1 < 32) ? __shfl_sync(FULL, my_off, k + 1) : last_off;
+      if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; beg = end = 0; }
+      U128 acc = U128{0ull, 0ull};
+      for (int64_t base = beg; base < end; base += E) {
+        const int64_t pos = base + seg;
+        const bool have = pos < end;
+        int e = have ? __ldg(p.ids + pos) : 0;
+        const bool in_range = (unsigned)e < (unsigned)p.catalogue;
+        if (have && !in_range) bad_id = true;
+        const bool use = have && in_range;
+        double s = 0.0;
+        for (int c = 0; c < n_chunks; ++c) {
+          const int jj = c * 32 + jl;
+          double a = 0.0;
+          if (use && jl < W && jj < n_le) {
+            const int j = layer_elts[lc.elt_begin + jj];
+            const double x = (double)dense[(int64_t)j * p.catalogue + e];
+            if (x != 0.0) a = clamp_terms(x, elt_ret[j], elt_lim[j]);  // absent: C(0) = 0
+          }
+          const int lim = min(32, n_le - c * 32);
+          for (int m = 0; m < min(lim, W); ++m) {
+            const double am = __shfl_sync(FULL, a, seg * W + m);
+            if (am != 0.0) s = __dadd_rn(s, am);
+          }
+        }
+        if (use && jl == 0 && s != 0.0) {
+          const double o = clamp_terms(s, lc.occ_ret, lc.occ_lim);
+          add_u64(acc, __double2ull_rn(__dmul_rn(o, lc.scale)));
+        }
+      }
+      acc = AccOps<U128>::warp_sum(acc);
+      if (lane == k) mine = acc;
+    }
+    if (lane < nt) {
+      uint8_t reg;
+      const double y = AccOps<U128>::finish(mine, lc, reg);
+      p.ylt[t0 + lane] = y;
+      if (p.regimes) p.regimes[t0 + lane] = reg;
+    }
+  }
+  if (bad_id) atomicOr(p.err, DERR_EVENT_RANGE);
+  if (bad_off) atomicOr(p.err, DERR_OFFSETS);
+}
+
+// Dense direct-access tables from the records: table[j][e] = loss (zero-filled beforehand).
+template <typename LossT>
+__global__ void k_scatter_dense(int32_t n_elts, int64_t catalogue, const int64_t* __restrict__ rec_off,
+                                const int32_t* __restrict__ rec_ids, const LossT* __restrict__ rec_loss,
+                                LossT* __restrict__ dense) {
+  const int j = blockIdx.y;
+  for (int64_t r = rec_off[j] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rec_off[j + 1];
+       r += (int64_t)gridDim.x * blockDim.x)
+    dense[(int64_t)j * catalogue + rec_ids[r]] = rec_loss[r];
+}
+
+// ------------------------------------------------------------------------------------------
+// Host launchers
+// ------------------------------------------------------------------------------------------
+// 32-bit words of a hit bitmap with one bit per 2^shift catalogue events.
+static int64_t coarse_words(int64_t catalogue, int shift) {
+  const int64_t bits = (catalogue + ((int64_t)1 << shift) - 1) >> shift;
+  return (bits + 31) / 32;
+}
+
+static int bitmap_shift(int64_t catalogue, int64_t max_bytes) {
+  int s = 0;
+  while (coarse_words(catalogue, s) * 4 > max_bytes) ++s;
+  return s;
+}
+
+static ara_status set_smem(const void* fn, int bytes) {
+  ARA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return ARA_OK;
+}
+
+ara_status build_dense(Portfolio& pf, cudaStream_t s) {
+  if (pf.n_elts == 0) return ARA_OK;
+  const size_t esz = pf.d_rec_loss32 ? sizeof(float) : sizeof(double);
+  ARA_TRY(cudaMemsetAsync(pf.d_dense, 0, esz * (size_t)pf.n_elts * pf.catalogue, s));
+  dim3 grid(64, pf.n_elts);
+  LaunchScope ls(ARA_K_FOLD, s);
+  if (pf.d_rec_loss32)
+    k_scatter_dense<float><<<grid, 256, 0, s>>>(pf.n_elts, pf.catalogue, pf.d_rec_off, pf.d_rec_ids,
+                                                pf.d_rec_loss32, (float*)pf.d_dense);
+  else
+    k_scatter_dense<double><<<grid, 256, 0, s>>>(pf.n_elts, pf.catalogue, pf.d_rec_off, pf.d_rec_ids,
+                                                 pf.d_rec_loss, (double*)pf.d_dense);
+  ARA_TRY(cudaGetLastError());
+  return ARA_OK;
+}
+
+ara_status launch_fold(Portfolio& pf, int32_t n_sel, const int32_t* sel_host, int32_t flags,
+                       cudaStream_t s) {
+  const int f64 = (flags & ARA_RUN_F64_SUM) ? 1 : 0;
+  for (int32_t b = 0; b < n_sel; b += MAX_SEL) {
+    SelList sl;
+    sl.n = min(MAX_SEL, n_sel - b);
+    for (int i = 0; i < sl.n; ++i) sl.idx[i] = sel_host[b + i];
+    dim3 grid((unsigned)((pf.catalogue + FOLD_TILE - 1) / FOLD_TILE), sl.n);
+    LaunchScope ls(ARA_K_FOLD, s);
+    if (pf.d_rec_loss32)
+      k_fold<float><<<grid, FOLD_THREADS, 0, s>>>(pf.catalogue, pf.d_rec_off, pf.d_rec_ids,
+                                                  pf.d_rec_loss32, pf.d_elt_ret, pf.d_elt_lim,
+                                                  pf.d_layer_elts, pf.d_layers, sl, pf.d_q,
+                                                  pf.d_bits, pf.bm_words, f64);
+    else
+      k_fold<double><<<grid, FOLD_THREADS, 0, s>>>(pf.catalogue, pf.d_rec_off, pf.d_rec_ids,
+                                                   pf.d_rec_loss, pf.d_elt_ret, pf.d_elt_lim,
+                                                   pf.d_layer_elts, pf.d_layers, sl, pf.d_q,
+                                                   pf.d_bits, pf.bm_words, f64);
+    ARA_TRY(cudaGetLastError());
+  }
+  return ARA_OK;
+}
+
+template <bool FILTER, typename Acc>
+static ara_status launch_folded_one(Portfolio& pf, StreamParams& sp, cudaStream_t s) {
+  constexpr int U = 2;
+  const auto fn = k_ylt_folded<FILTER, Acc, U>;
+  const int smem = FILTER ? (int)(sp.smem_words * 4) : 0;
+  if (smem > 48 * 1024) {
+    ara_status st = set_smem((const void*)fn, smem);
+    if (st != ARA_OK) return st;
+  }
+  LaunchScope ls(ARA_K_YLT, s);
+  fn<<<pf.n_sms, YLT_THREADS, smem, s>>>(sp);
+  ARA_TRY(cudaGetLastError());
+  return ARA_OK;
+}
+
+ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
+  const int64_t max_smem_bitmap = 200 * 1024;
+  StreamParams sp{};
+  sp.n_trials = a.n_trials;
+  sp.offsets = a.offsets;
+  sp.id_base = a.id_base;
+  sp.n_events = a.n_events;
+  sp.ids = a.ids;
+  sp.mis = (int32_t)(((uintptr_t)a.ids >> 2) & 3);
+  sp.catalogue = pf.catalogue;
+  sp.shift = bitmap_shift(pf.catalogue, max_smem_bitmap);
+  sp.smem_words = coarse_words(pf.catalogue, sp.shift);
+  sp.bm_words = pf.bm_words;
+  sp.err = pf.d_err;
+  const bool per_elt = (a.flags & ARA_RUN_PER_ELT) != 0;
+  for (int32_t i = 0; i < a.n_sel; ++i) {
+    const int layer = a.sel[i];
+    sp.q = pf.d_q + (int64_t)layer * pf.catalogue;
+    sp.bits = pf.d_bits + (int64_t)layer * pf.bm_words;
+    sp.layer = pf.d_layers + layer;
+    sp.ylt = a.ylt + (int64_t)i * a.row_stride;
+    sp.regimes = a.regimes ? a.regimes + (int64_t)i * a.row_stride : nullptr;
+    if (a.n_trials == 0) continue;
+    ara_status st;
+    if (per_elt) {
+      LaunchScope ls(ARA_K_YLT, s);
+      const int grid = pf.n_sms * 8;
+      if (pf.d_rec_loss32)
+        k_ylt_per_elt<float><<<grid, 256, 0, s>>>(sp, (const float*)pf.d_dense, pf.d_layer_elts,
+                                                  pf.d_elt_ret, pf.d_elt_lim);
+      else
+        k_ylt_per_elt<double><<<grid, 256, 0, s>>>(sp, (const double*)pf.d_dense, pf.d_layer_elts,
+                                                   pf.d_elt_ret, pf.d_elt_lim);
+      ARA_TRY(cudaGetLastError());
+      st = ARA_OK;
+    } else if (a.flags & ARA_RUN_F64_SUM) {
+      st = (a.flags & ARA_RUN_NO_FILTER) ? launch_folded_one<false, double>(pf, sp, s)
+                                         : launch_folded_one<true, double>(pf, sp, s);
+    } else {
+      st = (a.flags & ARA_RUN_NO_FILTER) ? launch_folded_one<false, U128>(pf, sp, s)
+                                         : launch_folded_one<true, U128>(pf, sp, s);
+    }
+    if (st != ARA_OK) return st;
+  }
+  return ARA_OK;
+}
+
+}  // namespace ara

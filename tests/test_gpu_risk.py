@@ -1,0 +1,76 @@
+"""GPU parity of PML / TVaR selection (ara_risk_metrics) against the oracle's order
+statistics.  Inputs are YLTs from the generator or the oracle, never from the CUDA path,
+except in the end-to-end test, which compares GPU(YLT_gpu) with oracle(YLT_oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_1606_04473_gb300 as ara
+
+RPS = [1.0, 2.0, 10.0, 100.0, 250.0]
+LEVELS = [0.0, 0.5, 0.9, 0.99]
+
+
+def check(ylt, rps=RPS, levels=LEVELS):
+    ylt = np.atleast_2d(ylt)
+    n = ylt.shape[1]
+    rps = [r for r in rps if np.ceil(n / r) >= 1]
+    p, t = ara.risk_metrics(torch.from_numpy(ylt).cuda(), rps, levels)
+    rp, rt = oracle.risk_metrics(ylt, rps, levels)
+    assert np.array_equal(p, rp)                       # PML is a copy of a YLT entry
+    np.testing.assert_allclose(t, rt, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 10, 1000, 4097, 100_003])
+def test_lognormal_ylt(n):
+    rng = np.random.default_rng(n)
+    check(rng.lognormal(14, 2, n))
+
+
+def test_many_ties_and_zeros():
+    rng = np.random.default_rng(1)
+    y = np.round(rng.lognormal(5, 1, 20_000), 0)
+    y[:12_000] = 0.0
+    y[12_000:12_500] = 5e6
+    check(y)
+
+
+def test_signed_and_special_values():
+    rng = np.random.default_rng(2)
+    y = rng.normal(0, 1e3, 5000)
+    y[:10] = [0.0, -0.0, 1e-310, -1e-310, 1e300, -1e300, 5e-324, 3.0, 3.0, 3.0]
+    check(y, levels=[0.5, 0.99, 0.999])   # tails contain +1e300 but not -1e300
+
+
+def test_multiple_layers_independent():
+    rng = np.random.default_rng(3)
+    y = np.stack([rng.lognormal(10, s, 30_000) for s in (0.5, 1.0, 2.0, 3.0)])
+    check(y)
+
+
+def test_hand_computed_example(golden_dir):
+    import json, os
+    g = json.load(open(os.path.join(golden_dir, "p8_order_statistics.json")))
+    y = np.array(g["ylt"])
+    rps = [float(k) for k in g["pml"]]
+    lv = [float(k) for k in g["tvar"]]
+    p, t = ara.risk_metrics(torch.from_numpy(y).cuda(), rps, lv)
+    assert p[0].tolist() == [g["pml"][k] for k in g["pml"]]
+    np.testing.assert_allclose(t[0], [g["tvar"][k] for k in g["tvar"]], rtol=1e-15)
+
+
+def test_end_to_end_tiny_workload():
+    pf, yet = synth.tiny(0)
+    g = ara.Portfolio.from_tables(pf)
+    y = g.run_ylt(torch.from_numpy(yet.offsets).cuda(), torch.from_numpy(yet.event_ids).cuda())
+    p, t = ara.risk_metrics(y, [100.0, 250.0], [0.99])
+    ref = oracle.ylt(pf, yet)
+    rp, rt = oracle.risk_metrics(ref, [100.0, 250.0], [0.99])
+    np.testing.assert_allclose(p, rp, rtol=1e-6)
+    np.testing.assert_allclose(t, rt, rtol=1e-6)

@@ -1,0 +1,290 @@
+"""GPU parity of the YLT path (C ABI through the binding) against the FP64 CPU oracle.
+
+Tolerance (every YLT entry): |y_gpu - y_ref| <= 1e-6 |y_ref| + 1e-12 S_ref, where S_ref is
+the oracle's aggregate loss before the aggregate terms.  The relative part is the required
+1e-6; the absolute part covers the rounding of any reordered FP64 summation of a trial
+(about n_t * 2^-53 * S_ref, below 1e-12 S_ref for the trial lengths used) and of the fixed
+point the device sums in (resolution below 2^-61 of the largest occurrence loss per event),
+which dominate only where y_ref is tiny next to S_ref (the aggregate retention kink).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_1606_04473_gb300 as ara
+
+INF = float("inf")
+FLAG_SETS = [0, 2, 4, 6]  # folded; no filter; FP64 sums; both
+
+
+def dev(yet):
+    return (torch.from_numpy(np.ascontiguousarray(yet.offsets)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(yet.event_ids)).cuda())
+
+
+def assert_ylt_close(got, ref, agg):
+    got = np.asarray(got)
+    err = np.abs(got - ref)
+    tol = 1e-6 * np.abs(ref) + 1e-12 * np.abs(agg)
+    bad = err > tol
+    assert not bad.any(), (f"{bad.sum()} of {bad.size} entries out of tolerance; worst "
+                           f"{np.max(err / np.maximum(tol, 1e-300)):.3g}x tol")
+
+
+def mid_case(seed, catalogue=200_000, n_elts=12, nnz=4000, n_layers=4, n_trials=5003,
+             lam=300.0, f32=True, max_le=None):
+    """Mid-size portfolio spanning many tiles, ragged trial lengths (empty, 1..7 events,
+    Poisson bulk), varied terms so that all clamp regimes occur."""
+    rng = np.random.default_rng(seed)
+    ids, losses = synth.make_elts(seed, n_elts, nnz, catalogue, 11.0, 2.0, f32=f32)
+    r, l = synth.percentile_terms(losses)
+    layers = []
+    for k in range(n_layers):
+        m = int(rng.integers(1, (max_le or n_elts) + 1))
+        layers.append(sorted(rng.choice(n_elts, size=min(m, n_elts), replace=False).tolist()))
+    counts = synth.poisson_counts(seed, lam, n_trials)
+    counts[:8] = [0, 1, 2, 3, 4, 5, 6, 7]
+    counts[-3:] = [0, 9, 1]
+    yet = synth.make_yet(seed, counts, catalogue, with_timestamps=False)
+    pf = synth.Portfolio(catalogue, ids, losses, r, l, layers, np.zeros(n_layers),
+                         np.zeros(n_layers), np.zeros(n_layers), np.zeros(n_layers), losses_f32=f32)
+    # layer terms from the oracle's own event/trial losses: retention at the 20th percentile,
+    # limits low enough that a share of trials saturates
+    from oracle.derive_terms import derive
+    nh = min(1000, n_trials)
+    head = synth.YET(yet.offsets[:nh + 1], yet.event_ids[:int(yet.offsets[nh])])
+    t = derive(pf, head, 20.0, 70.0)
+    return pf.with_terms(t), yet
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    pf, yet = synth.tiny(0)
+    ref, agg = oracle.ylt(pf, yet, return_agg=True)
+    return pf, yet, ref, agg
+
+
+@pytest.fixture(scope="module")
+def mid():
+    pf, yet = mid_case(1)
+    ref, agg = oracle.ylt(pf, yet, return_agg=True)
+    return pf, yet, ref, agg
+
+
+@pytest.mark.parametrize("flags", FLAG_SETS)
+def test_tiny_workload_matches_oracle(tiny, flags):
+    pf, yet, ref, agg = tiny
+    g = ara.Portfolio.from_tables(pf)
+    y = g.run_ylt(*dev(yet), flags=flags)
+    g.check()
+    assert_ylt_close(y.cpu().numpy(), ref, agg)
+
+
+def test_tiny_workload_per_elt_literal_path_equals_folded_bitwise(tiny):
+    pf, yet, ref, agg = tiny
+    g = ara.Portfolio.from_tables(pf, dense_tables=True)
+    off, ids = dev(yet)
+    a = g.run_ylt(off, ids, flags=ara.ARA_RUN_PER_ELT)
+    b = g.run_ylt(off, ids)
+    g.check()
+    assert torch.equal(a, b)
+    assert_ylt_close(a.cpu().numpy(), ref, agg)
+
+
+@pytest.mark.parametrize("flags", FLAG_SETS)
+def test_mid_size_multi_layer_ragged(mid, flags):
+    pf, yet, ref, agg = mid
+    g = ara.Portfolio.from_tables(pf)
+    y = g.run_ylt(*dev(yet), flags=flags)
+    g.check()
+    assert_ylt_close(y.cpu().numpy(), ref, agg)
+
+
+def test_mid_size_regimes_all_present_and_recorded(mid):
+    pf, yet, ref, agg = mid
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    reg = torch.empty((pf.n_layers, yet.n_trials), dtype=torch.uint8, device="cuda")
+    g.run_ylt(off, ids, regimes=reg)
+    g.check()
+    reg = reg.cpu().numpy()
+    ex = agg - pf.agg_ret[:, None]
+    want = np.where((ex > 0) & (ex < pf.agg_lim[:, None]), 1, np.where(ex > pf.agg_lim[:, None], 2, 0))
+    near = np.abs(ex) <= 1e-9 * np.abs(agg) + 1e-6
+    near |= np.abs(ex - pf.agg_lim[:, None]) <= 1e-9 * np.abs(agg) + 1e-6
+    assert np.array_equal(reg[~near], want[~near])
+    for r in (0, 1, 2):
+        assert (want == r).any(), f"regime {r} absent from the test case"
+
+
+def test_layer_subset_and_order(mid):
+    pf, yet, ref, agg = mid
+    g = ara.Portfolio.from_tables(pf)
+    y = g.run_ylt(*dev(yet), layers=[3, 0, 3])
+    assert_ylt_close(y.cpu().numpy(), ref[[3, 0, 3]], agg[[3, 0, 3]])
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_unaligned_event_id_pointer(mid, shift):
+    pf, yet, ref, agg = mid
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    buf = torch.empty(ids.numel() + 4, dtype=torch.int32, device="cuda")
+    view = buf[shift:shift + ids.numel()]
+    view.copy_(ids)
+    assert (view.data_ptr() // 4) % 4 == shift % 4
+    y = g.run_ylt(off, view)
+    g.check()
+    assert_ylt_close(y.cpu().numpy(), ref, agg)
+
+
+def test_large_catalogue_coarse_filter():
+    """A 6M-event catalogue: the shared-memory hit bitmap must be coarsened (one bit per 2^k
+    events); results stay exact."""
+    pf, yet = mid_case(2, catalogue=6_000_000, n_elts=6, nnz=30_000, n_layers=2, n_trials=1500,
+                       lam=500.0)
+    ref, agg = oracle.ylt(pf, yet, return_agg=True)
+    g = ara.Portfolio.from_tables(pf)
+    for flags in (0, 2):
+        y = g.run_ylt(*dev(yet), flags=flags)
+        g.check()
+        assert_ylt_close(y.cpu().numpy(), ref, agg)
+
+
+def test_per_elt_path_many_elts_and_fp64_losses():
+    """Layers wider than a warp (40 ELTs), a one-ELT layer and an empty layer; FP64 losses."""
+    pf, yet = mid_case(3, catalogue=50_000, n_elts=40, nnz=800, n_layers=1, n_trials=700,
+                       lam=200.0, f32=False)
+    pf.layer_elts = [list(range(40)), [7], []]
+    for name in ["occ_ret", "occ_lim", "agg_ret", "agg_lim"]:
+        setattr(pf, name, np.repeat(getattr(pf, name), 3))
+    ref, agg = oracle.ylt(pf, yet, return_agg=True)
+    g = ara.Portfolio.from_tables(pf, dense_tables=True)
+    off, ids = dev(yet)
+    a = g.run_ylt(off, ids, flags=ara.ARA_RUN_PER_ELT)
+    b = g.run_ylt(off, ids)
+    g.check()
+    assert torch.equal(a, b)
+    assert_ylt_close(a.cpu().numpy(), ref, agg)
+    assert np.all(ref[2] == 0.0)
+
+
+def test_identity_terms_give_raw_loss_sums():
+    pf, yet = mid_case(4, n_layers=2, n_trials=900)
+    pf = pf.with_terms({**pf.terms_dict(), "elt_ret": [0.0] * pf.n_elts, "elt_lim": [INF] * pf.n_elts,
+                        "occ_ret": [0.0, 0.0], "occ_lim": [INF, INF], "agg_ret": [0.0, 0.0],
+                        "agg_lim": [INF, INF]})
+    g = ara.Portfolio.from_tables(pf)
+    y = g.run_ylt(*dev(yet)).cpu().numpy()
+    trial = np.repeat(np.arange(yet.n_trials), np.diff(yet.offsets))
+    for l, elts in enumerate(pf.layer_elts):
+        dense = np.zeros(pf.catalogue)
+        for j in elts:
+            np.add.at(dense, pf.elt_ids[j], pf.elt_losses[j])
+        expect = np.bincount(trial, weights=dense[yet.event_ids], minlength=yet.n_trials)
+        np.testing.assert_allclose(y[l], expect, rtol=1e-12, atol=0)
+
+
+def test_edge_cases_empty_inputs(tiny):
+    pf, yet, ref, agg = tiny
+    g = ara.Portfolio.from_tables(pf)
+    off0 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ids0 = torch.zeros(0, dtype=torch.int32, device="cuda")
+    y = g.run_ylt(off0, ids0)
+    assert y.shape == (1, 0)
+    offz = torch.zeros(65, dtype=torch.int64, device="cuda")     # 64 empty trials
+    y = g.run_ylt(offz, ids0)
+    g.check()
+    assert torch.all(y == 0)
+
+
+def test_device_side_data_errors_are_reported_and_recoverable(tiny):
+    pf, yet, ref, agg = tiny
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    bad = ids.clone()
+    bad[17] = pf.catalogue          # event ID outside the catalogue
+    g.run_ylt(off, bad)
+    with pytest.raises(ara.AraError) as e:
+        g.check()
+    assert e.value.status == ara.ARA_EDATA
+    boff = off.clone()
+    boff[5] = boff[6] + 1           # decreasing offsets
+    g.run_ylt(boff, ids)
+    with pytest.raises(ara.AraError):
+        g.check()
+    y = g.run_ylt(off, ids)          # a good run afterwards is unaffected
+    g.check()
+    assert_ylt_close(y.cpu().numpy(), ref, agg)
+
+
+def test_repeatable_bitwise(mid):
+    pf, yet, ref, agg = mid
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    a = g.run_ylt(off, ids).clone()
+    b = g.run_ylt(off, ids)
+    assert torch.equal(a, b)
+
+
+def test_host_pipeline_equals_device_path(mid):
+    pf, yet, ref, agg = mid
+    g = ara.Portfolio.from_tables(pf)
+    y_dev = g.run_ylt(*dev(yet))
+    y_host = g.run_ylt_host(yet.offsets, yet.event_ids)
+    assert np.array_equal(y_dev.cpu().numpy(), y_host)
+    y2, p, t = g.run_ylt_host(yet.offsets, yet.event_ids, layers=[2, 1], return_periods=[100.0, 250.0],
+                              tvar_levels=[0.99])
+    assert np.array_equal(y2, y_host[[2, 1]])
+    p_dev, t_dev = ara.risk_metrics(y_dev[[2, 1]].contiguous(), [100.0, 250.0], [0.99])
+    assert np.array_equal(p, p_dev) and np.array_equal(t, t_dev)
+    _, p3, t3 = g.run_ylt_host(yet.offsets, yet.event_ids, return_periods=[10.0], tvar_levels=[0.5],
+                               want_ylt=False)
+    rp, rt = oracle.risk_metrics(ref, [10.0], [0.5])
+    np.testing.assert_allclose(p3, rp, rtol=1e-6)
+    np.testing.assert_allclose(t3, rt, rtol=1e-6)
+
+
+def test_host_pipeline_multi_chunk():
+    """More than one 16M-event chunk through the host pipeline, pinned host memory."""
+    pf = synth.paper_scale_portfolio(0)
+    n = 40_000
+    ids = torch.empty(n * 1000, dtype=torch.int32).pin_memory()
+    yet = synth.paper_scale_yet(0, n_trials=n, ids_out=ids.numpy())
+    g = ara.Portfolio.from_tables(pf)
+    y_host = g.run_ylt_host(yet.offsets, ids.numpy())
+    y_dev = g.run_ylt(torch.from_numpy(yet.offsets).cuda(), ids.cuda()).cpu().numpy()
+    assert np.array_equal(y_host, y_dev)
+    sample = np.arange(0, n, 97)
+    ref, agg = oracle.ylt(pf, yet, trials=sample, return_agg=True)
+    assert_ylt_close(y_host[:, sample], ref, agg)
+
+
+def test_paper_scale_full_size_sampled():
+    """The paper-scale workload (1 layer of 15 ELTs, 2M-event catalogue, 10^6 trials x 1000
+    events) in the benchmark's launch configuration; 4000 sampled trials against the oracle,
+    range and determinism properties on all entries."""
+    pf = synth.paper_scale_portfolio(0)
+    n = 1_000_000
+    ids_h = torch.empty(n * 1000, dtype=torch.int32).pin_memory()
+    yet = synth.paper_scale_yet(0, n_trials=n, ids_out=ids_h.numpy())
+    g = ara.Portfolio.from_tables(pf)
+    off = torch.from_numpy(yet.offsets).cuda()
+    ids = ids_h.cuda()
+    y = g.run_ylt(off, ids)
+    y2 = g.run_ylt(off, ids)
+    g.check()
+    assert torch.equal(y, y2)
+    yc = y.cpu().numpy()
+    assert np.all(yc >= 0) and np.all(yc <= pf.agg_lim[0])
+    rng = np.random.default_rng(5)
+    sample = np.unique(np.concatenate([rng.integers(0, n, 3990), [0, 1, n - 2, n - 1]]))
+    ref, agg = oracle.ylt(pf, yet, trials=sample, return_agg=True)
+    assert_ylt_close(yc[:, sample], ref, agg)
+    del ids
