@@ -371,7 +371,7 @@ ara_status ara_run_ylt(ara_portfolio* pf, int64_t n_trials, const int64_t* d_off
   ara_status st = check_selection(*pf, n_sel, layer_sel, sel);
   if (st != ARA_OK) return st;
   if ((st = check_flags(*pf, flags)) != ARA_OK) return st;
-  if (sel.empty()) return ARA_OK;
+  if (sel.empty() || n_trials == 0) return ARA_OK;
   if (!d_offsets || !d_ylt || (n_events > 0 && !d_ids)) return ARA_EINVAL;
   if (((uintptr_t)d_ids & 3) || ((uintptr_t)d_offsets & 7) || ((uintptr_t)d_ylt & 7)) return ARA_EINVAL;
   DeviceGuard g(pf->device);
