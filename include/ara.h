@@ -145,8 +145,8 @@ ARA_API ara_status ara_run_ylt(ara_portfolio* pf, int64_t n_trials, const int64_
  *   h_trial_offsets host [n_trials + 1], [0] = 0, non-decreasing (validated: ARA_EINVAL)
  *   h_event_ids     host [h_trial_offsets[n_trials]]
  *   h_ylt           host [n_layer_sel][n_trials] or NULL (then only the metrics are returned)
- *   n_rp, return_periods, n_tvar, tvar_levels, h_pml, h_tvar: as in ara_risk_metrics, or
- *                   n_rp = n_tvar = 0 for no metrics
+ *   n_rp, return_periods, n_tvar, tvar_levels, h_pml, h_tvar, h_mean: as in
+ *                   ara_risk_metrics, or n_rp = n_tvar = 0 and h_mean = NULL for no metrics
  * Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA, ARA_EDATA (event ID outside the catalogue).
  */
 ARA_API ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials,
@@ -154,7 +154,7 @@ ARA_API ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials,
                                     int32_t n_layer_sel, const int32_t* layer_sel, double* h_ylt,
                                     int32_t n_rp, const double* return_periods, int32_t n_tvar,
                                     const double* tvar_levels, double* h_pml, double* h_tvar,
-                                    int32_t flags, void* stream);
+                                    double* h_mean, int32_t flags, void* stream);
 
 /* Synchronise `stream`, then report (and clear) device-side data errors recorded by earlier
  * asynchronous runs of this portfolio: ARA_OK or ARA_EDATA. */
@@ -174,14 +174,15 @@ ARA_API ara_status ara_check(ara_portfolio* pf, void* stream);
  *   return_periods host [n_rp], each >= 1 with 1 <= ceil(N/RP) <= N
  *   tvar_levels   host [n_tvar], each in [0, 1) with ceil(N(1-p)) >= 1
  *   h_pml         host [n_layers][n_rp];  h_tvar host [n_layers][n_tvar]
- * n_rp + n_tvar <= 16, n_trials >= 1.  Allocates its scratch with the stream-ordered
- * allocator (cudaMallocAsync) on `stream`.
+ *   h_mean        host [n_layers] or NULL: the mean year loss (1/N) sum_t y_t of each row
+ * n_rp + n_tvar <= 16 (at least one metric requested), n_trials >= 1.  Allocates its scratch
+ * with the stream-ordered allocator (cudaMallocAsync) on `stream`.
  * Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA.
  */
 ARA_API ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, int32_t n_layers,
                             int32_t n_rp, const double* return_periods, int32_t n_tvar,
                             const double* tvar_levels, double* h_pml, double* h_tvar,
-                            void* stream);
+                            double* h_mean, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Introspection for measurement.

@@ -191,9 +191,11 @@ def risk_metrics(ylt_: np.ndarray, rps: Sequence[float], levels: Sequence[float]
 # ------------------------------------------------------------------------------------------
 
 def objective_weights(ylt_: np.ndarray, objective: str, level: float = 0.99):
-    """Per-trial weights w_t of J = sum_t w_t y_t: 1/N for the mean year loss; 1/m on the
-    m = ceil(N(1-p)) largest year losses for TVaR_p.  Returns (w, tie) where tie reports
-    y_(m) == y_(m+1) (TVaR's top set, and so its gradient, is then not unique)."""
+    """Per-trial weights w_t of J = sum_t w_t y_t: 1/N for the mean year loss; for TVaR_p, with
+    m = ceil(N(1-p)) and v the m-th largest year loss, 1/m on every y_t > v and the remaining
+    weight (m - #{y > v}) / m shared equally by the trials with y_t == v (the mean over every
+    choice of the top-m set).  Returns (w, tie): tie reports that the top-m set is not unique
+    (#{y >= v} > m), so TVaR is not differentiable in the usual sense there."""
     ylt_ = np.atleast_2d(ylt_)
     nl, n = ylt_.shape
     w = np.zeros((nl, n))
@@ -204,9 +206,13 @@ def objective_weights(ylt_: np.ndarray, objective: str, level: float = 0.99):
             ties.append(False)
         elif objective == "tvar":
             m = tail_count(n, level)
-            order = np.argsort(-ylt_[l], kind="stable")
-            w[l, order[:m]] = 1.0 / m
-            ties.append(bool(m < n and ylt_[l, order[m - 1]] == ylt_[l, order[m]]))
+            v = np.sort(ylt_[l])[::-1][m - 1]
+            gt = ylt_[l] > v
+            eq = ylt_[l] == v
+            c_gt, c_eq = int(gt.sum()), int(eq.sum())
+            w[l, gt] = 1.0 / m
+            w[l, eq] = (m - c_gt) / (c_eq * m)
+            ties.append(c_gt + c_eq > m)
         else:
             raise ValueError(objective)
     return w, ties

@@ -51,9 +51,9 @@ def lib() -> ctypes.CDLL:
     L.ara_destroy_portfolio.argtypes = [P]
     L.ara_destroy_portfolio.restype = None
     L.ara_run_ylt.argtypes = [P, i64, P, i64, P, P, i32, P, P, P, i32, P]
-    L.ara_run_ylt_host.argtypes = [P, i64, P, P, i32, P, P, i32, P, i32, P, P, P, i32, P]
+    L.ara_run_ylt_host.argtypes = [P, i64, P, P, i32, P, P, i32, P, i32, P, P, P, P, i32, P]
     L.ara_check.argtypes = [P, P]
-    L.ara_risk_metrics.argtypes = [P, i64, i32, i32, P, i32, P, P, P, P]
+    L.ara_risk_metrics.argtypes = [P, i64, i32, i32, P, i32, P, P, P, P, P]
     L.ara_launch_count.restype = i64
     L.ara_timing_enable.argtypes = [i32]
     L.ara_timing_enable.restype = None
@@ -177,7 +177,7 @@ class Portfolio:
 
     def run_ylt_host(self, offsets: np.ndarray, event_ids: np.ndarray, layers=None, out=None,
                      return_periods: Sequence[float] = (), tvar_levels: Sequence[float] = (),
-                     want_ylt: bool = True, flags: int = 0, stream=None):
+                     want_ylt: bool = True, want_mean: bool = False, flags: int = 0, stream=None):
         """The whole analysis from host memory (synchronous): YLT [n_layers_selected, n_trials]
         on the host, plus (PML, TVaR) when return periods / levels are given.  Pinned host
         arrays (e.g. from torch pin_memory) transfer at full link bandwidth."""
@@ -193,10 +193,14 @@ class Portfolio:
         lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
         pml = np.zeros((n_out, rp.size))
         tvar = np.zeros((n_out, lv.size))
+        mean = np.zeros(n_out) if want_mean else None
         st = lib().ara_run_ylt_host(self._h, n_trials, _np_ptr(offsets), _np_ptr(event_ids), n_sel,
                                     sel_p, _np_ptr(out), rp.size, _np_ptr(rp), lv.size, _np_ptr(lv),
-                                    _np_ptr(pml), _np_ptr(tvar), int(flags), _stream_handle(stream))
+                                    _np_ptr(pml), _np_ptr(tvar), _np_ptr(mean), int(flags),
+                                    _stream_handle(stream))
         _check(st, "ara_run_ylt_host")
+        if want_mean:
+            return out, pml, tvar, mean
         if rp.size or lv.size:
             return out, pml, tvar
         return out
@@ -206,8 +210,9 @@ class Portfolio:
 
 
 def risk_metrics(ylt, return_periods: Sequence[float] = (), tvar_levels: Sequence[float] = (),
-                 stream=None):
-    """(PML [n_layers, n_rp], TVaR [n_layers, n_tvar]) of a device YLT [n_layers, n_trials]."""
+                 stream=None, want_mean: bool = False):
+    """(PML [n_layers, n_rp], TVaR [n_layers, n_tvar][, mean [n_layers]]) of a device YLT
+    [n_layers, n_trials]."""
     import torch
     ylt2 = ylt if ylt.dim() == 2 else ylt.reshape(1, -1)
     nl, n = ylt2.shape
@@ -215,10 +220,12 @@ def risk_metrics(ylt, return_periods: Sequence[float] = (), tvar_levels: Sequenc
     lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
     pml = np.zeros((nl, rp.size))
     tvar = np.zeros((nl, lv.size))
+    mean = np.zeros(nl) if want_mean else None
     st = lib().ara_risk_metrics(_dev_ptr(ylt2, torch.float64, "ylt"), n, nl, rp.size, _np_ptr(rp),
-                                lv.size, _np_ptr(lv), _np_ptr(pml), _np_ptr(tvar), _stream_handle(stream))
+                                lv.size, _np_ptr(lv), _np_ptr(pml), _np_ptr(tvar), _np_ptr(mean),
+                                _stream_handle(stream))
     _check(st, "ara_risk_metrics")
-    return pml, tvar
+    return (pml, tvar, mean) if want_mean else (pml, tvar)
 
 
 def launch_count() -> int:

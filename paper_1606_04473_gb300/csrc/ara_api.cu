@@ -443,15 +443,15 @@ static ara_status ensure_stage(Portfolio& pf, int64_t events, int64_t trials, in
 ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* h_off,
                             const int32_t* h_ids, int32_t n_sel, const int32_t* layer_sel,
                             double* h_ylt, int32_t n_rp, const double* rps, int32_t n_tvar,
-                            const double* levels, double* h_pml, double* h_tvar, int32_t flags,
-                            void* stream) {
+                            const double* levels, double* h_pml, double* h_tvar, double* h_mean,
+                            int32_t flags, void* stream) {
   if (!pf || n_trials < 0 || !h_off) return ARA_EINVAL;
   std::vector<int32_t> sel;
   ara_status st = check_selection(*pf, n_sel, layer_sel, sel);
   if (st != ARA_OK) return st;
   if ((st = check_flags(*pf, flags)) != ARA_OK) return st;
   if (n_rp < 0 || n_tvar < 0) return ARA_EINVAL;
-  const bool metrics = n_rp + n_tvar > 0;
+  const bool metrics = n_rp + n_tvar > 0 || h_mean != nullptr;
   if (metrics && (sel.empty() || (n_rp > 0 && !h_pml) || (n_tvar > 0 && !h_tvar) ||
                   validate_metrics(n_trials, n_rp, rps, n_tvar, levels) != ARA_OK))
     return ARA_EINVAL;
@@ -515,7 +515,7 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
                             cudaMemcpyDeviceToHost, s));
   if (metrics) {
     if ((st = risk_metrics_device(pf->d_ylt_full, n_trials, (int32_t)sel.size(), n_rp, rps, n_tvar,
-                                  levels, h_pml, h_tvar, s)) != ARA_OK)
+                                  levels, h_pml, h_tvar, h_mean, s)) != ARA_OK)
       return st;
   }
   return ara_check(pf, stream);

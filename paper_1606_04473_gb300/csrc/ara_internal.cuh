@@ -120,6 +120,16 @@ struct YltArgs {
 
 ara_status launch_fold(Portfolio& pf, int32_t n_sel, const int32_t* sel_host, int32_t flags,
                        cudaStream_t s);
+// Fold into caller-chosen outputs (see k_fold): used by the adjoint for occurrence regimes.
+struct FoldOutHost {
+  uint64_t* q = nullptr;
+  uint32_t* bits = nullptr;
+  uint8_t* regime = nullptr;
+  int64_t q_stride = 0, bits_stride = 0, regime_stride = 0;
+  int by_slot = 0, f64_table = 0, bits_from_regime = 0;
+};
+ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
+                          const FoldOutHost& o, cudaStream_t s);
 ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s);
 ara_status build_dense(Portfolio& pf, cudaStream_t s);
 // Host check of risk-metric arguments (ranks within [1, n]); ARA_OK or ARA_EINVAL.
@@ -129,6 +139,6 @@ ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t 
 // stream-ordered allocator.
 ara_status risk_metrics_device(const double* d_ylt, int64_t n, int32_t n_layers, int32_t n_rp,
                                const double* rps, int32_t n_tvar, const double* levels,
-                               double* h_pml, double* h_tvar, cudaStream_t s);
+                               double* h_pml, double* h_tvar, double* h_mean, cudaStream_t s);
 
 }  // namespace ara

@@ -38,6 +38,9 @@ struct SelState {
 //   psum   [n_layers][n_t][blocks]                double
 //   pcnt   [n_layers][n_t][blocks]                int64
 //   out    [n_layers][n_t]                        double
+//   gt, eq [n_layers][n_t]                        int64: #{key > selected}, #{key == selected}
+//   pmean  [n_layers][blocks]                     double (block partial sums of the whole row)
+//   mean   [n_layers]                             double
 struct SelScratch {
   uint32_t* hist;
   uint32_t* ticket;
@@ -45,6 +48,10 @@ struct SelScratch {
   double* psum;
   int64_t* pcnt;
   double* out;
+  unsigned long long* gt;
+  unsigned long long* eq;
+  double* pmean;
+  double* mean;
 };
 
 size_t select_scratch_bytes(int32_t n_layers, int32_t n_t, int32_t blocks) {
@@ -56,6 +63,10 @@ size_t select_scratch_bytes(int32_t n_layers, int32_t n_t, int32_t blocks) {
   take(sizeof(double) * n_layers * n_t * blocks);
   take(sizeof(int64_t) * n_layers * n_t * blocks);
   take(sizeof(double) * n_layers * n_t);
+  take(sizeof(int64_t) * n_layers * n_t);
+  take(sizeof(int64_t) * n_layers * n_t);
+  take(sizeof(double) * n_layers * blocks);
+  take(sizeof(double) * n_layers);
   return (b + 255) / 256 * 256;
 }
 
@@ -75,6 +86,10 @@ static SelScratch carve(void* base, int32_t n_layers, int32_t n_t, int32_t block
   s.psum = (double*)take(sizeof(double) * n_layers * n_t * blocks);
   s.pcnt = (int64_t*)take(sizeof(int64_t) * n_layers * n_t * blocks);
   s.out = (double*)take(sizeof(double) * n_layers * n_t);
+  s.gt = (unsigned long long*)take(sizeof(int64_t) * n_layers * n_t);
+  s.eq = (unsigned long long*)take(sizeof(int64_t) * n_layers * n_t);
+  s.pmean = (double*)take(sizeof(double) * n_layers * blocks);
+  s.mean = (double*)take(sizeof(double) * n_layers);
   return s;
 }
 
@@ -153,12 +168,12 @@ k_select_pass(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScrat
   }
 }
 
-// Tail pass: for every target, the selected key; for TVaR targets the sum and count of the
-// values strictly above it.  The last block combines block partials in block order.
+// Tail pass: for every target, the selected key and the counts of keys above / equal to it;
+// for TVaR targets the sum of the values strictly above it; optionally the row sum (mean).
+// The last block combines block partials in block order (deterministic).
 __global__ void __launch_bounds__(SEL_THREADS)
-k_select_tail(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScratch sc) {
-  __shared__ double ssum[SEL_THREADS / 32][SEL_MAX_T];
-  __shared__ int64_t scnt[SEL_THREADS / 32][SEL_MAX_T];
+k_select_tail(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScratch sc, int want_mean) {
+  __shared__ double ssum[SEL_THREADS / 32][SEL_MAX_T + 1];
   __shared__ uint64_t thr[SEL_MAX_T];
   __shared__ bool last;
   const int layer = blockIdx.y, nt = tg.n_t;
@@ -166,29 +181,41 @@ k_select_tail(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScrat
   if (threadIdx.x < nt) thr[threadIdx.x] = sc.state[layer * nt + threadIdx.x].prefix;
   __syncthreads();
   const double* row = ylt + (int64_t)layer * n;
-  for (int t = tg.n_rp; t < nt; ++t) {
+  for (int t = 0; t <= nt; ++t) {
+    if (t == nt && !want_mean) break;
     double s = 0.0;
-    int64_t c = 0;
+    unsigned long long cg = 0, ce = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
       const double y = row[i];
-      if (key_of(y) > thr[t]) { s = __dadd_rn(s, y); ++c; }
+      if (t == nt) { s = __dadd_rn(s, y); continue; }
+      const uint64_t k = key_of(y);
+      if (k > thr[t]) { ++cg; if (t >= tg.n_rp) s = __dadd_rn(s, y); }
+      else if (k == thr[t]) ++ce;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
-      c += __shfl_down_sync(0xffffffffu, c, o);
+      cg += __shfl_down_sync(0xffffffffu, cg, o);
+      ce += __shfl_down_sync(0xffffffffu, ce, o);
     }
-    if (lane == 0) { ssum[warp][t] = s; scnt[warp][t] = c; }
+    if (lane == 0) {
+      ssum[warp][t] = s;
+      if (t < nt) {
+        if (cg) atomicAdd(&sc.gt[layer * nt + t], cg);
+        if (ce) atomicAdd(&sc.eq[layer * nt + t], ce);
+      }
+    }
   }
   __syncthreads();
-  if (threadIdx.x < nt && threadIdx.x >= tg.n_rp) {
-    double s = 0.0;
-    int64_t c = 0;
-    for (int w = 0; w < SEL_THREADS / 32; ++w) { s = __dadd_rn(s, ssum[w][threadIdx.x]); c += scnt[w][threadIdx.x]; }
-    const int64_t slot = ((int64_t)layer * nt + threadIdx.x) * gridDim.x + blockIdx.x;
-    sc.psum[slot] = s;
-    sc.pcnt[slot] = c;
+  if (threadIdx.x <= nt && (threadIdx.x >= tg.n_rp || threadIdx.x == nt)) {
+    const int t = threadIdx.x;
+    if (t < nt || want_mean) {
+      double s = 0.0;
+      for (int w = 0; w < SEL_THREADS / 32; ++w) s = __dadd_rn(s, ssum[w][t]);
+      if (t < nt) sc.psum[((int64_t)layer * nt + t) * gridDim.x + blockIdx.x] = s;
+      else sc.pmean[(int64_t)layer * gridDim.x + blockIdx.x] = s;
+    }
   }
   __threadfence();
   __syncthreads();
@@ -203,13 +230,17 @@ k_select_tail(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScrat
     double r = v;
     if (t >= tg.n_rp) {
       double s = 0.0;
-      int64_t c = 0;
       const int64_t base = ((int64_t)layer * nt + t) * gridDim.x;
-      for (unsigned b = 0; b < gridDim.x; ++b) { s = __dadd_rn(s, __ldcg(&sc.psum[base + b])); c += __ldcg(&sc.pcnt[base + b]); }
+      for (unsigned b = 0; b < gridDim.x; ++b) s = __dadd_rn(s, __ldcg(&sc.psum[base + b]));
       const int64_t m = tg.rank[t];
+      const int64_t c = (int64_t)__ldcg(&sc.gt[layer * nt + t]);
       r = (s + (double)(m - c) * v) / (double)m;
     }
     sc.out[layer * nt + t] = r;
+  } else if (threadIdx.x == nt && want_mean) {
+    double s = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s = __dadd_rn(s, __ldcg(&sc.pmean[(int64_t)layer * gridDim.x + b]));
+    sc.mean[layer] = s / (double)n;
   }
 }
 
@@ -222,8 +253,7 @@ static int64_t ceil_snap(double x) {
 
 ara_status select_targets(int64_t n, int32_t n_rp, const double* rps, int32_t n_tvar,
                           const double* levels, SelTargets& tg) {
-  if (n < 1 || n_rp < 0 || n_tvar < 0 || n_rp + n_tvar < 1 || n_rp + n_tvar > SEL_MAX_T)
-    return ARA_EINVAL;
+  if (n < 1 || n_rp < 0 || n_tvar < 0 || n_rp + n_tvar > SEL_MAX_T) return ARA_EINVAL;
   if ((n_rp > 0 && !rps) || (n_tvar > 0 && !levels)) return ARA_EINVAL;
   tg.n_t = n_rp + n_tvar;
   tg.n_rp = n_rp;
@@ -256,18 +286,19 @@ int32_t select_blocks(int64_t n, int n_sms, int32_t n_layers) {
 
 // Launch the whole selection into `scratch` (zero-filled here); results land in scratch.out.
 ara_status launch_select(const double* d_ylt, int64_t n, int32_t n_layers, const SelTargets& tg,
-                         void* scratch, size_t scratch_bytes, int32_t blocks, cudaStream_t s,
-                         double** d_out) {
+                         void* scratch, size_t scratch_bytes, int32_t blocks, int want_mean,
+                         cudaStream_t s, SelScratch* out) {
   SelScratch sc = carve(scratch, n_layers, tg.n_t, blocks);
   ARA_TRY(cudaMemsetAsync(scratch, 0, scratch_bytes, s));
   {
-    LaunchScope ls(ARA_K_SELECT, s, SEL_PASSES + 1);
+    LaunchScope ls(ARA_K_SELECT, s, tg.n_t > 0 ? SEL_PASSES + 1 : 1);
     dim3 grid(blocks, n_layers);
-    for (int p = 0; p < SEL_PASSES; ++p) k_select_pass<<<grid, SEL_THREADS, 0, s>>>(d_ylt, n, tg, sc, p);
-    k_select_tail<<<grid, SEL_THREADS, 0, s>>>(d_ylt, n, tg, sc);
+    if (tg.n_t > 0)
+      for (int p = 0; p < SEL_PASSES; ++p) k_select_pass<<<grid, SEL_THREADS, 0, s>>>(d_ylt, n, tg, sc, p);
+    k_select_tail<<<grid, SEL_THREADS, 0, s>>>(d_ylt, n, tg, sc, want_mean);
     ARA_TRY(cudaGetLastError());
   }
-  *d_out = sc.out;
+  *out = sc;
   return ARA_OK;
 }
 
@@ -280,13 +311,14 @@ namespace ara {
 ara_status risk_metrics_device(const double* d_ylt, int64_t n_trials, int32_t n_layers,
                                int32_t n_rp, const double* rps, int32_t n_tvar,
                                const double* levels, double* h_pml, double* h_tvar,
-                               cudaStream_t s) {
+                               double* h_mean, cudaStream_t s) {
   SelTargets tg;
   if (!d_ylt || n_layers < 1) return ARA_EINVAL;
   if ((n_rp > 0 && !h_pml) || (n_tvar > 0 && !h_tvar)) return ARA_EINVAL;
   if ((uintptr_t)d_ylt & 7) return ARA_EINVAL;
   ara_status st = select_targets(n_trials, n_rp, rps, n_tvar, levels, tg);
   if (st != ARA_OK) return st;
+  if (tg.n_t == 0 && !h_mean) return ARA_EINVAL;
   int dev = 0, sms = 0;
   ARA_TRY(cudaGetDevice(&dev));
   ARA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -294,12 +326,14 @@ ara_status risk_metrics_device(const double* d_ylt, int64_t n_trials, int32_t n_
   const size_t bytes = select_scratch_bytes(n_layers, tg.n_t, blocks);
   void* scratch = nullptr;
   ARA_TRY(cudaMallocAsync(&scratch, bytes, s));
-  double* d_out = nullptr;
-  st = launch_select(d_ylt, n_trials, n_layers, tg, scratch, bytes, blocks, s, &d_out);
+  SelScratch sc;
+  st = launch_select(d_ylt, n_trials, n_layers, tg, scratch, bytes, blocks, h_mean != nullptr, s, &sc);
   std::vector<double> out((size_t)n_layers * tg.n_t);
   if (st == ARA_OK) {
-    cudaError_t e = cudaMemcpyAsync(out.data(), d_out, sizeof(double) * out.size(),
+    cudaError_t e = cudaMemcpyAsync(out.data(), sc.out, sizeof(double) * out.size(),
                                     cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_mean)
+      e = cudaMemcpyAsync(h_mean, sc.mean, sizeof(double) * n_layers, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) st = ARA_ECUDA;
   }
   cudaFreeAsync(scratch, s);
@@ -317,7 +351,7 @@ ara_status risk_metrics_device(const double* d_ylt, int64_t n_trials, int32_t n_
 extern "C" ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, int32_t n_layers,
                                        int32_t n_rp, const double* rps, int32_t n_tvar,
                                        const double* levels, double* h_pml, double* h_tvar,
-                                       void* stream) {
+                                       double* h_mean, void* stream) {
   return risk_metrics_device(d_ylt, n_trials, n_layers, n_rp, rps, n_tvar, levels, h_pml, h_tvar,
-                             (cudaStream_t)stream);
+                             h_mean, (cudaStream_t)stream);
 }

@@ -50,22 +50,33 @@ __device__ __forceinline__ int64_t lower_bound_ids(const int32_t* __restrict__ i
 // point q(e) = round(o(e) * 2^frac_bits) (or the FP64 bits of o(e) when f64_table), and the
 // hit bitmap (bit e set iff the stored value is non-zero).
 // ------------------------------------------------------------------------------------------
+struct FoldOut {
+  uint64_t* q;          // table, or nullptr
+  uint32_t* bits;       // hit bitmap
+  uint8_t* regime;      // occurrence-clamp regime per event (0 / 1 / 2), or nullptr
+  int64_t q_stride, bits_stride, regime_stride;   // per output slot
+  int by_slot;          // outputs indexed by blockIdx.y (else by layer index)
+  int f64_table;        // store the FP64 bits of o(e) instead of fixed point
+  int bits_from_regime; // bitmap bit = (regime != 0) instead of (stored value != 0)
+};
+
 template <typename LossT>
 __global__ void __launch_bounds__(FOLD_THREADS)
 k_fold(int64_t catalogue, const int64_t* __restrict__ rec_off, const int32_t* __restrict__ rec_ids,
        const LossT* __restrict__ rec_loss, const double* __restrict__ elt_ret,
        const double* __restrict__ elt_lim, const int32_t* __restrict__ layer_elts,
-       const LayerConst* __restrict__ layers, SelList sel, uint64_t* __restrict__ q_out,
-       uint32_t* __restrict__ bits_out, int64_t bm_words, int f64_table) {
+       const LayerConst* __restrict__ layers, SelList sel, FoldOut out) {
   __shared__ double s[FOLD_TILE];
   __shared__ int32_t list[FOLD_TILE];
+  __shared__ uint8_t reg[FOLD_TILE];
   __shared__ int32_t n_list;
   __shared__ int64_t rng[2];
   const int layer = sel.idx[blockIdx.y];
+  const int64_t slot = out.by_slot ? blockIdx.y : layer;
   const LayerConst lc = layers[layer];
   const int64_t t0 = (int64_t)blockIdx.x * FOLD_TILE;
   const int64_t t1 = min(t0 + (int64_t)FOLD_TILE, catalogue);
-  for (int i = threadIdx.x; i < FOLD_TILE; i += blockDim.x) s[i] = 0.0;
+  for (int i = threadIdx.x; i < FOLD_TILE; i += blockDim.x) { s[i] = 0.0; reg[i] = 0; }
   if (threadIdx.x == 0) n_list = 0;
   for (int k = lc.elt_begin; k < lc.elt_end; ++k) {
     const int j = layer_elts[k];
@@ -89,20 +100,27 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ rec_off, const int32_t* __
   uint64_t* sq = reinterpret_cast<uint64_t*>(s);  // in place: untouched entries are +0.0 == 0
   for (int p = threadIdx.x; p < n_list; p += blockDim.x) {
     const int i = list[p];
-    const double o = clamp_terms(s[i], lc.occ_ret, lc.occ_lim);
-    sq[i] = f64_table ? (uint64_t)__double_as_longlong(o) : __double2ull_rn(__dmul_rn(o, lc.scale));
+    const double sv = s[i];
+    const double o = clamp_terms(sv, lc.occ_ret, lc.occ_lim);
+    const double ex = __dsub_rn(sv, lc.occ_ret);
+    reg[i] = (ex > 0.0 && ex < lc.occ_lim) ? 1 : (ex > lc.occ_lim ? 2 : 0);
+    sq[i] = out.f64_table ? (uint64_t)__double_as_longlong(o) : __double2ull_rn(__dmul_rn(o, lc.scale));
   }
   __syncthreads();
-  uint64_t* qo = q_out + (int64_t)layer * catalogue;
-  uint32_t* bo = bits_out + (int64_t)layer * bm_words;
+  uint64_t* qo = out.q ? out.q + slot * out.q_stride : nullptr;
+  uint32_t* bo = out.bits + slot * out.bits_stride;
+  uint8_t* ro = out.regime ? out.regime + slot * out.regime_stride : nullptr;
   for (int i = threadIdx.x; i < FOLD_TILE; i += blockDim.x) {  // FOLD_TILE % blockDim == 0
     const int64_t e = t0 + i;
-    const uint64_t q = e < t1 ? sq[i] : 0ull;
-    if (e < t1) qo[e] = q;
-    const unsigned b = __ballot_sync(FULL, q != 0ull);
+    const bool in = e < t1;
+    const uint64_t q = in ? sq[i] : 0ull;
+    const uint8_t r = in ? reg[i] : 0;
+    if (in && qo) qo[e] = q;
+    if (in && ro) ro[e] = r;
+    const unsigned b = __ballot_sync(FULL, out.bits_from_regime ? r != 0 : q != 0ull);
     if ((threadIdx.x & 31) == 0) {
       const int64_t w = (t0 + (i & ~31)) >> 5;
-      if (w < bm_words) bo[w] = b;
+      if (w < out.bits_stride) bo[w] = b;
     }
   }
 }
@@ -434,28 +452,52 @@ ara_status build_dense(Portfolio& pf, cudaStream_t s) {
   return ARA_OK;
 }
 
-ara_status launch_fold(Portfolio& pf, int32_t n_sel, const int32_t* sel_host, int32_t flags,
-                       cudaStream_t s) {
-  const int f64 = (flags & ARA_RUN_F64_SUM) ? 1 : 0;
+ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
+                          const FoldOutHost& o, cudaStream_t s) {
+  FoldOut out;
+  out.q = o.q;
+  out.bits = o.bits;
+  out.regime = o.regime;
+  out.q_stride = o.q_stride;
+  out.bits_stride = o.bits_stride;
+  out.regime_stride = o.regime_stride;
+  out.by_slot = o.by_slot;
+  out.f64_table = o.f64_table;
+  out.bits_from_regime = o.bits_from_regime;
   for (int32_t b = 0; b < n_sel; b += MAX_SEL) {
     SelList sl;
     sl.n = min(MAX_SEL, n_sel - b);
     for (int i = 0; i < sl.n; ++i) sl.idx[i] = sel_host[b + i];
+    FoldOut ob = out;
+    if (ob.by_slot) {  // slots continue across batches of MAX_SEL layers
+      if (ob.q) ob.q += (int64_t)b * ob.q_stride;
+      ob.bits += (int64_t)b * ob.bits_stride;
+      if (ob.regime) ob.regime += (int64_t)b * ob.regime_stride;
+    }
     dim3 grid((unsigned)((pf.catalogue + FOLD_TILE - 1) / FOLD_TILE), sl.n);
     LaunchScope ls(ARA_K_FOLD, s);
     if (pf.d_rec_loss32)
       k_fold<float><<<grid, FOLD_THREADS, 0, s>>>(pf.catalogue, pf.d_rec_off, pf.d_rec_ids,
                                                   pf.d_rec_loss32, pf.d_elt_ret, pf.d_elt_lim,
-                                                  pf.d_layer_elts, pf.d_layers, sl, pf.d_q,
-                                                  pf.d_bits, pf.bm_words, f64);
+                                                  pf.d_layer_elts, pf.d_layers, sl, ob);
     else
       k_fold<double><<<grid, FOLD_THREADS, 0, s>>>(pf.catalogue, pf.d_rec_off, pf.d_rec_ids,
                                                    pf.d_rec_loss, pf.d_elt_ret, pf.d_elt_lim,
-                                                   pf.d_layer_elts, pf.d_layers, sl, pf.d_q,
-                                                   pf.d_bits, pf.bm_words, f64);
+                                                   pf.d_layer_elts, pf.d_layers, sl, ob);
     ARA_TRY(cudaGetLastError());
   }
   return ARA_OK;
+}
+
+ara_status launch_fold(Portfolio& pf, int32_t n_sel, const int32_t* sel_host, int32_t flags,
+                       cudaStream_t s) {
+  FoldOutHost o{};
+  o.q = pf.d_q;
+  o.bits = pf.d_bits;
+  o.q_stride = pf.catalogue;
+  o.bits_stride = pf.bm_words;
+  o.f64_table = (flags & ARA_RUN_F64_SUM) ? 1 : 0;
+  return launch_fold_to(pf, n_sel, sel_host, o, s);
 }
 
 template <bool FILTER, typename Acc>

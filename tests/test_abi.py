@@ -100,7 +100,7 @@ def test_risk_metrics_rejects_invalid_levels(L):
         r = np.ascontiguousarray(rps, dtype=np.float64)
         v = np.ascontiguousarray(lv, dtype=np.float64)
         return L.ara_risk_metrics(p, n, 1, r.size, r.ctypes.data_as(ctypes.c_void_p), v.size,
-                                  v.ctypes.data_as(ctypes.c_void_p), po, po, None)
+                                  v.ctypes.data_as(ctypes.c_void_p), po, po, None, None)
     assert call(0, [10.0], []) == ara.ARA_EINVAL          # no trials
     assert call(100, [0.5], []) == ara.ARA_EINVAL         # return period < 1
     assert call(100, [], [1.0]) == ara.ARA_EINVAL         # level 1 -> empty tail

@@ -361,3 +361,16 @@ def test_tiny_workload_regimes_are_not_degenerate():
     above = np.mean(agg[0] >= pf.agg_ret[0] + pf.agg_lim[0])
     assert 0.0 < 1 - below - above
     assert np.mean(y[0] > 0) > 0.5
+
+
+def test_tvar_weights_share_the_boundary_among_ties():
+    """Symmetric tie rule: y = 10, 5, 5, 5, 0 and p = 0.6 give m = 2 and v = 5; the trial above
+    v gets 1/2 and the three tied trials share the remaining 1/2 (1/6 each); the weighted sum
+    is TVaR = (10 + 5) / 2 = 7.5."""
+    y = np.array([[10.0, 5.0, 5.0, 5.0, 0.0]])
+    w, ties = oracle.objective_weights(y, "tvar", 0.6)
+    assert w[0].tolist() == [0.5, 1 / 6, 1 / 6, 1 / 6, 0.0]
+    assert ties == [True]
+    assert float(w[0] @ y[0]) == pytest.approx(oracle.tvar(y[0], 0.6), rel=1e-15)
+    w, ties = oracle.objective_weights(np.array([[10.0, 5.0, 4.0]]), "tvar", 0.5)
+    assert w[0].tolist() == [0.5, 0.5, 0.0] and ties == [False]
