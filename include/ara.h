@@ -51,6 +51,7 @@ typedef int32_t ara_status;
 #define ARA_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
 #define ARA_EBUSY    (-5)   /* resource in use */
 #define ARA_EDATA    (-6)   /* device-side data check failed in an earlier asynchronous run */
+#define ARA_ERANGE   (-7)   /* request exceeds a fixed capacity of the library */
 
 typedef struct ara_portfolio ara_portfolio;
 
@@ -183,6 +184,31 @@ ARA_API ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, int32
                             int32_t n_rp, const double* return_periods, int32_t n_tvar,
                             const double* tvar_levels, double* h_pml, double* h_tvar,
                             double* h_mean, void* stream);
+
+/*
+ * ara_risk_metrics for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a deployment convenience.  Some callers may not call cudaMalloc or
+ * the stream-ordered allocator: a process whose device memory is already reserved in full by
+ * another allocator (a framework's caching pool, a serving process sized to the whole GPU),
+ * where any further allocation fails; or a latency-critical loop that cannot afford an
+ * allocation's latency or cudaFree's implicit device synchronisation.  This entry point
+ * allocates nothing: its scratch is one fixed array of ARA_STATIC_SELECT_BYTES bytes in
+ * device memory, defined in libara itself (every GPU that loads the library holds it until
+ * the process exits).  Arguments, results and errors are those of ara_risk_metrics, plus:
+ *   - a request whose scratch (about 8 KiB per layer per requested PML/TVaR level) does not
+ *     fit in the array returns ARA_ERANGE and launches nothing;
+ *   - the first call on each device looks up the array's device address on that device
+ *     (with it current); make that first call before any stream capture begins there;
+ *   - every call reuses the same array and clears the part it needs first; calls whose
+ *     work overlaps on a device (other streams, other host threads) race on it and must be
+ *     serialised by the caller.
+ */
+#define ARA_STATIC_SELECT_BYTES (4u << 20)
+ARA_API ara_status ara_risk_metrics_static(const double* d_ylt, int64_t n_trials,
+                                           int32_t n_layers, int32_t n_rp,
+                                           const double* return_periods, int32_t n_tvar,
+                                           const double* tvar_levels, double* h_pml,
+                                           double* h_tvar, double* h_mean, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Introspection for measurement.

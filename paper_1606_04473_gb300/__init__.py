@@ -23,6 +23,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libara.so")
 
 ARA_OK, ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA, ARA_ETIMEOUT, ARA_EBUSY, ARA_EDATA = 0, -1, -2, -3, -4, -5, -6
+ARA_ERANGE = -7
+ARA_STATIC_SELECT_BYTES = 4 << 20
 ARA_LOSSES_F32, ARA_DENSE_TABLES = 1, 2
 ARA_RUN_FOLDED, ARA_RUN_PER_ELT, ARA_RUN_NO_FILTER, ARA_RUN_F64_SUM = 0, 1, 2, 4
 ARA_K_FOLD, ARA_K_YLT, ARA_K_SELECT, ARA_K_ADJOINT = 0, 1, 2, 3
@@ -54,6 +56,7 @@ def lib() -> ctypes.CDLL:
     L.ara_run_ylt_host.argtypes = [P, i64, P, P, i32, P, P, i32, P, i32, P, P, P, P, i32, P]
     L.ara_check.argtypes = [P, P]
     L.ara_risk_metrics.argtypes = [P, i64, i32, i32, P, i32, P, P, P, P, P]
+    L.ara_risk_metrics_static.argtypes = [P, i64, i32, i32, P, i32, P, P, P, P, P]
     L.ara_launch_count.restype = i64
     L.ara_timing_enable.argtypes = [i32]
     L.ara_timing_enable.restype = None
@@ -62,7 +65,7 @@ def lib() -> ctypes.CDLL:
     L.ara_status_string.argtypes = [i32]
     L.ara_status_string.restype = ctypes.c_char_p
     for fn in ["ara_create_portfolio", "ara_run_ylt", "ara_run_ylt_host", "ara_check",
-               "ara_risk_metrics", "ara_timing_read"]:
+               "ara_risk_metrics", "ara_risk_metrics_static", "ara_timing_read"]:
         getattr(L, fn).restype = i32
     _lib = L
     return L
@@ -225,6 +228,27 @@ def risk_metrics(ylt, return_periods: Sequence[float] = (), tvar_levels: Sequenc
                                 lv.size, _np_ptr(lv), _np_ptr(pml), _np_ptr(tvar), _np_ptr(mean),
                                 _stream_handle(stream))
     _check(st, "ara_risk_metrics")
+    return (pml, tvar, mean) if want_mean else (pml, tvar)
+
+
+def risk_metrics_static(ylt, return_periods: Sequence[float] = (), tvar_levels: Sequence[float] = (),
+                        stream=None, want_mean: bool = False):
+    """risk_metrics() without any device allocation (ara_risk_metrics_static), for callers whose
+    device memory is owned by another allocator or who cannot pay for an allocation: scratch
+    comes from a fixed array inside libara.  Raises AraError(ARA_ERANGE) when the request does
+    not fit that array; concurrent calls on one device must be serialised by the caller."""
+    import torch
+    ylt2 = ylt if ylt.dim() == 2 else ylt.reshape(1, -1)
+    nl, n = ylt2.shape
+    rp = np.ascontiguousarray(return_periods, dtype=np.float64)
+    lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
+    pml = np.zeros((nl, rp.size))
+    tvar = np.zeros((nl, lv.size))
+    mean = np.zeros(nl) if want_mean else None
+    st = lib().ara_risk_metrics_static(_dev_ptr(ylt2, torch.float64, "ylt"), n, nl, rp.size,
+                                       _np_ptr(rp), lv.size, _np_ptr(lv), _np_ptr(pml),
+                                       _np_ptr(tvar), _np_ptr(mean), _stream_handle(stream))
+    _check(st, "ara_risk_metrics_static")
     return (pml, tvar, mean) if want_mean else (pml, tvar)
 
 

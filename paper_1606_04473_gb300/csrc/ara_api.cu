@@ -174,6 +174,7 @@ const char* ara_status_string(ara_status s) {
     case ARA_ETIMEOUT: return "device wait timed out";
     case ARA_EBUSY: return "busy";
     case ARA_EDATA: return "device-side data check failed";
+    case ARA_ERANGE: return "request exceeds a fixed capacity";
     default: return "unknown status";
   }
 }

@@ -8,6 +8,7 @@
 // FP64 sum (TVaR).
 
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "ara_internal.cuh"
@@ -354,4 +355,74 @@ extern "C" ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, in
                                        double* h_mean, void* stream) {
   return risk_metrics_device(d_ylt, n_trials, n_layers, n_rp, rps, n_tvar, levels, h_pml, h_tvar,
                              h_mean, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant: the selection scratch lives in a fixed device array of this
+// library.  Host code cannot use the array's name as a device address, so its address is
+// looked up once per device (with that device current) and cached.
+// ------------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_select_scratch[ARA_STATIC_SELECT_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_scratch[kMaxDevices];
+}  // namespace
+
+static ara_status static_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return ARA_ECUDA;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_scratch[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_select_scratch);
+    if (e != cudaSuccess || !p) {
+      note_cuda_error(e, "cudaGetSymbolAddress(g_select_scratch)", __FILE__, __LINE__);
+      return ARA_ECUDA;
+    }
+    g_static_scratch[dev] = p;
+  }
+  *out = g_static_scratch[dev];
+  return ARA_OK;
+}
+
+extern "C" ara_status ara_risk_metrics_static(const double* d_ylt, int64_t n_trials,
+                                              int32_t n_layers, int32_t n_rp, const double* rps,
+                                              int32_t n_tvar, const double* levels, double* h_pml,
+                                              double* h_tvar, double* h_mean, void* stream) {
+  SelTargets tg;
+  if (!d_ylt || n_layers < 1) return ARA_EINVAL;
+  if ((n_rp > 0 && !h_pml) || (n_tvar > 0 && !h_tvar)) return ARA_EINVAL;
+  if ((uintptr_t)d_ylt & 7) return ARA_EINVAL;
+  ara_status st = select_targets(n_trials, n_rp, rps, n_tvar, levels, tg);
+  if (st != ARA_OK) return st;
+  if (tg.n_t == 0 && !h_mean) return ARA_EINVAL;
+  int dev = 0, sms = 0;
+  ARA_TRY(cudaGetDevice(&dev));
+  ARA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // Fewer blocks shrink the per-block partials; if even one block does not fit, refuse.
+  int32_t blocks = select_blocks(n_trials, sms, n_layers);
+  while (blocks > 1 && select_scratch_bytes(n_layers, tg.n_t, blocks) > ARA_STATIC_SELECT_BYTES)
+    blocks = blocks / 2;
+  const size_t bytes = select_scratch_bytes(n_layers, tg.n_t, blocks);
+  if (bytes > ARA_STATIC_SELECT_BYTES) return ARA_ERANGE;
+  void* scratch = nullptr;
+  if ((st = static_scratch(dev, &scratch)) != ARA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  SelScratch sc;
+  // launch_select clears the used part of the scratch before its first kernel
+  if ((st = launch_select(d_ylt, n_trials, n_layers, tg, scratch, bytes, blocks, h_mean != nullptr,
+                          s, &sc)) != ARA_OK)
+    return st;
+  const size_t row = sizeof(double) * (size_t)tg.n_t;
+  if (n_rp > 0)
+    ARA_TRY(cudaMemcpy2DAsync(h_pml, sizeof(double) * n_rp, sc.out, row, sizeof(double) * n_rp,
+                              (size_t)n_layers, cudaMemcpyDeviceToHost, s));
+  if (n_tvar > 0)
+    ARA_TRY(cudaMemcpy2DAsync(h_tvar, sizeof(double) * n_tvar, sc.out + n_rp, row,
+                              sizeof(double) * n_tvar, (size_t)n_layers, cudaMemcpyDeviceToHost, s));
+  if (h_mean)
+    ARA_TRY(cudaMemcpyAsync(h_mean, sc.mean, sizeof(double) * n_layers, cudaMemcpyDeviceToHost, s));
+  ARA_TRY(cudaStreamSynchronize(s));
+  return ARA_OK;
 }

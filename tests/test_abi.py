@@ -38,7 +38,7 @@ def test_every_declared_function_is_exported(L):
 
 
 def test_status_strings(L):
-    for s in [0, -1, -2, -3, -4, -5, -6]:
+    for s in [0, -1, -2, -3, -4, -5, -6, -7]:
         assert ara.status_string(s) not in ("", "unknown status")
 
 
