@@ -111,6 +111,8 @@ ARA_API void ara_destroy_portfolio(ara_portfolio* pf);
 #define ARA_RUN_NO_FILTER 2   /* folded, without the shared-memory hit filter (measurement) */
 #define ARA_RUN_F64_SUM   4   /* folded, trial sums in FP64 instead of exact fixed point
                                  (measurement) */
+#define ARA_RUN_LDG       8   /* folded, YET read by per-trial 16-byte register loads instead of
+                                 the per-warp TMA bulk-copy ring (measurement) */
 
 /*
  * YLT of n_trials trials for the selected layers.  Asynchronous on `stream`.
@@ -157,8 +159,9 @@ ARA_API ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials,
                                     const double* tvar_levels, double* h_pml, double* h_tvar,
                                     double* h_mean, int32_t flags, void* stream);
 
-/* Synchronise `stream`, then report (and clear) device-side data errors recorded by earlier
- * asynchronous runs of this portfolio: ARA_OK or ARA_EDATA. */
+/* Synchronise `stream`, then report (and clear) device-side errors recorded by earlier
+ * asynchronous runs of this portfolio: ARA_OK, ARA_EDATA (bad event ID or offsets; the YLT of
+ * that run is unspecified) or ARA_ETIMEOUT (a bounded wait for a bulk copy gave up). */
 ARA_API ara_status ara_check(ara_portfolio* pf, void* stream);
 
 /* ---------------------------------------------------------------------------------------
@@ -216,6 +219,26 @@ ARA_API ara_status ara_risk_metrics_static(const double* d_ylt, int64_t n_trials
 
 /* Kernels launched by this library in this process so far. */
 ARA_API int64_t ara_launch_count(void);
+
+/* Launch shapes of the YET-stream kernel (tuning).  ara_stream_shapes writes up to `max`
+ * (warps per block, staging-ring stages) pairs into the host arrays and returns how many shapes
+ * are compiled in; ara_set_stream_shape selects one for every later run in this process
+ * (ARA_EINVAL for an unknown index).  Results do not depend on the shape. */
+ARA_API int32_t ara_stream_shapes(int32_t* warps, int32_t* stages, int32_t max);
+ARA_API ara_status ara_set_stream_shape(int32_t index);
+
+/* Failure-detection hooks (process-wide; for tests).
+ *   ARA_DBG_WAIT_LIMIT_NS  bound of every device-side wait for a bulk copy, in ns
+ *                          (default 1e9; >= 1000).  A wait that runs out makes the kernel
+ *                          record a timeout, wait (bounded) for its own copies in flight and
+ *                          return; ara_check then reports ARA_ETIMEOUT.
+ *   ARA_DBG_STARVE_COPIES  announce this many bytes more than each bulk copy delivers (a
+ *                          multiple of 16, <= 4096; 0 = normal): every wait then runs out,
+ *                          which exercises the timeout path without any fault.
+ * ARA_EINVAL for an unknown key or value. */
+#define ARA_DBG_WAIT_LIMIT_NS  1
+#define ARA_DBG_STARVE_COPIES  2
+ARA_API ara_status ara_debug_set(int32_t key, int64_t value);
 
 /* kernel classes for timing */
 #define ARA_K_FOLD    0   /* per-layer fold of per-ELT and occurrence terms */

@@ -26,7 +26,7 @@ ARA_OK, ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA, ARA_ETIMEOUT, ARA_EBUSY, ARA_EDATA = 
 ARA_ERANGE = -7
 ARA_STATIC_SELECT_BYTES = 4 << 20
 ARA_LOSSES_F32, ARA_DENSE_TABLES = 1, 2
-ARA_RUN_FOLDED, ARA_RUN_PER_ELT, ARA_RUN_NO_FILTER, ARA_RUN_F64_SUM = 0, 1, 2, 4
+ARA_RUN_FOLDED, ARA_RUN_PER_ELT, ARA_RUN_NO_FILTER, ARA_RUN_F64_SUM, ARA_RUN_LDG = 0, 1, 2, 4, 8
 ARA_K_FOLD, ARA_K_YLT, ARA_K_SELECT, ARA_K_ADJOINT = 0, 1, 2, 3
 
 _lib = None
@@ -58,6 +58,12 @@ def lib() -> ctypes.CDLL:
     L.ara_risk_metrics.argtypes = [P, i64, i32, i32, P, i32, P, P, P, P, P]
     L.ara_risk_metrics_static.argtypes = [P, i64, i32, i32, P, i32, P, P, P, P, P]
     L.ara_launch_count.restype = i64
+    L.ara_stream_shapes.argtypes = [P, P, i32]
+    L.ara_stream_shapes.restype = i32
+    L.ara_set_stream_shape.argtypes = [i32]
+    L.ara_set_stream_shape.restype = i32
+    L.ara_debug_set.argtypes = [i32, i64]
+    L.ara_debug_set.restype = i32
     L.ara_timing_enable.argtypes = [i32]
     L.ara_timing_enable.restype = None
     L.ara_timing_reset.restype = None
@@ -254,6 +260,26 @@ def risk_metrics_static(ylt, return_periods: Sequence[float] = (), tvar_levels: 
 
 def launch_count() -> int:
     return int(lib().ara_launch_count())
+
+
+def stream_shapes():
+    """Compiled (warps per block, ring stages) shapes of the YET-stream kernel."""
+    w = np.zeros(64, dtype=np.int32)
+    st = np.zeros(64, dtype=np.int32)
+    n = lib().ara_stream_shapes(_np_ptr(w), _np_ptr(st), 64)
+    return [(int(w[i]), int(st[i])) for i in range(n)]
+
+
+def set_stream_shape(index: int):
+    _check(lib().ara_set_stream_shape(int(index)), "ara_set_stream_shape")
+
+
+ARA_DBG_WAIT_LIMIT_NS, ARA_DBG_STARVE_COPIES = 1, 2
+
+
+def debug_set(key: int, value: int):
+    """Failure-detection hooks for tests (see ara_debug_set in include/ara.h)."""
+    _check(lib().ara_debug_set(int(key), int(value)), "ara_debug_set")
 
 
 def timing_enable(on: bool = True):

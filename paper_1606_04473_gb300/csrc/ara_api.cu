@@ -181,6 +181,33 @@ const char* ara_status_string(ara_status s) {
 
 int64_t ara_launch_count(void) { return g_launches.load(); }
 
+int32_t ara_stream_shapes(int32_t* warps, int32_t* stages, int32_t max) {
+  const int32_t n = n_bulk_shapes();
+  for (int32_t i = 0; i < n && i < max; ++i) bulk_shape(i, warps + i, stages + i);
+  return n;
+}
+
+ara_status ara_debug_set(int32_t key, int64_t value) {
+  switch (key) {
+    case ARA_DBG_WAIT_LIMIT_NS:
+      if (value < 1000) return ARA_EINVAL;
+      set_wait_limit_ns((uint64_t)value);
+      return ARA_OK;
+    case ARA_DBG_STARVE_COPIES:
+      if (value < 0 || value > 4096 || (value & 15)) return ARA_EINVAL;
+      set_debug_extra_tx((uint32_t)value);
+      return ARA_OK;
+    default:
+      return ARA_EINVAL;
+  }
+}
+
+ara_status ara_set_stream_shape(int32_t index) {
+  if (index < 0 || index >= n_bulk_shapes()) return ARA_EINVAL;
+  set_bulk_shape(index);
+  return ARA_OK;
+}
+
 void ara_timing_enable(int32_t on) {
   std::lock_guard<std::mutex> lk(g_tmu);
   g_timing = on != 0;
@@ -274,6 +301,9 @@ ara_status ara_create_portfolio(int64_t C, int32_t n_elts, const int64_t* rec_of
   if (cudaGetDevice(&p->device) != cudaSuccess) return fail(ARA_ECUDA);
   if (cudaDeviceGetAttribute(&p->n_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
     return fail(ARA_ECUDA);
+  if (cudaDeviceGetAttribute(&p->max_smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                             p->device) != cudaSuccess)
+    return fail(ARA_ECUDA);
   p->catalogue = C;
   p->n_elts = n_elts;
   p->n_layers = n_layers;
@@ -356,8 +386,9 @@ static ara_status check_selection(const Portfolio& pf, int32_t n_sel, const int3
 }
 
 static ara_status check_flags(const Portfolio& pf, int32_t flags) {
-  if (flags & ~(ARA_RUN_PER_ELT | ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM)) return ARA_EINVAL;
-  if ((flags & ARA_RUN_PER_ELT) && (flags & (ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM))) return ARA_EINVAL;
+  if (flags & ~(ARA_RUN_PER_ELT | ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG)) return ARA_EINVAL;
+  if ((flags & ARA_RUN_PER_ELT) && (flags & (ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG)))
+    return ARA_EINVAL;
   if ((flags & ARA_RUN_PER_ELT) && !pf.d_dense) return ARA_EINVAL;
   return ARA_OK;
 }
@@ -403,7 +434,7 @@ ara_status ara_check(ara_portfolio* pf, void* stream) {
   ARA_TRY(cudaMemcpy(&err, pf->d_err, sizeof(err), cudaMemcpyDeviceToHost));
   if (err) {
     ARA_TRY(cudaMemset(pf->d_err, 0, sizeof(uint32_t)));
-    return ARA_EDATA;
+    return (err & DERR_TIMEOUT) ? ARA_ETIMEOUT : ARA_EDATA;
   }
   return ARA_OK;
 }

@@ -26,7 +26,7 @@ namespace ara {
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
 // Device-side data error bits (atomicOr into the portfolio's error word).
-enum : uint32_t { DERR_EVENT_RANGE = 1u, DERR_OFFSETS = 2u };
+enum : uint32_t { DERR_EVENT_RANGE = 1u, DERR_OFFSETS = 2u, DERR_TIMEOUT = 4u };
 
 // ------------------------------------------------------------------------------------------
 // Launch accounting and per-class event timing
@@ -68,6 +68,7 @@ struct LayerConst {
 struct Portfolio {
   int device = 0;
   int n_sms = 0;
+  int max_smem_block = 0;           // opt-in shared memory per block (bytes)
   int64_t catalogue = 0;
   int32_t n_elts = 0, n_layers = 0, flags = 0;
   int64_t n_records = 0;
@@ -132,6 +133,12 @@ ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
                           const FoldOutHost& o, cudaStream_t s);
 ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s);
 ara_status build_dense(Portfolio& pf, cudaStream_t s);
+// Compiled shapes (warps per block, ring stages) of the bulk-staged YET stream kernel.
+int32_t n_bulk_shapes();
+void set_bulk_shape(int32_t i);
+void bulk_shape(int32_t i, int32_t* warps, int32_t* stages);
+void set_wait_limit_ns(uint64_t ns);
+void set_debug_extra_tx(uint32_t bytes);
 // Host check of risk-metric arguments (ranks within [1, n]); ARA_OK or ARA_EINVAL.
 ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t n_tvar,
                             const double* levels);

@@ -8,6 +8,7 @@
 // (k_fold), then streams the YET with one table gather per occurrence whose o(e) is non-zero
 // (k_ylt_folded).  k_ylt_per_elt keeps the literal per-occurrence, per-ELT lookups.
 
+#include <atomic>
 #include <cstdio>
 
 #include "ara_internal.cuh"
@@ -234,6 +235,8 @@ struct StreamParams {
   double* ylt;             // this layer's YLT row
   uint8_t* regimes;        // this layer's regime row or nullptr
   uint32_t* err;
+  uint64_t wait_limit_ns;  // bound of every mbarrier wait
+  uint32_t debug_extra_tx; // test hook: bytes announced but never copied (0 in normal use)
 };
 
 // One event ID: range check, hit filter, gather, accumulate.
@@ -327,6 +330,260 @@ __global__ void __launch_bounds__(YLT_THREADS, 1) k_ylt_folded(StreamParams p) {
   }
   if (bad_id) atomicOr(p.err, DERR_EVENT_RANGE);
   if (bad_off) atomicOr(p.err, DERR_OFFSETS);
+}
+
+// ------------------------------------------------------------------------------------------
+// Bulk-staged YET stream (the default).  Warp w of the grid owns the contiguous trials
+// [w N / W, (w+1) N / W) and therefore one contiguous range of event IDs.  It streams that range
+// through its own ring of BK_STAGES shared-memory stages of BK_CHUNK_IDS IDs, each filled by one
+// cp.async.bulk (TMA bulk copy, L2 evict-first) that completes on the stage's mbarrier; lane 0
+// refills a stage as soon as the warp has read it, so BK_STAGES - 1 chunks are in flight while
+// one is processed, across trial boundaries.  The unaligned head and tail of the range (< 4 IDs
+// each) use plain loads.  Positions are attributed to trials by a segmented walk over the
+// trial offsets (prefetched 32 at a time), with the per-lane partial sums reduced at each trial
+// end; lane k of a group collects trial k's sum and the aggregate terms of 32 trials run at once.
+// Every mbarrier wait is bounded: on timeout the warp records DERR_TIMEOUT, waits (bounded) for
+// its own copies still in flight, and returns.
+// ------------------------------------------------------------------------------------------
+constexpr int BK_CHUNK_IDS = 256;                      // 1 KiB per stage
+constexpr int BK_STEPS = BK_CHUNK_IDS / 32;
+
+template <int WARPS, int STAGES> struct BulkShape {
+  static constexpr int ring_bytes = WARPS * STAGES * BK_CHUNK_IDS * 4;
+  static constexpr int bar_bytes = WARPS * STAGES * 8;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                         uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)),
+      "l"(pol) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for a phase of an mbarrier for at most limit_ns nanoseconds; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// Warp-uniform cursor over the trials of one warp.
+template <typename Acc>
+struct TrialCursor {
+  int64_t t, t_hi, group_base;
+  int64_t end;          // event position (relative) where trial t ends
+  int64_t E0, E1;
+  int64_t next_off;     // lane i holds offset of trial (buf_base + i) end, i.e. offsets[buf_base+1+i]
+  int64_t buf_base;     // trial index whose end is in lane 0 of next_off
+  Acc acc, res;
+  bool bad;
+};
+
+template <bool FILTER, typename Acc, int BK_WARPS, int BK_STAGES>
+__global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int64_t bm_bytes = FILTER ? ((p.smem_words * 4 + 127) / 128) * 128 : 0;
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* ring = reinterpret_cast<int32_t*>(smem_raw + bm_bytes) + wid * BK_STAGES * BK_CHUNK_IDS;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + bm_bytes +
+                                               BulkShape<BK_WARPS, BK_STAGES>::ring_bytes) +
+                   wid * BK_STAGES;
+  if (lane == 0)
+    for (int s = 0; s < BK_STAGES; ++s) mbar_init(&bars[s], 1);
+  if (FILTER)
+    for (int64_t cw = threadIdx.x; cw < p.smem_words; cw += blockDim.x)
+      bm[cw] = coarsen_word(p.bits, cw, p.shift, p.bm_words);
+  if (lane == 0) fence_mbar_init();
+  __syncthreads();
+
+  const int64_t W = (int64_t)gridDim.x * BK_WARPS;
+  const int64_t gw = (int64_t)blockIdx.x * BK_WARPS + wid;
+  const int64_t t_lo = gw * p.n_trials / W, t_hi = (gw + 1) * p.n_trials / W;
+  if (t_lo >= t_hi) return;
+  const LayerConst lc = *p.layer;
+  const uint64_t* __restrict__ q = p.q;
+  bool bad_id = false;
+
+  TrialCursor<Acc> c;
+  c.t = t_lo;
+  c.t_hi = t_hi;
+  c.group_base = t_lo;
+  c.E0 = __ldg(p.offsets + t_lo) - p.id_base;
+  c.E1 = __ldg(p.offsets + t_hi) - p.id_base;
+  c.acc = AccOps<Acc>::zero();
+  c.res = AccOps<Acc>::zero();
+  c.bad = !(0 <= c.E0 && c.E0 <= c.E1 && c.E1 <= p.n_events);
+  if (c.bad) {
+    if (lane == 0) atomicOr(p.err, DERR_OFFSETS);
+    return;
+  }
+  c.buf_base = t_lo;
+  c.next_off = (t_lo + 1 + lane <= t_hi) ? __ldg(p.offsets + t_lo + 1 + lane) - p.id_base : c.E1;
+  c.end = __shfl_sync(FULL, c.next_off, 0);
+  if (c.end < c.E0 || c.end > c.E1) {
+    c.bad = true;
+    c.end = c.E1;
+  }
+
+  // Finish the current trial: reduce, park in its slot, flush a full group, move on.
+  auto advance = [&]() {
+    const Acc r = AccOps<Acc>::warp_sum(c.acc);
+    if (lane == (int)(c.t - c.group_base)) c.res = r;
+    c.acc = AccOps<Acc>::zero();
+    const int64_t prev_end = c.end;
+    ++c.t;
+    if (c.t - c.group_base == 32 || c.t == c.t_hi) {
+      if (c.group_base + lane < c.t) {
+        uint8_t reg;
+        const double y = AccOps<Acc>::finish(c.res, lc, reg);
+        p.ylt[c.group_base + lane] = y;
+        if (p.regimes) p.regimes[c.group_base + lane] = reg;
+      }
+      c.res = AccOps<Acc>::zero();
+      c.group_base = c.t;
+    }
+    if (c.t < c.t_hi) {
+      if (c.t - c.buf_base == 32) {
+        c.buf_base = c.t;
+        c.next_off = (c.t + 1 + lane <= c.t_hi) ? __ldg(p.offsets + c.t + 1 + lane) - p.id_base : c.E1;
+      }
+      c.end = __shfl_sync(FULL, c.next_off, (int)(c.t - c.buf_base));
+      if (c.end < prev_end || c.end > c.E1) {  // offsets not monotone inside [E0, E1]
+        c.bad = true;
+        c.end = c.E1;
+      }
+    }
+  };
+  // Attribute the values of positions [pos0, pos0 + cnt) (lane = position - pos0, cnt <= 32)
+  // to trials.
+  auto attribute = [&](int64_t pos0, int64_t cnt, uint64_t v) {
+    int64_t done = pos0;
+    const int64_t stop = pos0 + cnt;
+    while (true) {
+      while (c.t < c.t_hi && c.end <= done) advance();
+      if (c.t >= c.t_hi) return;
+      const int64_t seg = min(c.end, stop);
+      const int64_t mypos = pos0 + lane;
+      if (mypos >= done && mypos < seg && v) AccOps<Acc>::add(c.acc, v);
+      done = seg;
+      if (done >= stop) return;
+    }
+  };
+  auto value_of_id = [&](int e, bool valid) -> uint64_t {
+    if (!valid) return 0ull;
+    if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; return 0ull; }
+    if (FILTER) {
+      const uint32_t b = (uint32_t)e >> p.shift;
+      if (!((bm[b >> 5] >> (b & 31)) & 1u)) return 0ull;
+    }
+    return __ldg(q + e);
+  };
+
+  // Frame positions: element i lives at frame position i + mis; 16-byte aligned vectors are
+  // frame positions [4v, 4v + 4).
+  const int64_t fa = c.E0 + p.mis, fb = c.E1 + p.mis;
+  int64_t body0 = ((fa + 3) >> 2) << 2, body1 = (fb >> 2) << 2;  // frame
+  if (body0 > body1) body0 = body1 = fb;                            // no aligned body
+  const int64_t head_end = body0 - p.mis;                           // element index
+  const int64_t tail_begin = body1 - p.mis;
+  // head: elements [E0, head_end) (< 4 when a body exists, else the whole range, < 8)
+  if (head_end > c.E0) {
+    const int64_t pos = c.E0 + lane;
+    const bool valid = pos < head_end;
+    const int e = valid ? __ldg(p.ids + pos) : 0;
+    attribute(c.E0, head_end - c.E0, value_of_id(e, valid));
+  }
+  // body: frame [body0, body1) in chunks of BK_CHUNK_IDS
+  const int64_t n_body = body1 - body0;
+  const int64_t n_chunks = (n_body + BK_CHUNK_IDS - 1) / BK_CHUNK_IDS;
+  const int32_t* gbase = p.ids + (body0 - p.mis);                   // 16-byte aligned
+  const uint64_t pol = l2_evict_first_policy();
+  auto issue = [&](int64_t ch) {
+    const int s = (int)(ch % BK_STAGES);
+    const int64_t n = min((int64_t)BK_CHUNK_IDS, n_body - ch * BK_CHUNK_IDS);
+    const uint32_t bytes = (uint32_t)(n * 4);
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bars[s], bytes + p.debug_extra_tx);
+    bulk_g2s(ring + s * BK_CHUNK_IDS, gbase + ch * BK_CHUNK_IDS, bytes, &bars[s], pol);
+  };
+  if (lane == 0)
+    for (int64_t ch = 0; ch < min((int64_t)BK_STAGES, n_chunks); ++ch) issue(ch);
+  __syncwarp();
+  int64_t timed_out_at = -1;
+  for (int64_t ch = 0; ch < n_chunks; ++ch) {
+    const int s = (int)(ch % BK_STAGES);
+    const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((ch / BK_STAGES) & 1), p.wait_limit_ns);
+    if (__any_sync(FULL, !ok)) { timed_out_at = ch; break; }
+    const int64_t base = head_end + ch * BK_CHUNK_IDS;              // element index of slot 0
+    const int64_t n = min((int64_t)BK_CHUNK_IDS, n_body - ch * BK_CHUNK_IDS);
+    int ids[BK_STEPS];
+#pragma unroll
+    for (int k = 0; k < BK_STEPS; ++k) ids[k] = ring[s * BK_CHUNK_IDS + k * 32 + lane];
+    __syncwarp();
+    if (lane == 0 && ch + BK_STAGES < n_chunks) issue(ch + BK_STAGES);
+    uint64_t v[BK_STEPS];
+#pragma unroll
+    for (int k = 0; k < BK_STEPS; ++k) v[k] = value_of_id(ids[k], k * 32 + lane < n);
+#pragma unroll
+    for (int k = 0; k < BK_STEPS; ++k)
+      if (k * 32 < n) attribute(base + k * 32, min((int64_t)32, n - k * 32), v[k]);
+  }
+  if (timed_out_at >= 0) {
+    // Chunks timed_out_at .. timed_out_at + BK_STAGES - 1 may still be in flight: wait for
+    // them (bounded) before leaving, then give up on the range.
+    for (int64_t ch = timed_out_at; ch < min(timed_out_at + BK_STAGES, n_chunks); ++ch)
+      mbar_wait_bounded(&bars[ch % BK_STAGES], (uint32_t)((ch / BK_STAGES) & 1), p.wait_limit_ns);
+    if (lane == 0) atomicOr(p.err, DERR_TIMEOUT);
+    return;
+  }
+  // tail: elements [tail_begin, E1)
+  if (tail_begin < c.E1) {
+    const int64_t pos = tail_begin + lane;
+    const bool valid = pos < c.E1;
+    const int e = valid ? __ldg(p.ids + pos) : 0;
+    attribute(tail_begin, c.E1 - tail_begin, value_of_id(e, valid));
+  }
+  // finish the remaining trials (the last one, and trailing empty ones)
+  while (c.t < c.t_hi) advance();
+  if (bad_id) atomicOr(p.err, DERR_EVENT_RANGE);
+  if (lane == 0 && c.bad) atomicOr(p.err, DERR_OFFSETS);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -515,8 +772,57 @@ static ara_status launch_folded_one(Portfolio& pf, StreamParams& sp, cudaStream_
   return ARA_OK;
 }
 
+// Compiled shapes of the bulk kernel (warps per block, ring stages); the active one is chosen
+// with ara_set_stream_shape (default: the first).
+static const int kBulkShapes[][2] = {{32, 3}, {24, 4}, {16, 6}, {16, 4}, {32, 2}};
+static std::atomic<int> g_bulk_shape{0};
+static std::atomic<uint64_t> g_wait_limit_ns{1000000000ull};
+static std::atomic<uint32_t> g_debug_extra_tx{0};
+
+void set_wait_limit_ns(uint64_t ns) { g_wait_limit_ns.store(ns); }
+void set_debug_extra_tx(uint32_t b) { g_debug_extra_tx.store(b); }
+
+template <bool FILTER, typename Acc, int WARPS, int STAGES>
+static ara_status launch_bulk_shape(Portfolio& pf, StreamParams& sp, cudaStream_t s) {
+  const auto fn = k_ylt_bulk<FILTER, Acc, WARPS, STAGES>;
+  const int64_t bm_bytes = FILTER ? ((sp.smem_words * 4 + 127) / 128) * 128 : 0;
+  const int smem = (int)(bm_bytes + BulkShape<WARPS, STAGES>::ring_bytes + BulkShape<WARPS, STAGES>::bar_bytes);
+  ara_status st = set_smem((const void*)fn, smem);
+  if (st != ARA_OK) return st;
+  LaunchScope ls(ARA_K_YLT, s);
+  fn<<<pf.n_sms, WARPS * 32, smem, s>>>(sp);
+  ARA_TRY(cudaGetLastError());
+  return ARA_OK;
+}
+
+template <bool FILTER, typename Acc>
+static ara_status launch_bulk_one(Portfolio& pf, StreamParams& sp, cudaStream_t s) {
+  switch (g_bulk_shape.load()) {
+    case 1: return launch_bulk_shape<FILTER, Acc, 24, 4>(pf, sp, s);
+    case 2: return launch_bulk_shape<FILTER, Acc, 16, 6>(pf, sp, s);
+    case 3: return launch_bulk_shape<FILTER, Acc, 16, 4>(pf, sp, s);
+    case 4: return launch_bulk_shape<FILTER, Acc, 32, 2>(pf, sp, s);
+    default: return launch_bulk_shape<FILTER, Acc, 32, 3>(pf, sp, s);
+  }
+}
+
+static int bulk_ring_bytes() {
+  const int* sh = kBulkShapes[g_bulk_shape.load()];
+  return sh[0] * sh[1] * (BK_CHUNK_IDS * 4 + 8);
+}
+
+int32_t n_bulk_shapes() { return (int32_t)(sizeof(kBulkShapes) / sizeof(kBulkShapes[0])); }
+void set_bulk_shape(int32_t i) { g_bulk_shape.store(i); }
+void bulk_shape(int32_t i, int32_t* warps, int32_t* stages) {
+  *warps = kBulkShapes[i][0];
+  *stages = kBulkShapes[i][1];
+}
+
 ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
-  const int64_t max_smem_bitmap = 200 * 1024;
+  const bool ldg = (a.flags & ARA_RUN_LDG) != 0;
+  // shared-memory budget of the hit bitmap: what the block may use beyond the staging ring
+  const int64_t max_smem_bitmap =
+      ldg ? 200 * 1024 : (int64_t)pf.max_smem_block - bulk_ring_bytes() - 128;
   StreamParams sp{};
   sp.n_trials = a.n_trials;
   sp.offsets = a.offsets;
@@ -529,7 +835,11 @@ ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   sp.smem_words = coarse_words(pf.catalogue, sp.shift);
   sp.bm_words = pf.bm_words;
   sp.err = pf.d_err;
+  sp.wait_limit_ns = g_wait_limit_ns.load();
+  sp.debug_extra_tx = g_debug_extra_tx.load();
   const bool per_elt = (a.flags & ARA_RUN_PER_ELT) != 0;
+  const bool nof = (a.flags & ARA_RUN_NO_FILTER) != 0;
+  const bool f64 = (a.flags & ARA_RUN_F64_SUM) != 0;
   for (int32_t i = 0; i < a.n_sel; ++i) {
     const int layer = a.sel[i];
     sp.q = pf.d_q + (int64_t)layer * pf.catalogue;
@@ -550,12 +860,12 @@ ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
                                                    pf.d_elt_ret, pf.d_elt_lim);
       ARA_TRY(cudaGetLastError());
       st = ARA_OK;
-    } else if (a.flags & ARA_RUN_F64_SUM) {
-      st = (a.flags & ARA_RUN_NO_FILTER) ? launch_folded_one<false, double>(pf, sp, s)
-                                         : launch_folded_one<true, double>(pf, sp, s);
+    } else if (ldg) {
+      if (f64) st = nof ? launch_folded_one<false, double>(pf, sp, s) : launch_folded_one<true, double>(pf, sp, s);
+      else st = nof ? launch_folded_one<false, U128>(pf, sp, s) : launch_folded_one<true, U128>(pf, sp, s);
     } else {
-      st = (a.flags & ARA_RUN_NO_FILTER) ? launch_folded_one<false, U128>(pf, sp, s)
-                                         : launch_folded_one<true, U128>(pf, sp, s);
+      if (f64) st = nof ? launch_bulk_one<false, double>(pf, sp, s) : launch_bulk_one<true, double>(pf, sp, s);
+      else st = nof ? launch_bulk_one<false, U128>(pf, sp, s) : launch_bulk_one<true, U128>(pf, sp, s);
     }
     if (st != ARA_OK) return st;
   }

@@ -20,7 +20,7 @@ if torch.cuda.is_available():
     import paper_1606_04473_gb300 as ara
 
 INF = float("inf")
-FLAG_SETS = [0, 2, 4, 6]  # folded; no filter; FP64 sums; both
+FLAG_SETS = [0, 2, 4, 6, 8, 10, 12]  # bulk-staged folded; no filter; FP64 sums; both; LDG variants
 
 
 def dev(yet):
@@ -288,3 +288,44 @@ def test_paper_scale_full_size_sampled():
     ref, agg = oracle.ylt(pf, yet, trials=sample, return_agg=True)
     assert_ylt_close(yc[:, sample], ref, agg)
     del ids
+
+
+def test_every_stream_shape_gives_identical_ylt(mid):
+    pf, yet, ref, agg = mid
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    shapes = ara.stream_shapes()
+    assert len(shapes) >= 2
+    try:
+        outs = []
+        for i in range(len(shapes)):
+            ara.set_stream_shape(i)
+            outs.append(g.run_ylt(off, ids).clone())
+            g.check()
+    finally:
+        ara.set_stream_shape(0)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    assert_ylt_close(outs[0].cpu().numpy(), ref, agg)
+
+
+def test_bounded_copy_wait_times_out_and_reports(tiny):
+    """Every wait for a bulk copy is bounded: with copies that announce more bytes than they
+    deliver, each wait runs out after the (shortened) limit, the kernel returns, and the host
+    reads ARA_ETIMEOUT; the context stays usable."""
+    pf, yet, ref, agg = tiny
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    try:
+        ara.debug_set(ara.ARA_DBG_WAIT_LIMIT_NS, 2_000_000)
+        ara.debug_set(ara.ARA_DBG_STARVE_COPIES, 16)
+        g.run_ylt(off, ids)
+        with pytest.raises(ara.AraError) as e:
+            g.check()
+        assert e.value.status == ara.ARA_ETIMEOUT
+    finally:
+        ara.debug_set(ara.ARA_DBG_STARVE_COPIES, 0)
+        ara.debug_set(ara.ARA_DBG_WAIT_LIMIT_NS, 1_000_000_000)
+    y = g.run_ylt(off, ids)
+    g.check()
+    assert_ylt_close(y.cpu().numpy(), ref, agg)
