@@ -165,6 +165,63 @@ ARA_API ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials,
 ARA_API ara_status ara_check(ara_portfolio* pf, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Adjoint: sensitivities of the risk metrics (Section IV-A) to the financial terms and the
+ * ELT losses (Section IV-B).
+ * --------------------------------------------------------------------------------------- */
+
+/*
+ * For every selected layer, the gradients of two objectives of its YLT row y:
+ *   objective 0: the mean year loss (1/N) sum_t y_t
+ *   objective 1: TVaR at tvar_level, the mean of the m = ceil(N(1-p)) largest y
+ * with respect to every per-ELT retention and limit of the layer's ELTs, the layer's OccR,
+ * OccL, AggR, AggL, and every ELT loss record of the layer.  The clamps are piecewise linear;
+ * at a kink the derivative is taken as 0.  When the m-th and (m+1)-th largest year losses tie,
+ * the trials equal to the m-th share its weight equally (the mean over every choice of the
+ * top-m set) and h_ties reports it.  Uses the forward's YLT and recorded regimes instead of
+ * recomputing the trial sums.  Synchronous.
+ *   YET arguments and layer selection: exactly those of the ara_run_ylt call that produced
+ *                  d_ylt and d_regimes (same trials, same layers in the same order)
+ *   d_ylt          device [n_layer_sel][n_trials]  (from ara_run_ylt)
+ *   d_regimes      device [n_layer_sel][n_trials]  (from ara_run_ylt)
+ *   tvar_level     p in [0, 1) with ceil(N(1-p)) >= 1
+ *   d_grad_elt     device [2][K][2] double: K = total ELT slots of the selected layers (each
+ *                  layer's ELTs in layer order, layers in selection order); (d/dR_j, d/dL_j)
+ *   d_grad_layer   device [2][n_layer_sel][4] double: d/dOccR, d/dOccL, d/dAggR, d/dAggL
+ *   d_grad_loss    device [2][M] double: M = total records of those slots; slot by slot, each
+ *                  ELT's records in the order given to ara_create_portfolio
+ *   h_ties         host [n_layer_sel] int32 or NULL
+ * Errors: ARA_EINVAL, ARA_ERANGE (a layer with more than 256 ELTs), ARA_ENOMEM, ARA_ECUDA,
+ * ARA_EDATA.
+ */
+ARA_API ara_status ara_adjoint(ara_portfolio* pf, int64_t n_trials, const int64_t* d_trial_offsets,
+                               int64_t n_events, const int32_t* d_event_ids, int32_t n_layer_sel,
+                               const int32_t* layer_sel, const double* d_ylt,
+                               const uint8_t* d_regimes, double tvar_level, double* d_grad_elt,
+                               double* d_grad_layer, double* d_grad_loss, int32_t* h_ties,
+                               void* stream);
+
+/*
+ * ara_adjoint folded into the portfolio's own parameter layout, for reverse-mode automatic
+ * differentiation: with upstream weights w[i][o] (selected layer i, objective o as above),
+ *   d_g_elt_ret[j], d_g_elt_lim[j]   += sum over (i, o, slots of ELT j) w[i][o] * dJ/d(R_j, L_j)
+ *   d_g_layer[l][0..3]               += sum over (i selecting l, o) w[i][o] * dJ/d(OccR..AggL)
+ *   d_g_loss[r]                      += the same for every ELT record r, records in the order
+ *                                       given to ara_create_portfolio (ELT by ELT)
+ *   h_weights   host [n_layer_sel][2]
+ *   d_g_elt_ret, d_g_elt_lim  device [n_elts]; d_g_layer device [n_layers][4];
+ *   d_g_loss    device [total records]   (accumulated into: zero them first)
+ * Synchronous.  Errors as ara_adjoint.
+ */
+ARA_API ara_status ara_adjoint_accumulate(ara_portfolio* pf, int64_t n_trials,
+                                          const int64_t* d_trial_offsets, int64_t n_events,
+                                          const int32_t* d_event_ids, int32_t n_layer_sel,
+                                          const int32_t* layer_sel, const double* d_ylt,
+                                          const uint8_t* d_regimes, double tvar_level,
+                                          const double* h_weights, double* d_g_elt_ret,
+                                          double* d_g_elt_lim, double* d_g_layer,
+                                          double* d_g_loss, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Risk metrics of Section IV-A (PML, TVaR), read as empirical order statistics of the YLT:
  *   PML(RP)  = the k-th largest year loss, k = ceil(N / RP)
  *   TVaR(p)  = mean of the m largest year losses, m = ceil(N (1 - p))

@@ -64,6 +64,10 @@ def lib() -> ctypes.CDLL:
     L.ara_set_stream_shape.restype = i32
     L.ara_debug_set.argtypes = [i32, i64]
     L.ara_debug_set.restype = i32
+    L.ara_adjoint.argtypes = [P, i64, P, i64, P, i32, P, P, P, d, P, P, P, P, P]
+    L.ara_adjoint.restype = i32
+    L.ara_adjoint_accumulate.argtypes = [P, i64, P, i64, P, i32, P, P, P, d, P, P, P, P, P, P]
+    L.ara_adjoint_accumulate.restype = i32
     L.ara_timing_enable.argtypes = [i32]
     L.ara_timing_enable.restype = None
     L.ara_timing_reset.restype = None
@@ -140,6 +144,9 @@ class Portfolio:
         self.catalogue = int(catalogue)
         self.n_layers = len(layer_elts)
         self.n_elts = n_elts
+        self.layer_elts = [list(map(int, l)) for l in layer_elts]
+        self.elt_nnz = [int(len(x)) for x in elt_ids]
+        self.n_records = int(off[-1])
 
     @classmethod
     def from_tables(cls, pf, dense_tables: bool = False) -> "Portfolio":
@@ -212,6 +219,57 @@ class Portfolio:
             return out, pml, tvar, mean
         if rp.size or lv.size:
             return out, pml, tvar
+        return out
+
+    def adjoint(self, offsets, event_ids, ylt, regimes, tvar_level: float = 0.99, layers=None,
+                stream=None):
+        """Gradients of each selected layer's mean year loss (objective 0) and TVaR (objective 1)
+        from a forward run's YLT and regimes (ara_adjoint).  Returns a dict of device tensors:
+        'elt' [2, K, 2] (d/dR, d/dL per ELT slot), 'layer' [2, n_sel, 4] (OccR, OccL, AggR, AggL),
+        'loss' [2, M] (per record of each slot, creation order), and 'ties' (numpy int32)."""
+        import torch
+        n_trials = offsets.numel() - 1
+        n_sel, sel_p, n_out, sel = self._sel(layers)
+        lay = list(range(self.n_layers)) if sel is None else [int(x) for x in sel]
+        K = sum(len(self.layer_elts[l]) for l in lay)
+        M = sum(self.elt_nnz[j] for l in lay for j in self.layer_elts[l])
+        dev = offsets.device
+        ge = torch.zeros((2, max(K, 1), 2), dtype=torch.float64, device=dev)
+        gl = torch.zeros((2, n_out, 4), dtype=torch.float64, device=dev)
+        gx = torch.zeros((2, max(M, 1)), dtype=torch.float64, device=dev)
+        ties = np.zeros(n_out, dtype=np.int32)
+        st = lib().ara_adjoint(self._h, n_trials, _dev_ptr(offsets, torch.int64, "offsets"),
+                               event_ids.numel(), _dev_ptr(event_ids, torch.int32, "event_ids"),
+                               n_sel, sel_p, _dev_ptr(ylt, torch.float64, "ylt"),
+                               _dev_ptr(regimes, torch.uint8, "regimes"), float(tvar_level),
+                               _dev_ptr(ge, torch.float64, "g"), _dev_ptr(gl, torch.float64, "g"),
+                               _dev_ptr(gx, torch.float64, "g"), _np_ptr(ties), _stream_handle(stream))
+        _check(st, "ara_adjoint")
+        return {"elt": ge[:, :K], "layer": gl, "loss": gx[:, :M], "ties": ties}
+
+    def adjoint_accumulate(self, offsets, event_ids, ylt, regimes, weights, tvar_level: float = 0.99,
+                           layers=None, out=None, stream=None):
+        """Upstream-weighted gradients in parameter layout (ara_adjoint_accumulate): weights
+        [n_sel, 2] for (mean, TVaR) of each selected layer; returns (or adds into `out`) the dict
+        'elt_ret' [n_elts], 'elt_lim' [n_elts], 'layer' [n_layers, 4], 'loss' [n_records]."""
+        import torch
+        n_trials = offsets.numel() - 1
+        n_sel, sel_p, n_out, _s = self._sel(layers)
+        dev = offsets.device
+        if out is None:
+            out = {"elt_ret": torch.zeros(max(self.n_elts, 1), dtype=torch.float64, device=dev),
+                   "elt_lim": torch.zeros(max(self.n_elts, 1), dtype=torch.float64, device=dev),
+                   "layer": torch.zeros((max(self.n_layers, 1), 4), dtype=torch.float64, device=dev),
+                   "loss": torch.zeros(max(self.n_records, 1), dtype=torch.float64, device=dev)}
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(n_out, 2))
+        st = lib().ara_adjoint_accumulate(
+            self._h, n_trials, _dev_ptr(offsets, torch.int64, "offsets"), event_ids.numel(),
+            _dev_ptr(event_ids, torch.int32, "event_ids"), n_sel, sel_p,
+            _dev_ptr(ylt, torch.float64, "ylt"), _dev_ptr(regimes, torch.uint8, "regimes"),
+            float(tvar_level), _np_ptr(w), _dev_ptr(out["elt_ret"], torch.float64, "g"),
+            _dev_ptr(out["elt_lim"], torch.float64, "g"), _dev_ptr(out["layer"], torch.float64, "g"),
+            _dev_ptr(out["loss"], torch.float64, "g"), _stream_handle(stream))
+        _check(st, "ara_adjoint_accumulate")
         return out
 
     def check(self, stream=None):

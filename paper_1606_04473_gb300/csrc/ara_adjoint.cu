@@ -1,0 +1,584 @@
+// Adjoint of the YLT path: sensitivities of each layer's mean year loss and TVaR to every
+// retention and limit (per-ELT terms I, layer terms T of Section IV-B) and to every ELT loss.
+//
+// With J = sum_t w_t y_t and the clamp C(x; R, L) = min(max(x - R, 0), L) (slope 1 in x and -1
+// in R when 0 < x - R < L, slope 1 in L when x - R > L, 0 at the kinks):
+//   g_t  = [aggregate clamp interior for trial t]        (recorded by the forward as regime 1)
+//   c(e) = sum_t w_t g_t cnt_t(e)                          (weighted event histogram)
+//   dJ/dAggR = -sum_t w_t g_t            dJ/dAggL = sum_t w_t [regime_t == 2]
+//   dJ/dOccR = -sum_e c(e) [r_o(e)==1]   dJ/dOccL = sum_e c(e) [r_o(e)==2]
+//   dJ/dx_j(e) = c(e) [r_o(e)==1][r_j(e)==1]
+//   dJ/dR_j  = -sum_e c(e) [r_o(e)==1][r_j(e)==1]   dJ/dL_j = sum_e c(e) [r_o(e)==1][r_j(e)==2]
+// Mean: w_t = 1/N.  TVaR_p: w_t = 1/m above the m-th largest year loss v, and f/m on the
+// trials equal to v, f = (m - #{y > v}) / #{y == v} (ties share the boundary weight).
+// Every sum is kept as an exact integer count (histograms and counters of trials/events);
+// the only roundings are the final divisions by N and m and the products by f.
+
+#include <algorithm>
+#include <vector>
+
+#include "ara_internal.cuh"
+
+namespace ara {
+
+constexpr unsigned FULLM = 0xffffffffu;
+constexpr int ADJ_MAX_SLOTS = 256;
+
+struct AdjCounts {          // per layer
+  unsigned long long occ[2][3];   // [regime 1 / 2][mean, gt, eq] sums of histogram counts
+  unsigned long long agg[2][3];   // [regime 1 / 2][mean, gt, eq] trial counts
+};
+struct SlotCounts {          // per ELT slot
+  unsigned long long rl[2][3];    // [R (interior) / L (above)][mean, gt, eq]
+};
+
+__device__ __forceinline__ uint64_t adj_key(double y) {
+  const uint64_t b = (uint64_t)__double_as_longlong(y);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_int(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULLM, v, o);
+  return v;
+}
+
+// Block-wide sum of K unsigned 64-bit counters into global counters (one atomic per counter).
+template <int K>
+__device__ __forceinline__ void block_add(unsigned long long (&v)[K], unsigned long long* out) {
+  __shared__ unsigned long long part[32][K];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum_int(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) part[warp][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x < K) {
+    unsigned long long s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w][threadIdx.x];
+    if (s) atomicAdd(&out[threadIdx.x], s);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Histogram of the events of interior trials, restricted to events whose occurrence clamp is
+// not in its zero regime (hit bitmap in shared memory).  One warp per trial of a 32-trial
+// group; trials outside the aggregate interior are skipped without reading their events.
+// ------------------------------------------------------------------------------------------
+struct AdjHistParams {
+  int64_t n_trials;
+  const int64_t* offsets;
+  int64_t n_events;
+  const int32_t* ids;
+  int64_t catalogue;
+  const uint8_t* regimes;     // this layer's recorded aggregate regimes [n_trials]
+  const double* ylt;          // this layer's YLT [n_trials]
+  const uint64_t* thr_key;    // device: key of the m-th largest year loss
+  const uint32_t* bits;       // exact bitmap of r_o(e) != 0
+  int64_t bm_words, smem_words;
+  int32_t shift;
+  uint32_t* h_mean;
+  uint32_t* h_gt;
+  uint32_t* h_eq;
+  uint32_t* err;
+};
+
+__device__ __forceinline__ uint32_t adj_coarsen(const uint32_t* __restrict__ src, int64_t cw,
+                                                int shift, int64_t n_words) {
+  if (shift == 0) return cw < n_words ? src[cw] : 0u;
+  uint32_t out = 0;
+  const int G = 1 << shift;
+  if (shift <= 4) {
+    const int per = 32 >> shift;
+    for (int w = 0; w < G; ++w) {
+      const int64_t ew = (cw << shift) + w;
+      const uint32_t x = ew < n_words ? src[ew] : 0u;
+      for (int b = 0; b < per; ++b)
+        out |= (((x >> (b * G)) & ((1u << G) - 1u)) ? 1u : 0u) << (w * per + b);
+    }
+  } else {
+    const int64_t wpb = (int64_t)1 << (shift - 5);
+    for (int b = 0; b < 32; ++b) {
+      const int64_t w0 = (cw * 32 + b) * wpb;
+      uint32_t any = 0;
+      for (int64_t w = w0; w < w0 + wpb && w < n_words; ++w) any |= src[w];
+      out |= (any ? 1u : 0u) << b;
+    }
+  }
+  return out;
+}
+
+__global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
+  extern __shared__ uint32_t bm[];
+  for (int64_t cw = threadIdx.x; cw < p.smem_words; cw += blockDim.x)
+    bm[cw] = adj_coarsen(p.bits, cw, p.shift, p.bm_words);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n_groups = (p.n_trials + 31) >> 5;
+  const uint64_t thr = *p.thr_key;
+  bool bad_id = false, bad_off = false;
+  for (int64_t g = warp; g < n_groups; g += nwarps) {
+    const int64_t t0 = g << 5;
+    const int nt = (int)min((int64_t)32, p.n_trials - t0);
+    int cls = 0;
+    if (lane < nt && p.regimes[t0 + lane] == 1) {
+      const uint64_t k = adj_key(p.ylt[t0 + lane]);
+      cls = k > thr ? 2 : (k == thr ? 3 : 1);
+    }
+    unsigned todo = __ballot_sync(FULLM, cls != 0);
+    if (!todo) continue;
+    const int64_t my_off = (lane <= nt) ? __ldg(p.offsets + t0 + lane) : 0;
+    const int64_t last_off = (nt == 32) ? __ldg(p.offsets + t0 + 32) : 0;
+    while (todo) {
+      const int k = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int c = __shfl_sync(FULLM, cls, k);
+      int64_t beg = __shfl_sync(FULLM, my_off, k);
+      int64_t end = (k + 1 < 32) ? __shfl_sync(FULLM, my_off, k + 1) : last_off;
+      if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; continue; }
+      for (int64_t i = beg + lane; i < end; i += 32) {
+        const int e = __ldcs(p.ids + i);
+        if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; continue; }
+        const uint32_t b = (uint32_t)e >> p.shift;
+        if (!((bm[b >> 5] >> (b & 31)) & 1u)) continue;
+        atomicAdd(p.h_mean + e, 1u);
+        if (c == 2) atomicAdd(p.h_gt + e, 1u);
+        else if (c == 3) atomicAdd(p.h_eq + e, 1u);
+      }
+    }
+  }
+  if (bad_id) atomicOr(p.err, DERR_EVENT_RANGE);
+  if (bad_off) atomicOr(p.err, DERR_OFFSETS);
+}
+
+// Sums over catalogue events of the histograms, split by occurrence regime.
+__global__ void __launch_bounds__(256) k_adj_events(int64_t catalogue, const uint8_t* __restrict__ reg,
+                                                    const uint32_t* __restrict__ hm,
+                                                    const uint32_t* __restrict__ hg,
+                                                    const uint32_t* __restrict__ he,
+                                                    AdjCounts* __restrict__ acc) {
+  unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < catalogue;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t r = reg[e];
+    if (r == 0) continue;
+    const int o = (r == 1) ? 0 : 3;
+    v[o + 0] += hm[e];
+    v[o + 1] += hg[e];
+    v[o + 2] += he[e];
+  }
+  block_add<6>(v, &acc->occ[0][0]);
+}
+
+// Per ELT record: its loss gradient for both objectives, and per ELT slot the counts of the
+// retention (interior) and limit (above) derivatives.
+struct AdjRecParams {
+  const int64_t* rec_off;
+  const int32_t* rec_ids;
+  const float* loss32;
+  const double* loss64;
+  const int32_t* rec_orig;     // original position of each (sorted) record within its ELT
+  const double* elt_ret;
+  const double* elt_lim;
+  const uint8_t* reg;
+  const uint32_t* hm;
+  const uint32_t* hg;
+  const uint32_t* he;
+  const unsigned long long* sel_gt;   // #{y > v} of this layer
+  const unsigned long long* sel_eq;   // #{y == v}
+  int64_t n_trials, m;
+  double* grad_loss_mean;      // [M] objective 0
+  double* grad_loss_tvar;      // [M] objective 1
+  SlotCounts* slots;           // [n_slots of this layer]
+  int32_t n_slots;
+  int32_t elt[ADJ_MAX_SLOTS];
+  int64_t base[ADJ_MAX_SLOTS];
+};
+
+__global__ void __launch_bounds__(256) k_adj_records(AdjRecParams p) {
+  const int k = blockIdx.y;
+  const int j = p.elt[k];
+  const double R = p.elt_ret[j], L = p.elt_lim[j];
+  const double invN = 1.0 / (double)p.n_trials, invM = 1.0 / (double)p.m;
+  const unsigned long long cg = *p.sel_gt, ce = *p.sel_eq;
+  const double f = ce ? (double)(p.m - (int64_t)cg) / (double)ce : 0.0;
+  unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t r = p.rec_off[j] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < p.rec_off[j + 1];
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int e = p.rec_ids[r];
+    const double x = p.loss32 ? (double)p.loss32[r] : p.loss64[r];
+    const double ex = __dsub_rn(x, R);
+    const int rj = (ex > 0.0 && ex < L) ? 1 : (ex > L ? 2 : 0);
+    double gm = 0.0, gt = 0.0;
+    if (p.reg[e] == 1 && rj != 0) {
+      const uint32_t a = p.hm[e], b = p.hg[e], c = p.he[e];
+      const int o = (rj == 1) ? 0 : 3;
+      v[o + 0] += a;
+      v[o + 1] += b;
+      v[o + 2] += c;
+      if (rj == 1) {
+        gm = (double)a * invN;
+        gt = ((double)b + f * (double)c) * invM;
+      }
+    }
+    const int64_t pos = p.base[k] + p.rec_orig[r];
+    p.grad_loss_mean[pos] = gm;
+    p.grad_loss_tvar[pos] = gt;
+  }
+  block_add<6>(v, &p.slots[k].rl[0][0]);
+}
+
+// Per trial: counts of interior / saturated aggregate regimes, overall and in TVaR's top set.
+__global__ void __launch_bounds__(256) k_adj_trials(int64_t n, const uint8_t* __restrict__ regimes,
+                                                    const double* __restrict__ ylt,
+                                                    const uint64_t* __restrict__ thr_key,
+                                                    AdjCounts* __restrict__ acc) {
+  const uint64_t thr = *thr_key;
+  unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t r = regimes[t];
+    if (r == 0) continue;
+    const int o = (r == 1) ? 0 : 3;
+    const uint64_t k = adj_key(ylt[t]);
+    v[o + 0] += 1;
+    v[o + 1] += k > thr ? 1 : 0;
+    v[o + 2] += k == thr ? 1 : 0;
+  }
+  block_add<6>(v, &acc->agg[0][0]);
+}
+
+// Final per-layer gradients from the integer counts.
+__global__ void k_adj_finish(const AdjCounts* __restrict__ acc, const SlotCounts* __restrict__ slots,
+                             int32_t n_slots, const unsigned long long* sel_gt,
+                             const unsigned long long* sel_eq, int64_t n, int64_t m,
+                             double* grad_layer_mean, double* grad_layer_tvar,
+                             double* grad_elt_mean, double* grad_elt_tvar) {
+  const double invN = 1.0 / (double)n, invM = 1.0 / (double)m;
+  const unsigned long long cg = *sel_gt, ce = *sel_eq;
+  const double f = ce ? (double)(m - (int64_t)cg) / (double)ce : 0.0;
+  auto mean_of = [&](const unsigned long long (&c)[3]) { return (double)c[0] * invN; };
+  auto tvar_of = [&](const unsigned long long (&c)[3]) {
+    return ((double)c[1] + f * (double)c[2]) * invM;
+  };
+  if (threadIdx.x == 0) {
+    grad_layer_mean[0] = -mean_of(acc->occ[0]);
+    grad_layer_mean[1] = mean_of(acc->occ[1]);
+    grad_layer_mean[2] = -mean_of(acc->agg[0]);
+    grad_layer_mean[3] = mean_of(acc->agg[1]);
+    grad_layer_tvar[0] = -tvar_of(acc->occ[0]);
+    grad_layer_tvar[1] = tvar_of(acc->occ[1]);
+    grad_layer_tvar[2] = -tvar_of(acc->agg[0]);
+    grad_layer_tvar[3] = tvar_of(acc->agg[1]);
+  }
+  for (int k = threadIdx.x; k < n_slots; k += blockDim.x) {
+    grad_elt_mean[2 * k + 0] = -mean_of(slots[k].rl[0]);
+    grad_elt_mean[2 * k + 1] = mean_of(slots[k].rl[1]);
+    grad_elt_tvar[2 * k + 0] = -tvar_of(slots[k].rl[0]);
+    grad_elt_tvar[2 * k + 1] = tvar_of(slots[k].rl[1]);
+  }
+}
+
+// Weighted accumulation of one layer's gradients into the portfolio's parameter layout:
+// out += w0 * objective-0 gradient + w1 * objective-1 gradient.
+struct AdjScatterParams {
+  double w0, w1;
+  int32_t layer, n_slots;
+  const double* gl0;   // [4] layer gradients, objective 0
+  const double* gl1;
+  const double* ge0;   // [n_slots][2] ELT-slot gradients
+  const double* ge1;
+  const double* gx0;   // [records of the layer's slots] loss gradients
+  const double* gx1;
+  const int64_t* rec_off;
+  const int32_t* rec_orig;
+  double* g_elt_ret;   // [n_elts]
+  double* g_elt_lim;
+  double* g_layer;     // [n_layers][4]
+  double* g_loss;      // [n_records], creation order
+  int32_t elt[ADJ_MAX_SLOTS];
+  int64_t base[ADJ_MAX_SLOTS];
+};
+
+__global__ void __launch_bounds__(256) k_adj_scatter(AdjScatterParams p) {
+  const int k = blockIdx.y;
+  const int j = p.elt[k];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(&p.g_elt_ret[j], p.w0 * p.ge0[2 * k] + p.w1 * p.ge1[2 * k]);
+    atomicAdd(&p.g_elt_lim[j], p.w0 * p.ge0[2 * k + 1] + p.w1 * p.ge1[2 * k + 1]);
+    if (k == 0)
+      for (int c = 0; c < 4; ++c) p.g_layer[4 * p.layer + c] += p.w0 * p.gl0[c] + p.w1 * p.gl1[c];
+  }
+  const int64_t r0 = p.rec_off[j], n = p.rec_off[j + 1] - r0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = p.rec_orig[r0 + i];        // creation-order position within the ELT
+    const int64_t src = p.base[k] + o;
+    const double g = p.w0 * p.gx0[src] + p.w1 * p.gx1[src];
+    if (g != 0.0) atomicAdd(&p.g_loss[r0 + o], g);
+  }
+}
+
+}  // namespace ara
+
+using namespace ara;
+
+extern "C" ara_status ara_adjoint(ara_portfolio* pf_, int64_t n_trials, const int64_t* d_offsets,
+                                  int64_t n_events, const int32_t* d_ids, int32_t n_sel_in,
+                                  const int32_t* layer_sel, const double* d_ylt,
+                                  const uint8_t* d_regimes, double tvar_level, double* d_grad_elt,
+                                  double* d_grad_layer, double* d_grad_loss, int32_t* h_ties,
+                                  void* stream) {
+  Portfolio* pf = static_cast<Portfolio*>(pf_);
+  if (!pf || n_trials < 1 || n_events < 0 || !d_offsets || !d_ylt || !d_regimes) return ARA_EINVAL;
+  if (n_events > 0 && !d_ids) return ARA_EINVAL;
+  if (!d_grad_elt || !d_grad_layer || !d_grad_loss) return ARA_EINVAL;
+  std::vector<int32_t> sel;
+  if (n_sel_in == 0 && layer_sel == nullptr) {
+    for (int32_t l = 0; l < pf->n_layers; ++l) sel.push_back(l);
+  } else {
+    if (n_sel_in < 0 || !layer_sel) return ARA_EINVAL;
+    for (int32_t i = 0; i < n_sel_in; ++i) {
+      if (layer_sel[i] < 0 || layer_sel[i] >= pf->n_layers) return ARA_EINVAL;
+      sel.push_back(layer_sel[i]);
+    }
+  }
+  const int32_t n_sel = (int32_t)sel.size();
+  if (n_sel == 0) return ARA_OK;
+  if (((uintptr_t)d_ids & 3) || ((uintptr_t)d_ylt & 7)) return ARA_EINVAL;
+  const int64_t m = tail_count_snap(n_trials, tvar_level);
+  if (m < 1) return ARA_EINVAL;
+  for (int32_t i = 0; i < n_sel; ++i)
+    if (pf->layer_off[sel[i] + 1] - pf->layer_off[sel[i]] > ADJ_MAX_SLOTS) return ARA_ERANGE;
+  DeviceGuard g(pf->device);
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // TVaR threshold, #{y > v} and #{y == v} of every selected layer
+  SelectResult sr;
+  ara_status st = select_one_rank(d_ylt, n_trials, n_sel, m, pf->n_sms, s, &sr);
+  if (st != ARA_OK) return st;
+
+  // scratch
+  const int64_t C = pf->catalogue;
+  const int64_t bmw = pf->bm_words;
+  size_t off = 0;
+  auto take = [&](size_t n) { size_t o = (off + 255) / 256 * 256; off = o + n; return o; };
+  const size_t o_reg = take((size_t)C), o_bits = take(4 * (size_t)bmw);
+  const size_t o_hm = take(4 * (size_t)C), o_hg = take(4 * (size_t)C), o_he = take(4 * (size_t)C);
+  const size_t o_acc = take(sizeof(AdjCounts)), o_slots = take(sizeof(SlotCounts) * ADJ_MAX_SLOTS);
+  char* scratch = nullptr;
+  cudaError_t ce = cudaMallocAsync((void**)&scratch, off, s);
+  if (ce != cudaSuccess) {
+    free_select_result(sr, s);
+    return ce == cudaErrorMemoryAllocation ? ARA_ENOMEM : ARA_ECUDA;
+  }
+  uint8_t* reg = (uint8_t*)(scratch + o_reg);
+  uint32_t* bits = (uint32_t*)(scratch + o_bits);
+  uint32_t* hm = (uint32_t*)(scratch + o_hm);
+  uint32_t* hg = (uint32_t*)(scratch + o_hg);
+  uint32_t* he = (uint32_t*)(scratch + o_he);
+  AdjCounts* acc = (AdjCounts*)(scratch + o_acc);
+  SlotCounts* slots = (SlotCounts*)(scratch + o_slots);
+
+  // shared-memory bitmap for the histogram pass
+  int shift = 0;
+  auto cw = [&](int sh) { return (((C + ((int64_t)1 << sh) - 1) >> sh) + 31) / 32; };
+  const int64_t bm_budget = std::min<int64_t>(pf->max_smem_block, 200 * 1024);
+  while (cw(shift) * 4 > bm_budget) ++shift;
+  const int smem = (int)(cw(shift) * 4);
+  ara_status out_st = ARA_OK;
+  if (cudaFuncSetAttribute((const void*)k_adj_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           std::max(smem, 48 * 1024)) != cudaSuccess)
+    out_st = ARA_ECUDA;
+
+  int64_t elt_slot0 = 0, loss_base0 = 0;
+  int64_t total_slots = 0, total_loss = 0;
+  for (int32_t i = 0; i < n_sel; ++i) {
+    const int l = sel[i];
+    for (int k = pf->layer_off[l]; k < pf->layer_off[l + 1]; ++k) {
+      const int j = pf->layer_elts[k];
+      total_loss += pf->rec_off[j + 1] - pf->rec_off[j];
+      ++total_slots;
+    }
+  }
+  for (int32_t i = 0; i < n_sel && out_st == ARA_OK; ++i) {
+    const int l = sel[i];
+    const LayerConst& lc = pf->layers[l];
+    const int n_le = lc.elt_end - lc.elt_begin;
+    // 1. occurrence regimes of every catalogue event and the bitmap of regime != 0
+    FoldOutHost fo;
+    fo.bits = bits;
+    fo.regime = reg;
+    fo.bits_stride = bmw;
+    fo.regime_stride = C;
+    fo.by_slot = 1;
+    fo.bits_from_regime = 1;
+    if ((out_st = launch_fold_to(*pf, 1, &l, fo, s)) != ARA_OK) break;
+    // 2. histograms and counters
+    if (cudaMemsetAsync(scratch + o_hm, 0, off - o_hm, s) != cudaSuccess) { out_st = ARA_ECUDA; break; }
+    AdjHistParams hp{};
+    hp.n_trials = n_trials;
+    hp.offsets = d_offsets;
+    hp.n_events = n_events;
+    hp.ids = d_ids ? d_ids : reinterpret_cast<const int32_t*>(d_offsets);
+    hp.catalogue = C;
+    hp.regimes = d_regimes + (int64_t)i * n_trials;
+    hp.ylt = d_ylt + (int64_t)i * n_trials;
+    hp.thr_key = sr.thr_key + (int64_t)i * sr.thr_stride;
+    hp.bits = bits;
+    hp.bm_words = bmw;
+    hp.smem_words = cw(shift);
+    hp.shift = shift;
+    hp.h_mean = hm;
+    hp.h_gt = hg;
+    hp.h_eq = he;
+    hp.err = pf->d_err;
+    {
+      LaunchScope ls(ARA_K_ADJOINT, s, 4);
+      // the threshold key is read on the device from the selection result
+      k_adj_hist<<<pf->n_sms, 1024, smem, s>>>(hp);
+      k_adj_events<<<std::max(1, (int)std::min<int64_t>((C + 2047) / 2048, 4 * pf->n_sms)), 256, 0, s>>>(
+          C, reg, hm, hg, he, acc);
+      k_adj_trials<<<std::max(1, (int)std::min<int64_t>((n_trials + 2047) / 2048, 4 * pf->n_sms)), 256, 0, s>>>(
+          n_trials, d_regimes + (int64_t)i * n_trials, d_ylt + (int64_t)i * n_trials,
+          sr.thr_key + (int64_t)i * sr.thr_stride, acc);
+      AdjRecParams rp{};
+      rp.rec_off = pf->d_rec_off;
+      rp.rec_ids = pf->d_rec_ids;
+      rp.loss32 = pf->d_rec_loss32;
+      rp.loss64 = pf->d_rec_loss;
+      rp.rec_orig = pf->d_rec_orig;
+      rp.elt_ret = pf->d_elt_ret;
+      rp.elt_lim = pf->d_elt_lim;
+      rp.reg = reg;
+      rp.hm = hm;
+      rp.hg = hg;
+      rp.he = he;
+      rp.sel_gt = sr.gt + i;
+      rp.sel_eq = sr.eq + i;
+      rp.n_trials = n_trials;
+      rp.m = m;
+      rp.grad_loss_mean = d_grad_loss;
+      rp.grad_loss_tvar = d_grad_loss + total_loss;
+      rp.slots = slots;
+      rp.n_slots = n_le;
+      int64_t b = loss_base0;
+      for (int k = 0; k < n_le; ++k) {
+        const int j = pf->layer_elts[lc.elt_begin + k];
+        rp.elt[k] = j;
+        rp.base[k] = b;
+        b += pf->rec_off[j + 1] - pf->rec_off[j];
+      }
+      if (n_le > 0) {
+        dim3 grid(16, n_le);
+        k_adj_records<<<grid, 256, 0, s>>>(rp);
+      }
+      k_adj_finish<<<1, 256, 0, s>>>(acc, slots, n_le, sr.gt + i, sr.eq + i, n_trials, m,
+                                     d_grad_layer + (int64_t)i * 4,
+                                     d_grad_layer + (int64_t)(n_sel + i) * 4,
+                                     d_grad_elt + 2 * elt_slot0,
+                                     d_grad_elt + 2 * (total_slots + elt_slot0));
+      if (cudaGetLastError() != cudaSuccess) { out_st = ARA_ECUDA; break; }
+      loss_base0 = b;
+      elt_slot0 += n_le;
+    }
+  }
+  std::vector<unsigned long long> gt(n_sel), eq(n_sel);
+  if (out_st == ARA_OK && h_ties) {
+    if (cudaMemcpyAsync(gt.data(), sr.gt, 8 * n_sel, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(eq.data(), sr.eq, 8 * n_sel, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      out_st = ARA_ECUDA;
+  }
+  cudaFreeAsync(scratch, s);
+  free_select_result(sr, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && out_st == ARA_OK) out_st = ARA_ECUDA;
+  if (out_st == ARA_OK && h_ties)
+    for (int32_t i = 0; i < n_sel; ++i) h_ties[i] = (int64_t)(gt[i] + eq[i]) > m ? 1 : 0;
+  if (out_st != ARA_OK) return out_st;
+  return ara_check(pf_, stream);
+}
+
+extern "C" ara_status ara_adjoint_accumulate(ara_portfolio* pf_, int64_t n_trials,
+                                             const int64_t* d_offsets, int64_t n_events,
+                                             const int32_t* d_ids, int32_t n_sel_in,
+                                             const int32_t* layer_sel, const double* d_ylt,
+                                             const uint8_t* d_regimes, double tvar_level,
+                                             const double* h_weights, double* d_g_elt_ret,
+                                             double* d_g_elt_lim, double* d_g_layer,
+                                             double* d_g_loss, void* stream) {
+  Portfolio* pf = static_cast<Portfolio*>(pf_);
+  if (!pf || !h_weights || !d_g_elt_ret || !d_g_elt_lim || !d_g_layer || !d_g_loss) return ARA_EINVAL;
+  std::vector<int32_t> sel;
+  if (n_sel_in == 0 && layer_sel == nullptr) {
+    for (int32_t l = 0; l < pf->n_layers; ++l) sel.push_back(l);
+  } else {
+    if (n_sel_in < 0 || !layer_sel) return ARA_EINVAL;
+    for (int32_t i = 0; i < n_sel_in; ++i) {
+      if (layer_sel[i] < 0 || layer_sel[i] >= pf->n_layers) return ARA_EINVAL;
+      sel.push_back(layer_sel[i]);
+    }
+  }
+  const int32_t n_sel = (int32_t)sel.size();
+  if (n_sel == 0) return ARA_OK;
+  int64_t K = 0, M = 0;
+  for (int32_t i = 0; i < n_sel; ++i)
+    for (int k = pf->layer_off[sel[i]]; k < pf->layer_off[sel[i] + 1]; ++k) {
+      const int j = pf->layer_elts[k];
+      M += pf->rec_off[j + 1] - pf->rec_off[j];
+      ++K;
+    }
+  DeviceGuard g(pf->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * (size_t)(2 * 2 * std::max<int64_t>(K, 1) + 2 * 4 * n_sel +
+                                                 2 * std::max<int64_t>(M, 1));
+  double* buf = nullptr;
+  ARA_TRY(cudaMallocAsync((void**)&buf, bytes, s));
+  double* ge = buf;
+  double* gl = ge + 2 * 2 * std::max<int64_t>(K, 1);
+  double* gx = gl + 2 * 4 * n_sel;
+  ara_status st = ara_adjoint(pf_, n_trials, d_offsets, n_events, d_ids, n_sel, sel.data(), d_ylt,
+                              d_regimes, tvar_level, ge, gl, gx, nullptr, stream);
+  int64_t slot0 = 0, base0 = 0;
+  for (int32_t i = 0; i < n_sel && st == ARA_OK; ++i) {
+    const int l = sel[i];
+    const LayerConst& lc = pf->layers[l];
+    AdjScatterParams sp{};
+    sp.w0 = h_weights[2 * i];
+    sp.w1 = h_weights[2 * i + 1];
+    sp.layer = l;
+    sp.n_slots = lc.elt_end - lc.elt_begin;
+    sp.gl0 = gl + 4 * i;
+    sp.gl1 = gl + 4 * (n_sel + i);
+    sp.ge0 = ge + 2 * slot0;
+    sp.ge1 = ge + 2 * (K + slot0);
+    sp.gx0 = gx;
+    sp.gx1 = gx + M;
+    sp.rec_off = pf->d_rec_off;
+    sp.rec_orig = pf->d_rec_orig;
+    sp.g_elt_ret = d_g_elt_ret;
+    sp.g_elt_lim = d_g_elt_lim;
+    sp.g_layer = d_g_layer;
+    sp.g_loss = d_g_loss;
+    int64_t b = base0;
+    for (int k = 0; k < sp.n_slots; ++k) {
+      const int j = pf->layer_elts[lc.elt_begin + k];
+      sp.elt[k] = j;
+      sp.base[k] = b;
+      b += pf->rec_off[j + 1] - pf->rec_off[j];
+    }
+    if (sp.n_slots > 0) {
+      LaunchScope ls(ARA_K_ADJOINT, s);
+      k_adj_scatter<<<dim3(8, sp.n_slots), 256, 0, s>>>(sp);
+      if (cudaGetLastError() != cudaSuccess) st = ARA_ECUDA;
+    }  // a layer without ELTs has S = 0 in every trial: all its gradients are 0
+    slot0 += sp.n_slots;
+    base0 = b;
+  }
+  cudaFreeAsync(buf, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && st == ARA_OK) st = ARA_ECUDA;
+  return st;
+}

@@ -12,8 +12,6 @@
 
 #include "ara_internal.cuh"
 
-struct ara_portfolio : public ara::Portfolio {};
-
 namespace ara {
 
 std::atomic<int64_t> g_launches{0};
@@ -123,22 +121,10 @@ static void layer_scale(Portfolio& pf, LayerConst& lc) {
   to_u128(lc.agg_lim * lc.scale, lc.agg_lim_lo, lc.agg_lim_hi);
 }
 
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 static void free_portfolio(ara_portfolio* p) {
   if (!p) return;
-  void* ptrs[] = {p->d_rec_off, p->d_rec_ids, p->d_rec_loss, p->d_rec_loss32, p->d_elt_ret,
-                  p->d_elt_lim, p->d_layer_elts, p->d_layers, p->d_dense, p->d_q, p->d_bits,
+  void* ptrs[] = {p->d_rec_off, p->d_rec_ids, p->d_rec_orig, p->d_rec_loss, p->d_rec_loss32, p->d_elt_ret,
+                  p->d_elt_lim, p->d_layer_elts, p->d_layers, p->d_dense, p->d_q, p->d_bits, p->d_cbits,
                   p->d_err, p->d_stage_ids[0], p->d_stage_ids[1], p->d_stage_off[0],
                   p->d_stage_off[1], p->d_ylt_full};
   for (void* q : ptrs)
@@ -274,6 +260,7 @@ ara_status ara_create_portfolio(int64_t C, int32_t n_elts, const int64_t* rec_of
   }
   // records sorted by event ID within each ELT; duplicates rejected
   std::vector<int32_t> ids_sorted((size_t)n_rec);
+  std::vector<int32_t> orig_pos((size_t)n_rec);
   std::vector<double> loss_sorted((size_t)n_rec);
   std::vector<double> max_loss((size_t)n_elts, 0.0);
   {
@@ -285,6 +272,7 @@ ara_status ara_create_portfolio(int64_t C, int32_t n_elts, const int64_t* rec_of
       std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return rec_ids[x] < rec_ids[y]; });
       for (int64_t i = 0; i < b - a; ++i) {
         ids_sorted[(size_t)(a + i)] = rec_ids[idx[(size_t)i]];
+        orig_pos[(size_t)(a + i)] = (int32_t)(idx[(size_t)i] - a);
         loss_sorted[(size_t)(a + i)] = rec_loss[idx[(size_t)i]];
         max_loss[(size_t)j] = std::max(max_loss[(size_t)j], rec_loss[idx[(size_t)i]]);
         if (i > 0 && ids_sorted[(size_t)(a + i)] == ids_sorted[(size_t)(a + i - 1)]) return ARA_EINVAL;
@@ -334,6 +322,7 @@ ara_status ara_create_portfolio(int64_t C, int32_t n_elts, const int64_t* rec_of
   ara_status st;
   if ((st = upload(&p->d_rec_off, rec_off, (size_t)n_elts + 1)) != ARA_OK) return fail(st);
   if ((st = upload(&p->d_rec_ids, ids_sorted.data(), (size_t)n_rec)) != ARA_OK) return fail(st);
+  if ((st = upload(&p->d_rec_orig, orig_pos.data(), (size_t)n_rec)) != ARA_OK) return fail(st);
   if (f32) {
     std::vector<float> l32(loss_sorted.begin(), loss_sorted.end());
     if ((st = upload(&p->d_rec_loss32, l32.data(), (size_t)n_rec)) != ARA_OK) return fail(st);
@@ -346,10 +335,12 @@ ara_status ara_create_portfolio(int64_t C, int32_t n_elts, const int64_t* rec_of
     return fail(st);
   if ((st = upload(&p->d_layers, p->layers.data(), p->layers.size())) != ARA_OK) return fail(st);
   p->bm_words = ((C + 31) / 32 + 3) / 4 * 4;
+  p->cbits_stride = (((C + 1) / 2 + 31) / 32 + 3) / 4 * 4;   // coarsest needed: 1 bit per 2 events
   if (n_layers > 0) {
     if (cudaMalloc(&p->d_q, sizeof(uint64_t) * (size_t)n_layers * C) != cudaSuccess) return fail(ARA_ENOMEM);
     if (cudaMalloc(&p->d_bits, 4 * (size_t)n_layers * p->bm_words) != cudaSuccess) return fail(ARA_ENOMEM);
     if (cudaMemset(p->d_bits, 0, 4 * (size_t)n_layers * p->bm_words) != cudaSuccess) return fail(ARA_ECUDA);
+    if (cudaMalloc(&p->d_cbits, 4 * (size_t)n_layers * p->cbits_stride) != cudaSuccess) return fail(ARA_ENOMEM);
   }
   if (cudaMalloc(&p->d_err, sizeof(uint32_t)) != cudaSuccess) return fail(ARA_ENOMEM);
   if (cudaMemset(p->d_err, 0, sizeof(uint32_t)) != cudaSuccess) return fail(ARA_ECUDA);

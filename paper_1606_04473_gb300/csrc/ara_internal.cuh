@@ -80,6 +80,7 @@ struct Portfolio {
   // device tables
   int64_t* d_rec_off = nullptr;     // [n_elts + 1]
   int32_t* d_rec_ids = nullptr;     // [n_records], sorted by event ID within each ELT
+  int32_t* d_rec_orig = nullptr;    // [n_records]: position of each sorted record in the order given
   double* d_rec_loss = nullptr;     // [n_records] (FP64 storage) or nullptr
   float* d_rec_loss32 = nullptr;    // [n_records] (FP32 storage) or nullptr
   double* d_elt_ret = nullptr;      // [n_elts]
@@ -91,6 +92,8 @@ struct Portfolio {
   uint64_t* d_q = nullptr;          // [n_layers][catalogue]: q(e) (or o(e) bits for F64_SUM)
   uint32_t* d_bits = nullptr;       // [n_layers][bm_words]: bit e set iff q(e) != 0
   int64_t bm_words = 0;             // words per layer (padded to a multiple of 4)
+  uint32_t* d_cbits = nullptr;      // [n_layers][cbits_stride]: coarse bitmap (1 bit / 2^k events)
+  int64_t cbits_stride = 0;
   uint32_t* d_err = nullptr;        // device error word
   // host-input pipeline resources (grown on demand)
   cudaStream_t copy_stream = nullptr;
@@ -142,10 +145,44 @@ void set_debug_extra_tx(uint32_t bytes);
 // Host check of risk-metric arguments (ranks within [1, n]); ARA_OK or ARA_EINVAL.
 ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t n_tvar,
                             const double* levels);
+// m = ceil(N (1 - p)) with the library's integer snapping; -1 when p is outside [0, 1).
+int64_t tail_count_snap(int64_t n, double p);
+// The m-th largest value of each of n_layers device rows: its order key (device, stride
+// thr_stride 64-bit words), #{y > v} and #{y == v} (device, one per layer).  Scratch from the
+// stream-ordered allocator; release with free_select_result.
+struct SelectResult {
+  void* scratch = nullptr;
+  const uint64_t* thr_key = nullptr;
+  int64_t thr_stride = 0;
+  const unsigned long long* gt = nullptr;
+  const unsigned long long* eq = nullptr;
+};
+ara_status select_one_rank(const double* d_ylt, int64_t n, int32_t n_layers, int64_t m, int n_sms,
+                           cudaStream_t s, SelectResult* out);
+void free_select_result(SelectResult& r, cudaStream_t s);
 // PML / TVaR of n_layers device YLT rows into host arrays (synchronises s); scratch from the
 // stream-ordered allocator.
 ara_status risk_metrics_device(const double* d_ylt, int64_t n, int32_t n_layers, int32_t n_rp,
                                const double* rps, int32_t n_tvar, const double* levels,
                                double* h_pml, double* h_tvar, double* h_mean, cudaStream_t s);
+
+}  // namespace ara
+
+// The opaque handle of the C ABI is the portfolio itself.
+struct ara_portfolio : public ara::Portfolio {};
+
+namespace ara {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 }  // namespace ara

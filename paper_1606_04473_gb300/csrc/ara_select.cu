@@ -273,6 +273,12 @@ ara_status select_targets(int64_t n, int32_t n_rp, const double* rps, int32_t n_
   return ARA_OK;
 }
 
+int64_t tail_count_snap(int64_t n, double p) {
+  if (!(p >= 0.0 && p < 1.0) || n < 1) return -1;
+  const int64_t m = ceil_snap((double)n * (1.0 - p));
+  return (m >= 1 && m <= n) ? m : -1;
+}
+
 ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t n_tvar,
                             const double* levels) {
   SelTargets tg;
@@ -308,6 +314,35 @@ ara_status launch_select(const double* d_ylt, int64_t n, int32_t n_layers, const
 using namespace ara;
 
 namespace ara {
+
+ara_status select_one_rank(const double* d_ylt, int64_t n, int32_t n_layers, int64_t m, int n_sms,
+                           cudaStream_t s, SelectResult* out) {
+  SelTargets tg;
+  tg.n_t = 1;
+  tg.n_rp = 0;
+  tg.rank[0] = m;
+  const int32_t blocks = select_blocks(n, n_sms, n_layers);
+  const size_t bytes = select_scratch_bytes(n_layers, 1, blocks);
+  void* scratch = nullptr;
+  ARA_TRY(cudaMallocAsync(&scratch, bytes, s));
+  SelScratch sc;
+  ara_status st = launch_select(d_ylt, n, n_layers, tg, scratch, bytes, blocks, 0, s, &sc);
+  if (st != ARA_OK) {
+    cudaFreeAsync(scratch, s);
+    return st;
+  }
+  out->scratch = scratch;
+  out->thr_key = &sc.state[0].prefix;
+  out->thr_stride = sizeof(SelState) / sizeof(uint64_t);
+  out->gt = sc.gt;
+  out->eq = sc.eq;
+  return ARA_OK;
+}
+
+void free_select_result(SelectResult& r, cudaStream_t s) {
+  if (r.scratch) cudaFreeAsync(r.scratch, s);
+  r.scratch = nullptr;
+}
 
 ara_status risk_metrics_device(const double* d_ylt, int64_t n_trials, int32_t n_layers,
                                int32_t n_rp, const double* rps, int32_t n_tvar,

@@ -8,6 +8,7 @@
 // (k_fold), then streams the YET with one table gather per occurrence whose o(e) is non-zero
 // (k_ylt_folded).  k_ylt_per_elt keeps the literal per-occurrence, per-ELT lookups.
 
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 
@@ -147,6 +148,10 @@ template <typename Acc> struct AccOps;
 template <> struct AccOps<U128> {
   static __device__ __forceinline__ U128 zero() { return U128{0ull, 0ull}; }
   static __device__ __forceinline__ void add(U128& a, uint64_t v) { add_u64(a, v); }
+  // add the sum of up to 8 table values (each < 2^61, so their u64 sum cannot wrap)
+  static __device__ __forceinline__ void add_partial(U128& a, uint64_t part, const uint64_t (&)[8]) {
+    add_u64(a, part);
+  }
   static __device__ __forceinline__ U128 warp_sum(U128 a) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -178,6 +183,10 @@ template <> struct AccOps<double> {
   static __device__ __forceinline__ double zero() { return 0.0; }
   static __device__ __forceinline__ void add(double& a, uint64_t v) {
     a = __dadd_rn(a, __longlong_as_double((long long)v));
+  }
+  static __device__ __forceinline__ void add_partial(double& a, uint64_t, const uint64_t (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a = __dadd_rn(a, __longlong_as_double((long long)v[i]));
   }
   static __device__ __forceinline__ double warp_sum(double a) {
 #pragma unroll
@@ -403,17 +412,94 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
-// Warp-uniform cursor over the trials of one warp.
+// Coarse hit bitmap of a layer, built once per run when the exact one does not fit in shared
+// memory: coarse bit b = OR of the exact bits of events [b << shift, (b + 1) << shift).
+__global__ void k_coarsen(const uint32_t* __restrict__ exact, int64_t n_exact, int shift,
+                          uint32_t* __restrict__ coarse, int64_t n_coarse) {
+  for (int64_t cw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cw < n_coarse;
+       cw += (int64_t)gridDim.x * blockDim.x)
+    coarse[cw] = coarsen_word(exact, cw, shift, n_exact);
+}
+
+// State of one warp's walk over its trials (all fields warp-uniform except acc/res, which are
+// per-lane partial sums).  Positions and trial numbers are relative to the warp's range.
 template <typename Acc>
-struct TrialCursor {
-  int64_t t, t_hi, group_base;
-  int64_t end;          // event position (relative) where trial t ends
-  int64_t E0, E1;
-  int64_t next_off;     // lane i holds offset of trial (buf_base + i) end, i.e. offsets[buf_base+1+i]
-  int64_t buf_base;     // trial index whose end is in lane 0 of next_off
-  Acc acc, res;
+struct Walk {
+  int32_t k;        // current trial, relative to t_lo
+  int32_t nk;       // number of trials of the warp
+  int32_t end;      // relative end position of trial k
+  int32_t span;     // E1 - E0
+  int32_t gbase;    // first trial of the current group of 32
+  int32_t bbase;    // trial whose end is in lane 0 of nxt
+  int32_t nxt;      // lane i: relative end of trial bbase + i
   bool bad;
+  Acc acc, res;
 };
+
+template <typename Acc>
+__device__ __forceinline__ void walk_load_ends(Walk<Acc>& w, const StreamParams& p, int64_t t_lo,
+                                               int64_t base_abs, int lane) {
+  const int64_t t = t_lo + w.bbase + 1 + lane;       // trial end index into offsets
+  int32_t v = w.span;
+  if (w.bbase + 1 + lane <= w.nk) {
+    const int64_t rel = __ldg(p.offsets + t) - base_abs;
+    v = (rel < 0 || rel > w.span) ? -1 : (int32_t)rel;
+  }
+  w.nxt = v;
+}
+
+// Finish trial k: reduce the lanes' partial sums, park the sum in lane (k - gbase), flush a
+// full group of 32 (aggregate terms for all of them at once), move to trial k + 1.
+template <typename Acc>
+__device__ __forceinline__ void walk_finish(Walk<Acc>& w, const StreamParams& p, const LayerConst& lc,
+                                         int64_t t_lo, int64_t base_abs, int lane) {
+  const Acc r = AccOps<Acc>::warp_sum(w.acc);
+  if (lane == w.k - w.gbase) w.res = r;
+  w.acc = AccOps<Acc>::zero();
+  const int32_t prev = w.end;
+  ++w.k;
+  if (w.k - w.gbase == 32 || w.k == w.nk) {
+    if (w.gbase + lane < w.k) {
+      uint8_t reg;
+      const double y = AccOps<Acc>::finish(w.res, lc, reg);
+      p.ylt[t_lo + w.gbase + lane] = y;
+      if (p.regimes) p.regimes[t_lo + w.gbase + lane] = reg;
+    }
+    w.res = AccOps<Acc>::zero();
+    w.gbase = w.k;
+  }
+  if (w.k < w.nk) {
+    if (w.k - w.bbase == 32) {
+      w.bbase = w.k;
+      walk_load_ends(w, p, t_lo, base_abs, lane);
+    }
+    w.end = __shfl_sync(FULL, w.nxt, w.k - w.bbase);
+    if (w.end < prev) {          // out of [0, span] (-1) or decreasing: bad offsets
+      w.bad = true;
+      w.end = w.span;
+    }
+  }
+}
+
+// Slow path: attribute values at relative positions pos[i] (< 0: none) of the window
+// [rb, re) to trials, finishing every trial that ends inside the window.
+template <typename Acc, int K>
+__device__ __forceinline__ void walk_window(Walk<Acc>& w, const StreamParams& p, const LayerConst& lc,
+                                            int64_t t_lo, int64_t base_abs, int lane, int32_t rb,
+                                            int32_t re, const int32_t (&pos)[K],
+                                            const uint64_t (&val)[K]) {
+  int32_t done = rb;
+  while (true) {
+    while (w.k < w.nk && w.end <= done) walk_finish(w, p, lc, t_lo, base_abs, lane);
+    if (w.k >= w.nk) return;
+    const int32_t seg = min(w.end, re);
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (pos[i] >= done && pos[i] < seg) AccOps<Acc>::add(w.acc, val[i]);
+    done = seg;
+    if (done >= re) return;
+  }
+}
 
 template <bool FILTER, typename Acc, int BK_WARPS, int BK_STAGES>
 __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
@@ -427,9 +513,12 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
                    wid * BK_STAGES;
   if (lane == 0)
     for (int s = 0; s < BK_STAGES; ++s) mbar_init(&bars[s], 1);
-  if (FILTER)
-    for (int64_t cw = threadIdx.x; cw < p.smem_words; cw += blockDim.x)
-      bm[cw] = coarsen_word(p.bits, cw, p.shift, p.bm_words);
+  if (FILTER) {  // the layer's (coarse) hit bitmap, 16 bytes per thread per step
+    const uint4* src = reinterpret_cast<const uint4*>(p.bits);
+    uint4* dst = reinterpret_cast<uint4*>(bm);
+    const int64_t n16 = (p.smem_words + 3) / 4;   // source padded to whole 16-byte words
+    for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
   if (lane == 0) fence_mbar_init();
   __syncthreads();
 
@@ -439,151 +528,122 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
   if (t_lo >= t_hi) return;
   const LayerConst lc = *p.layer;
   const uint64_t* __restrict__ q = p.q;
-  bool bad_id = false;
+  const uint32_t cat = (uint32_t)p.catalogue;
+  const int shift = p.shift;
 
-  TrialCursor<Acc> c;
-  c.t = t_lo;
-  c.t_hi = t_hi;
-  c.group_base = t_lo;
-  c.E0 = __ldg(p.offsets + t_lo) - p.id_base;
-  c.E1 = __ldg(p.offsets + t_hi) - p.id_base;
-  c.acc = AccOps<Acc>::zero();
-  c.res = AccOps<Acc>::zero();
-  c.bad = !(0 <= c.E0 && c.E0 <= c.E1 && c.E1 <= p.n_events);
-  if (c.bad) {
+  const int64_t E0 = __ldg(p.offsets + t_lo) - p.id_base;
+  const int64_t E1 = __ldg(p.offsets + t_hi) - p.id_base;
+  if (!(0 <= E0 && E0 <= E1 && E1 <= p.n_events && E1 - E0 < ((int64_t)1 << 31))) {
     if (lane == 0) atomicOr(p.err, DERR_OFFSETS);
     return;
   }
-  c.buf_base = t_lo;
-  c.next_off = (t_lo + 1 + lane <= t_hi) ? __ldg(p.offsets + t_lo + 1 + lane) - p.id_base : c.E1;
-  c.end = __shfl_sync(FULL, c.next_off, 0);
-  if (c.end < c.E0 || c.end > c.E1) {
-    c.bad = true;
-    c.end = c.E1;
-  }
+  const int64_t base_abs = E0 + p.id_base;          // absolute offset of relative position 0
+  Walk<Acc> w;
+  w.k = 0;
+  w.nk = (int32_t)(t_hi - t_lo);
+  w.span = (int32_t)(E1 - E0);
+  w.gbase = 0;
+  w.bbase = 0;
+  w.bad = false;
+  w.acc = AccOps<Acc>::zero();
+  w.res = AccOps<Acc>::zero();
+  walk_load_ends(w, p, t_lo, base_abs, lane);
+  w.end = __shfl_sync(FULL, w.nxt, 0);
+  if (w.end < 0) { w.bad = true; w.end = w.span; }
+  bool bad_id = false;
 
-  // Finish the current trial: reduce, park in its slot, flush a full group, move on.
-  auto advance = [&]() {
-    const Acc r = AccOps<Acc>::warp_sum(c.acc);
-    if (lane == (int)(c.t - c.group_base)) c.res = r;
-    c.acc = AccOps<Acc>::zero();
-    const int64_t prev_end = c.end;
-    ++c.t;
-    if (c.t - c.group_base == 32 || c.t == c.t_hi) {
-      if (c.group_base + lane < c.t) {
-        uint8_t reg;
-        const double y = AccOps<Acc>::finish(c.res, lc, reg);
-        p.ylt[c.group_base + lane] = y;
-        if (p.regimes) p.regimes[c.group_base + lane] = reg;
-      }
-      c.res = AccOps<Acc>::zero();
-      c.group_base = c.t;
-    }
-    if (c.t < c.t_hi) {
-      if (c.t - c.buf_base == 32) {
-        c.buf_base = c.t;
-        c.next_off = (c.t + 1 + lane <= c.t_hi) ? __ldg(p.offsets + c.t + 1 + lane) - p.id_base : c.E1;
-      }
-      c.end = __shfl_sync(FULL, c.next_off, (int)(c.t - c.buf_base));
-      if (c.end < prev_end || c.end > c.E1) {  // offsets not monotone inside [E0, E1]
-        c.bad = true;
-        c.end = c.E1;
-      }
-    }
-  };
-  // Attribute the values of positions [pos0, pos0 + cnt) (lane = position - pos0, cnt <= 32)
-  // to trials.
-  auto attribute = [&](int64_t pos0, int64_t cnt, uint64_t v) {
-    int64_t done = pos0;
-    const int64_t stop = pos0 + cnt;
-    while (true) {
-      while (c.t < c.t_hi && c.end <= done) advance();
-      if (c.t >= c.t_hi) return;
-      const int64_t seg = min(c.end, stop);
-      const int64_t mypos = pos0 + lane;
-      if (mypos >= done && mypos < seg && v) AccOps<Acc>::add(c.acc, v);
-      done = seg;
-      if (done >= stop) return;
-    }
-  };
-  auto value_of_id = [&](int e, bool valid) -> uint64_t {
-    if (!valid) return 0ull;
-    if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; return 0ull; }
+  // value of one event ID: the table entry when the event is in the catalogue and hits
+  auto val_of = [&](int e, bool valid) -> uint64_t {
+    const bool in = (uint32_t)e < cat;
+    bad_id |= valid && !in;
+    bool hit = valid && in;
     if (FILTER) {
-      const uint32_t b = (uint32_t)e >> p.shift;
-      if (!((bm[b >> 5] >> (b & 31)) & 1u)) return 0ull;
+      const uint32_t b = (uint32_t)(in ? e : 0) >> shift;
+      hit = hit && ((bm[b >> 5] >> (b & 31)) & 1u);
     }
-    return __ldg(q + e);
+    uint64_t v = 0;
+    if (hit) v = __ldg(q + e);
+    return v;
   };
 
-  // Frame positions: element i lives at frame position i + mis; 16-byte aligned vectors are
-  // frame positions [4v, 4v + 4).
-  const int64_t fa = c.E0 + p.mis, fb = c.E1 + p.mis;
-  int64_t body0 = ((fa + 3) >> 2) << 2, body1 = (fb >> 2) << 2;  // frame
-  if (body0 > body1) body0 = body1 = fb;                            // no aligned body
-  const int64_t head_end = body0 - p.mis;                           // element index
-  const int64_t tail_begin = body1 - p.mis;
-  // head: elements [E0, head_end) (< 4 when a body exists, else the whole range, < 8)
-  if (head_end > c.E0) {
-    const int64_t pos = c.E0 + lane;
-    const bool valid = pos < head_end;
-    const int e = valid ? __ldg(p.ids + pos) : 0;
-    attribute(c.E0, head_end - c.E0, value_of_id(e, valid));
+  // Frame: element i at frame position i + mis; 16-byte vectors at frame multiples of 4.
+  const int32_t mis_head = (int32_t)((4 - ((E0 + p.mis) & 3)) & 3);
+  const int32_t head = min(mis_head, w.span);
+  const int32_t n_body = ((w.span - head) >> 2) << 2;
+  const int32_t tail0 = head + n_body;
+  // head and tail (< 4 IDs each): scalar loads, slow path
+  if (head > 0) {
+    int32_t pos[1] = {lane < head ? lane : -1};
+    uint64_t val[1] = {val_of(lane < head ? __ldg(p.ids + E0 + lane) : 0, lane < head)};
+    walk_window<Acc, 1>(w, p, lc, t_lo, base_abs, lane, 0, head, pos, val);
   }
-  // body: frame [body0, body1) in chunks of BK_CHUNK_IDS
-  const int64_t n_body = body1 - body0;
-  const int64_t n_chunks = (n_body + BK_CHUNK_IDS - 1) / BK_CHUNK_IDS;
-  const int32_t* gbase = p.ids + (body0 - p.mis);                   // 16-byte aligned
+  const int32_t n_chunks = (n_body + BK_CHUNK_IDS - 1) / BK_CHUNK_IDS;
+  const int32_t* gbase = p.ids + E0 + head;          // 16-byte aligned
   const uint64_t pol = l2_evict_first_policy();
-  auto issue = [&](int64_t ch) {
-    const int s = (int)(ch % BK_STAGES);
-    const int64_t n = min((int64_t)BK_CHUNK_IDS, n_body - ch * BK_CHUNK_IDS);
-    const uint32_t bytes = (uint32_t)(n * 4);
-    fence_proxy_async_smem();
-    mbar_expect_tx(&bars[s], bytes + p.debug_extra_tx);
-    bulk_g2s(ring + s * BK_CHUNK_IDS, gbase + ch * BK_CHUNK_IDS, bytes, &bars[s], pol);
-  };
   if (lane == 0)
-    for (int64_t ch = 0; ch < min((int64_t)BK_STAGES, n_chunks); ++ch) issue(ch);
+    for (int32_t ch = 0; ch < min(BK_STAGES, n_chunks); ++ch) {
+      const int32_t n = min(BK_CHUNK_IDS, n_body - ch * BK_CHUNK_IDS);
+      fence_proxy_async_smem();
+      mbar_expect_tx(&bars[ch], (uint32_t)n * 4 + p.debug_extra_tx);
+      bulk_g2s(ring + ch * BK_CHUNK_IDS, gbase + ch * BK_CHUNK_IDS, (uint32_t)n * 4, &bars[ch], pol);
+    }
   __syncwarp();
-  int64_t timed_out_at = -1;
-  for (int64_t ch = 0; ch < n_chunks; ++ch) {
-    const int s = (int)(ch % BK_STAGES);
+  int32_t timed_out_at = -1;
+  for (int32_t ch = 0; ch < n_chunks; ++ch) {
+    const int s = ch % BK_STAGES;
     const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((ch / BK_STAGES) & 1), p.wait_limit_ns);
     if (__any_sync(FULL, !ok)) { timed_out_at = ch; break; }
-    const int64_t base = head_end + ch * BK_CHUNK_IDS;              // element index of slot 0
-    const int64_t n = min((int64_t)BK_CHUNK_IDS, n_body - ch * BK_CHUNK_IDS);
-    int ids[BK_STEPS];
-#pragma unroll
-    for (int k = 0; k < BK_STEPS; ++k) ids[k] = ring[s * BK_CHUNK_IDS + k * 32 + lane];
+    const int32_t rb = head + ch * BK_CHUNK_IDS;
+    const int32_t n = min(BK_CHUNK_IDS, n_body - ch * BK_CHUNK_IDS);
+    // lane l holds chunk slots 4l..4l+3 and 128+4l..128+4l+3 (two conflict-free 16-byte loads)
+    const int4 a = reinterpret_cast<const int4*>(ring + s * BK_CHUNK_IDS)[lane];
+    const int4 b = reinterpret_cast<const int4*>(ring + s * BK_CHUNK_IDS)[32 + lane];
     __syncwarp();
-    if (lane == 0 && ch + BK_STAGES < n_chunks) issue(ch + BK_STAGES);
-    uint64_t v[BK_STEPS];
-#pragma unroll
-    for (int k = 0; k < BK_STEPS; ++k) v[k] = value_of_id(ids[k], k * 32 + lane < n);
-#pragma unroll
-    for (int k = 0; k < BK_STEPS; ++k)
-      if (k * 32 < n) attribute(base + k * 32, min((int64_t)32, n - k * 32), v[k]);
+    if (lane == 0 && ch + BK_STAGES < n_chunks) {
+      const int32_t c2 = ch + BK_STAGES;
+      const int32_t n2 = min(BK_CHUNK_IDS, n_body - c2 * BK_CHUNK_IDS);
+      fence_proxy_async_smem();
+      mbar_expect_tx(&bars[s], (uint32_t)n2 * 4 + p.debug_extra_tx);
+      bulk_g2s(ring + s * BK_CHUNK_IDS, gbase + c2 * BK_CHUNK_IDS, (uint32_t)n2 * 4, &bars[s], pol);
+    }
+    const int sa = 4 * lane, sb = 128 + 4 * lane;
+    uint64_t v[8];
+    v[0] = val_of(a.x, sa + 0 < n);
+    v[1] = val_of(a.y, sa + 1 < n);
+    v[2] = val_of(a.z, sa + 2 < n);
+    v[3] = val_of(a.w, sa + 3 < n);
+    v[4] = val_of(b.x, sb + 0 < n);
+    v[5] = val_of(b.y, sb + 1 < n);
+    v[6] = val_of(b.z, sb + 2 < n);
+    v[7] = val_of(b.w, sb + 3 < n);
+    while (w.k < w.nk && w.end <= rb) walk_finish(w, p, lc, t_lo, base_abs, lane);
+    if (w.k < w.nk && w.end >= rb + n) {
+      // fast path: the whole chunk belongs to the current trial (sum of <= 8 values < 2^64)
+      const uint64_t part = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+      AccOps<Acc>::add_partial(w.acc, part, v);
+    } else {
+      int32_t pos[8] = {rb + sa, rb + sa + 1, rb + sa + 2, rb + sa + 3,
+                        rb + sb, rb + sb + 1, rb + sb + 2, rb + sb + 3};
+      walk_window<Acc, 8>(w, p, lc, t_lo, base_abs, lane, rb, rb + n, pos, v);
+    }
   }
   if (timed_out_at >= 0) {
-    // Chunks timed_out_at .. timed_out_at + BK_STAGES - 1 may still be in flight: wait for
-    // them (bounded) before leaving, then give up on the range.
-    for (int64_t ch = timed_out_at; ch < min(timed_out_at + BK_STAGES, n_chunks); ++ch)
+    // chunks timed_out_at .. timed_out_at + BK_STAGES - 1 may still be in flight: wait for
+    // them (bounded) before leaving; the range is abandoned.
+    for (int32_t ch = timed_out_at; ch < min(timed_out_at + BK_STAGES, n_chunks); ++ch)
       mbar_wait_bounded(&bars[ch % BK_STAGES], (uint32_t)((ch / BK_STAGES) & 1), p.wait_limit_ns);
     if (lane == 0) atomicOr(p.err, DERR_TIMEOUT);
     return;
   }
-  // tail: elements [tail_begin, E1)
-  if (tail_begin < c.E1) {
-    const int64_t pos = tail_begin + lane;
-    const bool valid = pos < c.E1;
-    const int e = valid ? __ldg(p.ids + pos) : 0;
-    attribute(tail_begin, c.E1 - tail_begin, value_of_id(e, valid));
+  if (tail0 < w.span) {
+    const int32_t nt = w.span - tail0;
+    int32_t pos[1] = {lane < nt ? tail0 + lane : -1};
+    uint64_t val[1] = {val_of(lane < nt ? __ldg(p.ids + E0 + tail0 + lane) : 0, lane < nt)};
+    walk_window<Acc, 1>(w, p, lc, t_lo, base_abs, lane, tail0, w.span, pos, val);
   }
-  // finish the remaining trials (the last one, and trailing empty ones)
-  while (c.t < c.t_hi) advance();
+  while (w.k < w.nk) walk_finish(w, p, lc, t_lo, base_abs, lane);
   if (bad_id) atomicOr(p.err, DERR_EVENT_RANGE);
-  if (lane == 0 && c.bad) atomicOr(p.err, DERR_OFFSETS);
+  if (lane == 0 && w.bad) atomicOr(p.err, DERR_OFFSETS);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -835,6 +895,8 @@ ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   sp.smem_words = coarse_words(pf.catalogue, sp.shift);
   sp.bm_words = pf.bm_words;
   sp.err = pf.d_err;
+  // the bulk kernel copies a ready bitmap: exact when it fits, else the coarse one built here
+  const int64_t cwords_pad = (sp.smem_words + 3) / 4 * 4;
   sp.wait_limit_ns = g_wait_limit_ns.load();
   sp.debug_extra_tx = g_debug_extra_tx.load();
   const bool per_elt = (a.flags & ARA_RUN_PER_ELT) != 0;
@@ -845,6 +907,15 @@ ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
     sp.q = pf.d_q + (int64_t)layer * pf.catalogue;
     sp.bits = pf.d_bits + (int64_t)layer * pf.bm_words;
     sp.layer = pf.d_layers + layer;
+    if (!ldg && !per_elt && !nof && sp.shift > 0 && a.n_trials > 0) {
+      uint32_t* cb = pf.d_cbits + (int64_t)layer * pf.cbits_stride;
+      if (cwords_pad > pf.cbits_stride) return ARA_EINVAL;
+      LaunchScope ls(ARA_K_FOLD, s);
+      k_coarsen<<<(unsigned)std::min<int64_t>((cwords_pad + 255) / 256, 4096), 256, 0, s>>>(
+          pf.d_bits + (int64_t)layer * pf.bm_words, pf.bm_words, sp.shift, cb, cwords_pad);
+      ARA_TRY(cudaGetLastError());
+      sp.bits = cb;
+    }
     sp.ylt = a.ylt + (int64_t)i * a.row_stride;
     sp.regimes = a.regimes ? a.regimes + (int64_t)i * a.row_stride : nullptr;
     if (a.n_trials == 0) continue;
