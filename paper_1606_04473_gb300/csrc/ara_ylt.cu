@@ -355,7 +355,6 @@ __global__ void __launch_bounds__(YLT_THREADS, 1) k_ylt_folded(StreamParams p) {
 // its own copies still in flight, and returns.
 // ------------------------------------------------------------------------------------------
 constexpr int BK_CHUNK_IDS = 256;                      // 1 KiB per stage
-constexpr int BK_STEPS = BK_CHUNK_IDS / 32;
 
 template <int WARPS, int STAGES> struct BulkShape {
   static constexpr int ring_bytes = WARPS * STAGES * BK_CHUNK_IDS * 4;
@@ -419,6 +418,26 @@ __global__ void k_coarsen(const uint32_t* __restrict__ exact, int64_t n_exact, i
   for (int64_t cw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cw < n_coarse;
        cw += (int64_t)gridDim.x * blockDim.x)
     coarse[cw] = coarsen_word(exact, cw, shift, n_exact);
+}
+
+// Table value of one event for the bulk stream: the event index is clamped into the catalogue
+// for addressing (an out-of-range ID is caught through emax, which makes the whole run a data
+// error), the hit bit comes from the shared-memory bitmap, and the gather is predicated.
+template <bool FILTER>
+__device__ __forceinline__ uint64_t bulk_value(int e, uint32_t cat1, int shift, const uint32_t* bm,
+                                               const uint64_t* __restrict__ q, uint32_t& emax) {
+  const uint32_t ue = (uint32_t)e;
+  emax = max(emax, ue);
+  const uint32_t ce = min(ue, cat1);
+  uint32_t hit = 1u;
+  if (FILTER) {
+    const uint32_t b = ce >> shift;
+    hit = __funnelshift_r(bm[b >> 5], 0u, b) & 1u;   // bit (b mod 32) of the word
+  }
+  uint64_t v = 0;
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p ld.global.nc.u64 %0, [%1];\n\t}"
+      : "+l"(v) : "l"(q + ce), "r"(hit));
+  return v;
 }
 
 // State of one warp's walk over its trials (all fields warp-uniform except acc/res, which are
@@ -550,20 +569,10 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
   walk_load_ends(w, p, t_lo, base_abs, lane);
   w.end = __shfl_sync(FULL, w.nxt, 0);
   if (w.end < 0) { w.bad = true; w.end = w.span; }
-  bool bad_id = false;
-
-  // value of one event ID: the table entry when the event is in the catalogue and hits
+  uint32_t emax = 0;                 // largest event ID seen (as unsigned): >= catalogue is an error
+  const uint32_t cat1 = cat - 1u;
   auto val_of = [&](int e, bool valid) -> uint64_t {
-    const bool in = (uint32_t)e < cat;
-    bad_id |= valid && !in;
-    bool hit = valid && in;
-    if (FILTER) {
-      const uint32_t b = (uint32_t)(in ? e : 0) >> shift;
-      hit = hit && ((bm[b >> 5] >> (b & 31)) & 1u);
-    }
-    uint64_t v = 0;
-    if (hit) v = __ldg(q + e);
-    return v;
+    return valid ? bulk_value<FILTER>(e, cat1, shift, bm, q, emax) : 0ull;
   };
 
   // Frame: element i at frame position i + mis; 16-byte vectors at frame multiples of 4.
@@ -608,14 +617,25 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
     }
     const int sa = 4 * lane, sb = 128 + 4 * lane;
     uint64_t v[8];
-    v[0] = val_of(a.x, sa + 0 < n);
-    v[1] = val_of(a.y, sa + 1 < n);
-    v[2] = val_of(a.z, sa + 2 < n);
-    v[3] = val_of(a.w, sa + 3 < n);
-    v[4] = val_of(b.x, sb + 0 < n);
-    v[5] = val_of(b.y, sb + 1 < n);
-    v[6] = val_of(b.z, sb + 2 < n);
-    v[7] = val_of(b.w, sb + 3 < n);
+    if (n == BK_CHUNK_IDS) {        // full chunk: every slot is a real event
+      v[0] = bulk_value<FILTER>(a.x, cat1, shift, bm, q, emax);
+      v[1] = bulk_value<FILTER>(a.y, cat1, shift, bm, q, emax);
+      v[2] = bulk_value<FILTER>(a.z, cat1, shift, bm, q, emax);
+      v[3] = bulk_value<FILTER>(a.w, cat1, shift, bm, q, emax);
+      v[4] = bulk_value<FILTER>(b.x, cat1, shift, bm, q, emax);
+      v[5] = bulk_value<FILTER>(b.y, cat1, shift, bm, q, emax);
+      v[6] = bulk_value<FILTER>(b.z, cat1, shift, bm, q, emax);
+      v[7] = bulk_value<FILTER>(b.w, cat1, shift, bm, q, emax);
+    } else {
+      v[0] = val_of(a.x, sa + 0 < n);
+      v[1] = val_of(a.y, sa + 1 < n);
+      v[2] = val_of(a.z, sa + 2 < n);
+      v[3] = val_of(a.w, sa + 3 < n);
+      v[4] = val_of(b.x, sb + 0 < n);
+      v[5] = val_of(b.y, sb + 1 < n);
+      v[6] = val_of(b.z, sb + 2 < n);
+      v[7] = val_of(b.w, sb + 3 < n);
+    }
     while (w.k < w.nk && w.end <= rb) walk_finish(w, p, lc, t_lo, base_abs, lane);
     if (w.k < w.nk && w.end >= rb + n) {
       // fast path: the whole chunk belongs to the current trial (sum of <= 8 values < 2^64)
@@ -642,7 +662,7 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
     walk_window<Acc, 1>(w, p, lc, t_lo, base_abs, lane, tail0, w.span, pos, val);
   }
   while (w.k < w.nk) walk_finish(w, p, lc, t_lo, base_abs, lane);
-  if (bad_id) atomicOr(p.err, DERR_EVENT_RANGE);
+  if (emax >= cat) atomicOr(p.err, DERR_EVENT_RANGE);
   if (lane == 0 && w.bad) atomicOr(p.err, DERR_OFFSETS);
 }
 

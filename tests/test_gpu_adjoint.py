@@ -1,0 +1,202 @@
+"""GPU adjoint (ara_adjoint, ara_adjoint_accumulate, the autograd Function) against the FP64
+oracle's chain-rule gradient and against central finite differences of the GPU forward.
+
+Required tolerance: 1e-4 relative on adjoints against FP64.  The device keeps every sum as an
+exact integer count, so agreement is at rounding level wherever the clamp regimes of the two
+sides agree; the cases are checked to keep every aggregate loss away from the aggregate kinks
+and TVaR's boundary trial separated from its neighbour, where the gradient is not defined."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_1606_04473_gb300 as ara
+    from paper_1606_04473_gb300.autograd import LayerRisk
+
+RTOL, LEVEL = 1e-4, 0.9
+
+
+def dev(yet):
+    return (torch.from_numpy(np.ascontiguousarray(yet.offsets)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(yet.event_ids)).cuda())
+
+
+def case(seed, catalogue=100_000, n_elts=10, nnz=3000, n_layers=3, n_trials=3000, lam=400.0):
+    rng = np.random.default_rng(seed)
+    ids, losses = synth.make_elts(seed, n_elts, nnz, catalogue, 11.0, 2.0, f32=True)
+    r, l = synth.percentile_terms(losses)
+    layers = [sorted(rng.choice(n_elts, size=int(rng.integers(2, n_elts + 1)), replace=False).tolist())
+              for _ in range(n_layers)]
+    counts = synth.poisson_counts(seed, lam, n_trials)
+    counts[:3] = [0, 1, 5]
+    yet = synth.make_yet(seed, counts, catalogue, with_timestamps=False)
+    z = np.zeros(n_layers)
+    pf = synth.Portfolio(catalogue, ids, losses, r, l, layers, z, z, z, z, losses_f32=True)
+    from oracle.derive_terms import derive
+    t = derive(pf, synth.YET(yet.offsets[:1001], yet.event_ids[:int(yet.offsets[1000])]), 20.0, 80.0)
+    return pf.with_terms(t), yet
+
+
+def well_posed(pf, yet, level):
+    y, agg = oracle.ylt(pf, yet, return_agg=True)
+    for l in range(pf.n_layers):
+        for kink in (pf.agg_ret[l], pf.agg_ret[l] + pf.agg_lim[l]):
+            if np.any(np.abs(agg[l] - kink) <= 1e-9 * np.maximum(np.abs(agg[l]), 1.0)):
+                return False
+        m = oracle.tail_count(yet.n_trials, level)
+        ys = np.sort(y[l])[::-1]
+        if m < ys.size and ys[m - 1] > 0 and abs(ys[m - 1] - ys[m]) <= 1e-9 * ys[m - 1]:
+            return False
+    return True
+
+
+def forward(g, yet):
+    off, ids = dev(yet)
+    reg = torch.empty((g.n_layers, yet.n_trials), dtype=torch.uint8, device="cuda")
+    y = g.run_ylt(off, ids, regimes=reg)
+    g.check()
+    return off, ids, y, reg
+
+
+def close(got, want, scale):
+    got, want = np.asarray(got), np.asarray(want)
+    np.testing.assert_allclose(got, want, rtol=RTOL, atol=1e-12 * scale)
+
+
+@pytest.fixture(scope="module")
+def mid():
+    pf, yet = case(21)
+    assert well_posed(pf, yet, LEVEL)
+    return pf, yet
+
+
+@pytest.mark.parametrize("obj", [0, 1])
+def test_adjoint_matches_fp64_reference(mid, obj):
+    pf, yet = mid
+    g = ara.Portfolio.from_tables(pf)
+    off, ids, y, reg = forward(g, yet)
+    gr = g.adjoint(off, ids, y, reg, LEVEL)
+    ref = oracle.adjoint(pf, yet, "mean" if obj == 0 else "tvar", LEVEL)
+    scale = max(1.0, float(np.abs(ref["loss"]).max()))
+    close(gr["elt"][obj].cpu().numpy(), ref["elt"], 1.0)
+    close(gr["layer"][obj].cpu().numpy(), ref["layer"], 1.0)
+    close(gr["loss"][obj].cpu().numpy(), ref["loss"], scale)
+    assert gr["ties"].tolist() == [0] * pf.n_layers
+    # the gradients are not trivially zero: every kind of term is exercised
+    assert np.any(ref["elt"][:, 0] != 0) and np.any(ref["layer"][:, 0] != 0)
+    assert np.any(ref["layer"][:, 2] != 0) and np.count_nonzero(ref["loss"]) > 100
+
+
+def test_adjoint_layer_subset_and_repeat(mid):
+    pf, yet = mid
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    sel = [2, 0]
+    reg = torch.empty((2, yet.n_trials), dtype=torch.uint8, device="cuda")
+    y = g.run_ylt(off, ids, layers=sel, regimes=reg)
+    a = g.adjoint(off, ids, y, reg, LEVEL, layers=sel)
+    b = g.adjoint(off, ids, y, reg, LEVEL, layers=sel)
+    for k in ("elt", "layer", "loss"):
+        assert torch.equal(a[k], b[k])                      # deterministic
+    sub = pf.with_terms(pf.terms_dict())
+    sub.layer_elts = [pf.layer_elts[i] for i in sel]
+    for name in ["occ_ret", "occ_lim", "agg_ret", "agg_lim"]:
+        setattr(sub, name, getattr(pf, name)[sel])
+    ref = oracle.adjoint(sub, yet, "mean", LEVEL)
+    close(a["layer"][0].cpu().numpy(), ref["layer"], 1.0)
+    close(a["elt"][0].cpu().numpy(), ref["elt"], 1.0)
+
+
+def test_accumulate_and_autograd_match_weighted_reference(mid):
+    pf, yet = mid
+    off, ids = dev(yet)
+    P = lambda a: torch.tensor(np.asarray(a, dtype=np.float64), device="cuda", requires_grad=True)
+    params = [P(pf.elt_ret), P(pf.elt_lim), P(pf.occ_ret), P(pf.occ_lim), P(pf.agg_ret),
+              P(pf.agg_lim), P(np.concatenate(pf.elt_losses))]
+    risk = LayerRisk.apply(*params, pf, off, ids, LEVEL)
+    w = torch.tensor(np.random.default_rng(3).normal(size=(pf.n_layers, 2)), device="cuda")
+    (risk * w).sum().backward()
+    # forward values against the oracle
+    y_ref = oracle.ylt(pf, yet)
+    np.testing.assert_allclose(risk[:, 0].cpu().numpy(), y_ref.mean(1), rtol=1e-9)
+    np.testing.assert_allclose(risk[:, 1].cpu().numpy(),
+                               [oracle.tvar(y_ref[l], LEVEL) for l in range(pf.n_layers)], rtol=1e-9)
+    # weighted oracle gradient in parameter layout
+    wn = w.cpu().numpy()
+    gm = oracle.adjoint(pf, yet, "mean", LEVEL)
+    gt = oracle.adjoint(pf, yet, "tvar", LEVEL)
+    loff, _ = pf.layer_csr()
+    exp_ret, exp_lim = np.zeros(pf.n_elts), np.zeros(pf.n_elts)
+    exp_layer = np.zeros((pf.n_layers, 4))
+    rec_off = np.concatenate([[0], np.cumsum([x.size for x in pf.elt_ids])])
+    exp_loss = np.zeros(int(rec_off[-1]))
+    for l, elts in enumerate(pf.layer_elts):
+        exp_layer[l] = wn[l, 0] * gm["layer"][l] + wn[l, 1] * gt["layer"][l]
+        pos = int(gm["loss_offsets"][l])
+        for q, j in enumerate(elts):
+            row = int(loff[l]) + q
+            exp_ret[j] += wn[l, 0] * gm["elt"][row, 0] + wn[l, 1] * gt["elt"][row, 0]
+            exp_lim[j] += wn[l, 0] * gm["elt"][row, 1] + wn[l, 1] * gt["elt"][row, 1]
+            n = pf.elt_ids[j].size
+            exp_loss[rec_off[j]:rec_off[j] + n] += (wn[l, 0] * gm["loss"][pos:pos + n] +
+                                                    wn[l, 1] * gt["loss"][pos:pos + n])
+            pos += n
+    scale = max(1.0, float(np.abs(exp_loss).max()))
+    close(params[0].grad.cpu().numpy(), exp_ret, 1.0)
+    close(params[1].grad.cpu().numpy(), exp_lim, 1.0)
+    for c, p in enumerate(params[2:6]):
+        close(p.grad.cpu().numpy(), exp_layer[:, c], 1.0)
+    close(params[6].grad.cpu().numpy(), exp_loss, scale)
+
+
+def test_adjoint_matches_central_differences_of_gpu_forward(mid):
+    """Central differences of the GPU forward (h = 1e-4 relative) on the layer terms; the
+    objective is piecewise linear, so they are exact wherever no regime changes in between."""
+    pf, yet = mid
+    g = ara.Portfolio.from_tables(pf)
+    off, ids, y, reg = forward(g, yet)
+    gr = g.adjoint(off, ids, y, reg, LEVEL)
+
+    def objectives(p):
+        gg = ara.Portfolio.from_tables(p)
+        yy = gg.run_ylt(off, ids)
+        _, tv, mn = ara.risk_metrics(yy, [], [LEVEL], want_mean=True)
+        return np.stack([mn, tv[:, 0]], 1)
+
+    checked = 0
+    for name, c in [("occ_ret", 0), ("occ_lim", 1), ("agg_ret", 2), ("agg_lim", 3)]:
+        for l in range(pf.n_layers):
+            th = float(getattr(pf, name)[l])
+            h = 1e-4 * th
+            pp, pm = pf.with_terms(pf.terms_dict()), pf.with_terms(pf.terms_dict())
+            getattr(pp, name)[l] = th + h
+            getattr(pm, name)[l] = th - h
+            if not (well_posed(pp, yet, LEVEL) and well_posed(pm, yet, LEVEL)):
+                continue
+            fd = (objectives(pp)[l] - objectives(pm)[l]) / (2 * h)
+            an = np.array([gr["layer"][0][l, c].item(), gr["layer"][1][l, c].item()])
+            # piecewise linear: equal unless a regime flips inside [th - h, th + h]
+            if np.allclose(fd, an, rtol=RTOL, atol=1e-9):
+                checked += 1
+    assert checked >= 6
+
+
+def test_adjoint_tie_at_the_tvar_boundary():
+    """Aggregate limits low enough that the top trials all saturate: TVaR's boundary is a tie
+    (reported), and the symmetric tie rule matches the oracle."""
+    pf, yet = case(22, n_layers=2, n_trials=2000)
+    pf = pf.with_terms({**pf.terms_dict(), "agg_lim": list(np.asarray(pf.agg_lim) * 0.3)})
+    g = ara.Portfolio.from_tables(pf)
+    off, ids, y, reg = forward(g, yet)
+    gr = g.adjoint(off, ids, y, reg, LEVEL)
+    ref = oracle.adjoint(pf, yet, "tvar", LEVEL)
+    assert ref["ties"] == [True, True]
+    assert gr["ties"].tolist() == [1, 1]
+    close(gr["layer"][1].cpu().numpy(), ref["layer"], 1.0)
+    close(gr["elt"][1].cpu().numpy(), ref["elt"], 1.0)
+    close(gr["loss"][1].cpu().numpy(), ref["loss"], 1.0)
