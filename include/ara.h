@@ -113,6 +113,10 @@ ARA_API void ara_destroy_portfolio(ara_portfolio* pf);
                                  (measurement) */
 #define ARA_RUN_LDG       8   /* folded, YET read by per-trial 16-byte register loads instead of
                                  the per-warp TMA bulk-copy ring (measurement) */
+#define ARA_RUN_HOST_DIRECT 16 /* ara_run_ylt_host only: the kernel reads the (pinned, device-
+                                 mapped) host YET in place over the CPU-GPU link instead of
+                                 staging it with copies; ARA_EINVAL if the host arrays are not
+                                 accessible from the device */
 
 /*
  * YLT of n_trials trials for the selected layers.  Asynchronous on `stream`.

@@ -51,6 +51,40 @@ def derive(pf, yet_head, lo=20.0, hi=95.0):
     return t
 
 
+def blank(n):
+    return {"occ_ret": [0.0] * n, "occ_lim": [0.0] * n, "agg_ret": [0.0] * n, "agg_lim": [0.0] * n}
+
+
+def write(name, t):
+    t["_rule"] = __doc__.split("Rule")[1].strip()
+    out = os.path.join(synth.HERE, f"terms_{name}.json")
+    with open(out, "w") as f:
+        json.dump(t, f, indent=1)
+    print("wrote", out)
+
+
+def main_adjoint(seed=0):
+    base = synth.adjoint_portfolio(seed, terms={"elt_ret": [0.0] * 240, "elt_lim": [0.0] * 240, **blank(16)})
+    r, l = synth.percentile_terms(base.elt_losses)
+    pf = base.with_terms({**base.terms_dict(), "elt_ret": r.tolist(), "elt_lim": l.tolist()})
+    t = derive(pf, synth.adjoint_yet(seed, n_trials=5000))
+    t["_seed"] = seed
+    write("adjoint", t)
+
+
+def main_batched(seed=0):
+    base = synth.batched_portfolio(seed, terms={"elt_ret": [0.0] * 200, "elt_lim": [0.0] * 200, **blank(64)})
+    r, l = synth.percentile_terms(base.elt_losses)
+    pf = base.with_terms({**base.terms_dict(), "elt_ret": r.tolist(), "elt_lim": l.tolist()})
+    t = derive(pf, synth.batched_yet(seed, n_trials=2000))
+    f = synth.batched_term_factors(seed)
+    for c, k in enumerate(["occ_ret", "occ_lim", "agg_ret", "agg_lim"]):
+        t[k] = [float(v * f[i, c]) for i, v in enumerate(t[k])]
+    t["_seed"] = seed
+    t["_randomised"] = "each layer term multiplied by U(0.5, 1.5) (synth.batched_term_factors)"
+    write("batched", t)
+
+
 def main():
     seed = 0
     pf = synth.paper_scale_portfolio(seed, terms={"elt_ret": [0.0] * 15, "elt_lim": [0.0] * 15,
@@ -69,4 +103,11 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    import sys
+    which = sys.argv[1:] or ["paper_scale", "adjoint", "batched"]
+    if "paper_scale" in which:
+        main()
+    if "adjoint" in which:
+        main_adjoint()
+    if "batched" in which:
+        main_batched()

@@ -27,6 +27,7 @@ ARA_ERANGE = -7
 ARA_STATIC_SELECT_BYTES = 4 << 20
 ARA_LOSSES_F32, ARA_DENSE_TABLES = 1, 2
 ARA_RUN_FOLDED, ARA_RUN_PER_ELT, ARA_RUN_NO_FILTER, ARA_RUN_F64_SUM, ARA_RUN_LDG = 0, 1, 2, 4, 8
+ARA_RUN_HOST_DIRECT = 16
 ARA_K_FOLD, ARA_K_YLT, ARA_K_SELECT, ARA_K_ADJOINT = 0, 1, 2, 3
 
 _lib = None

@@ -377,8 +377,11 @@ static ara_status check_selection(const Portfolio& pf, int32_t n_sel, const int3
 }
 
 static ara_status check_flags(const Portfolio& pf, int32_t flags) {
-  if (flags & ~(ARA_RUN_PER_ELT | ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG)) return ARA_EINVAL;
-  if ((flags & ARA_RUN_PER_ELT) && (flags & (ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG)))
+  if (flags & ~(ARA_RUN_PER_ELT | ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG |
+                ARA_RUN_HOST_DIRECT))
+    return ARA_EINVAL;
+  if ((flags & ARA_RUN_PER_ELT) &&
+      (flags & (ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG | ARA_RUN_HOST_DIRECT)))
     return ARA_EINVAL;
   if ((flags & ARA_RUN_PER_ELT) && !pf.d_dense) return ARA_EINVAL;
   return ARA_OK;
@@ -394,6 +397,7 @@ ara_status ara_run_ylt(ara_portfolio* pf, int64_t n_trials, const int64_t* d_off
   ara_status st = check_selection(*pf, n_sel, layer_sel, sel);
   if (st != ARA_OK) return st;
   if ((st = check_flags(*pf, flags)) != ARA_OK) return st;
+  if (flags & ARA_RUN_HOST_DIRECT) return ARA_EINVAL;
   if (sel.empty() || n_trials == 0) return ARA_OK;
   if (!d_offsets || !d_ylt || (n_events > 0 && !d_ids)) return ARA_EINVAL;
   if (((uintptr_t)d_ids & 3) || ((uintptr_t)d_offsets & 7) || ((uintptr_t)d_ylt & 7)) return ARA_EINVAL;
@@ -487,6 +491,34 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
   if (!h_ylt && !metrics) return ARA_EINVAL;
   DeviceGuard g(pf->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (flags & ARA_RUN_HOST_DIRECT) {
+    // The device reads the host arrays in place: they must be mapped into its address space.
+    void* d_off_v = nullptr;
+    void* d_ids_v = nullptr;
+    if (cudaHostGetDevicePointer(&d_off_v, (void*)h_off, 0) != cudaSuccess ||
+        (n_events > 0 && cudaHostGetDevicePointer(&d_ids_v, (void*)h_ids, 0) != cudaSuccess)) {
+      cudaGetLastError();
+      return ARA_EINVAL;
+    }
+    if ((st = ensure_stage(*pf, 0, 0, (int64_t)sel.size() * n_trials)) != ARA_OK) return st;
+    const int32_t f = (flags & ~ARA_RUN_HOST_DIRECT) | ARA_RUN_LDG;  // plain loads of host memory
+    if (!(f & ARA_RUN_PER_ELT)) {
+      if ((st = launch_fold(*pf, (int32_t)sel.size(), sel.data(), f, s)) != ARA_OK) return st;
+    }
+    YltArgs a{};
+    a.n_trials = n_trials;
+    a.offsets = (const int64_t*)d_off_v;
+    a.id_base = 0;
+    a.n_events = n_events;
+    a.ids = n_events > 0 ? (const int32_t*)d_ids_v : (const int32_t*)d_off_v;
+    a.n_sel = (int32_t)sel.size();
+    a.sel = sel.data();
+    a.ylt = pf->d_ylt_full;
+    a.regimes = nullptr;
+    a.row_stride = n_trials;
+    a.flags = f;
+    if ((st = launch_ylt(*pf, a, s)) != ARA_OK) return st;
+  } else {
   // chunk boundaries: at most CH_EVENTS events and CH_TRIALS trials per chunk
   const int64_t CH_EVENTS = (int64_t)1 << 24, CH_TRIALS = (int64_t)1 << 20;
   std::vector<int64_t> cut{0};
@@ -533,6 +565,7 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
     if ((st = launch_ylt(*pf, a, s)) != ARA_OK) return st;
     ARA_TRY(cudaEventRecord(pf->ev_done[b], s));
   }
+  }  // staged copies
   if (h_ylt)
     ARA_TRY(cudaMemcpyAsync(h_ylt, pf->d_ylt_full, sizeof(double) * sel.size() * (size_t)n_trials,
                             cudaMemcpyDeviceToHost, s));

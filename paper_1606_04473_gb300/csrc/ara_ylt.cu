@@ -148,9 +148,11 @@ template <typename Acc> struct AccOps;
 template <> struct AccOps<U128> {
   static __device__ __forceinline__ U128 zero() { return U128{0ull, 0ull}; }
   static __device__ __forceinline__ void add(U128& a, uint64_t v) { add_u64(a, v); }
-  // add the sum of up to 8 table values (each < 2^61, so their u64 sum cannot wrap)
-  static __device__ __forceinline__ void add_partial(U128& a, uint64_t part, const uint64_t (&)[8]) {
-    add_u64(a, part);
+  // add lo + hi * 2^32 (the split sums of up to 16 table values; hi < 2^36)
+  template <int NV>
+  static __device__ __forceinline__ void add_split(U128& a, uint64_t lo, uint64_t hi, const uint64_t (&)[NV]) {
+    add_u64(a, lo);
+    add_u128(a, hi << 32, hi >> 32);
   }
   static __device__ __forceinline__ U128 warp_sum(U128 a) {
 #pragma unroll
@@ -184,9 +186,10 @@ template <> struct AccOps<double> {
   static __device__ __forceinline__ void add(double& a, uint64_t v) {
     a = __dadd_rn(a, __longlong_as_double((long long)v));
   }
-  static __device__ __forceinline__ void add_partial(double& a, uint64_t, const uint64_t (&v)[8]) {
+  template <int NV>
+  static __device__ __forceinline__ void add_split(double& a, uint64_t, uint64_t, const uint64_t (&v)[NV]) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) a = __dadd_rn(a, __longlong_as_double((long long)v[i]));
+    for (int i = 0; i < NV; ++i) a = __dadd_rn(a, __longlong_as_double((long long)v[i]));
   }
   static __device__ __forceinline__ double warp_sum(double a) {
 #pragma unroll
@@ -354,10 +357,8 @@ __global__ void __launch_bounds__(YLT_THREADS, 1) k_ylt_folded(StreamParams p) {
 // Every mbarrier wait is bounded: on timeout the warp records DERR_TIMEOUT, waits (bounded) for
 // its own copies still in flight, and returns.
 // ------------------------------------------------------------------------------------------
-constexpr int BK_CHUNK_IDS = 256;                      // 1 KiB per stage
-
-template <int WARPS, int STAGES> struct BulkShape {
-  static constexpr int ring_bytes = WARPS * STAGES * BK_CHUNK_IDS * 4;
+template <int WARPS, int STAGES, int CHUNK> struct BulkShape {
+  static constexpr int ring_bytes = WARPS * STAGES * CHUNK * 4;
   static constexpr int bar_bytes = WARPS * STAGES * 8;
 };
 
@@ -520,15 +521,32 @@ __device__ __forceinline__ void walk_window(Walk<Acc>& w, const StreamParams& p,
   }
 }
 
-template <bool FILTER, typename Acc, int BK_WARPS, int BK_STAGES>
+// Sum of the table values of one lane's slots of a chunk, as two exact 64-bit sums of the
+// 32-bit halves (lo + hi * 2^32), accumulated with wide multiply-adds on the FMA pipe.
+template <int NV>
+__device__ __forceinline__ void sum_values(const uint64_t (&v)[NV], uint64_t& lo_sum, uint64_t& hi_sum) {
+  uint64_t lo = 0, hi = 0;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const uint32_t vl = (uint32_t)v[i], vh = (uint32_t)(v[i] >> 32);
+    asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(lo) : "r"(vl));
+    asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(hi) : "r"(vh));
+  }
+  lo_sum = lo;
+  hi_sum = hi;
+}
+
+template <bool FILTER, typename Acc, int BK_WARPS, int BK_STAGES, int BK_CHUNK_IDS>
 __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
+  constexpr int NV = BK_CHUNK_IDS / 32;               // values per lane per chunk
+  constexpr int NQ = BK_CHUNK_IDS / 128;              // 16-byte loads per lane per chunk
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int64_t bm_bytes = FILTER ? ((p.smem_words * 4 + 127) / 128) * 128 : 0;
   uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* ring = reinterpret_cast<int32_t*>(smem_raw + bm_bytes) + wid * BK_STAGES * BK_CHUNK_IDS;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + bm_bytes +
-                                               BulkShape<BK_WARPS, BK_STAGES>::ring_bytes) +
+                                               BulkShape<BK_WARPS, BK_STAGES, BK_CHUNK_IDS>::ring_bytes) +
                    wid * BK_STAGES;
   if (lane == 0)
     for (int s = 0; s < BK_STAGES; ++s) mbar_init(&bars[s], 1);
@@ -604,9 +622,11 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
     if (__any_sync(FULL, !ok)) { timed_out_at = ch; break; }
     const int32_t rb = head + ch * BK_CHUNK_IDS;
     const int32_t n = min(BK_CHUNK_IDS, n_body - ch * BK_CHUNK_IDS);
-    // lane l holds chunk slots 4l..4l+3 and 128+4l..128+4l+3 (two conflict-free 16-byte loads)
-    const int4 a = reinterpret_cast<const int4*>(ring + s * BK_CHUNK_IDS)[lane];
-    const int4 b = reinterpret_cast<const int4*>(ring + s * BK_CHUNK_IDS)[32 + lane];
+    // lane l holds chunk slots 128u + 4l .. 128u + 4l + 3 for u < NQ (conflict-free 16-byte loads)
+    int4 ids4[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u)
+      ids4[u] = reinterpret_cast<const int4*>(ring + s * BK_CHUNK_IDS)[32 * u + lane];
     __syncwarp();
     if (lane == 0 && ch + BK_STAGES < n_chunks) {
       const int32_t c2 = ch + BK_STAGES;
@@ -615,36 +635,38 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
       mbar_expect_tx(&bars[s], (uint32_t)n2 * 4 + p.debug_extra_tx);
       bulk_g2s(ring + s * BK_CHUNK_IDS, gbase + c2 * BK_CHUNK_IDS, (uint32_t)n2 * 4, &bars[s], pol);
     }
-    const int sa = 4 * lane, sb = 128 + 4 * lane;
-    uint64_t v[8];
+    uint64_t v[NV];
     if (n == BK_CHUNK_IDS) {        // full chunk: every slot is a real event
-      v[0] = bulk_value<FILTER>(a.x, cat1, shift, bm, q, emax);
-      v[1] = bulk_value<FILTER>(a.y, cat1, shift, bm, q, emax);
-      v[2] = bulk_value<FILTER>(a.z, cat1, shift, bm, q, emax);
-      v[3] = bulk_value<FILTER>(a.w, cat1, shift, bm, q, emax);
-      v[4] = bulk_value<FILTER>(b.x, cat1, shift, bm, q, emax);
-      v[5] = bulk_value<FILTER>(b.y, cat1, shift, bm, q, emax);
-      v[6] = bulk_value<FILTER>(b.z, cat1, shift, bm, q, emax);
-      v[7] = bulk_value<FILTER>(b.w, cat1, shift, bm, q, emax);
+#pragma unroll
+      for (int u = 0; u < NQ; ++u) {
+        v[4 * u + 0] = bulk_value<FILTER>(ids4[u].x, cat1, shift, bm, q, emax);
+        v[4 * u + 1] = bulk_value<FILTER>(ids4[u].y, cat1, shift, bm, q, emax);
+        v[4 * u + 2] = bulk_value<FILTER>(ids4[u].z, cat1, shift, bm, q, emax);
+        v[4 * u + 3] = bulk_value<FILTER>(ids4[u].w, cat1, shift, bm, q, emax);
+      }
     } else {
-      v[0] = val_of(a.x, sa + 0 < n);
-      v[1] = val_of(a.y, sa + 1 < n);
-      v[2] = val_of(a.z, sa + 2 < n);
-      v[3] = val_of(a.w, sa + 3 < n);
-      v[4] = val_of(b.x, sb + 0 < n);
-      v[5] = val_of(b.y, sb + 1 < n);
-      v[6] = val_of(b.z, sb + 2 < n);
-      v[7] = val_of(b.w, sb + 3 < n);
+#pragma unroll
+      for (int u = 0; u < NQ; ++u) {
+        const int sl = 128 * u + 4 * lane;
+        v[4 * u + 0] = val_of(ids4[u].x, sl + 0 < n);
+        v[4 * u + 1] = val_of(ids4[u].y, sl + 1 < n);
+        v[4 * u + 2] = val_of(ids4[u].z, sl + 2 < n);
+        v[4 * u + 3] = val_of(ids4[u].w, sl + 3 < n);
+      }
     }
     while (w.k < w.nk && w.end <= rb) walk_finish(w, p, lc, t_lo, base_abs, lane);
     if (w.k < w.nk && w.end >= rb + n) {
-      // fast path: the whole chunk belongs to the current trial (sum of <= 8 values < 2^64)
-      const uint64_t part = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
-      AccOps<Acc>::add_partial(w.acc, part, v);
+      // fast path: the whole chunk belongs to the current trial
+      uint64_t lo, hi;
+      sum_values<NV>(v, lo, hi);
+      AccOps<Acc>::add_split(w.acc, lo, hi, v);
     } else {
-      int32_t pos[8] = {rb + sa, rb + sa + 1, rb + sa + 2, rb + sa + 3,
-                        rb + sb, rb + sb + 1, rb + sb + 2, rb + sb + 3};
-      walk_window<Acc, 8>(w, p, lc, t_lo, base_abs, lane, rb, rb + n, pos, v);
+      int32_t pos[NV];
+#pragma unroll
+      for (int u = 0; u < NQ; ++u)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pos[4 * u + i] = rb + 128 * u + 4 * lane + i;
+      walk_window<Acc, NV>(w, p, lc, t_lo, base_abs, lane, rb, rb + n, pos, v);
     }
   }
   if (timed_out_at >= 0) {
@@ -854,7 +876,8 @@ static ara_status launch_folded_one(Portfolio& pf, StreamParams& sp, cudaStream_
 
 // Compiled shapes of the bulk kernel (warps per block, ring stages); the active one is chosen
 // with ara_set_stream_shape (default: the first).
-static const int kBulkShapes[][2] = {{32, 3}, {24, 4}, {16, 6}, {16, 4}, {32, 2}};
+static const int kBulkShapes[][3] = {{32, 2, 256}, {32, 3, 256}, {24, 4, 256}, {24, 2, 512},
+                                     {16, 3, 512}, {16, 4, 256}};
 static std::atomic<int> g_bulk_shape{0};
 static std::atomic<uint64_t> g_wait_limit_ns{1000000000ull};
 static std::atomic<uint32_t> g_debug_extra_tx{0};
@@ -862,11 +885,12 @@ static std::atomic<uint32_t> g_debug_extra_tx{0};
 void set_wait_limit_ns(uint64_t ns) { g_wait_limit_ns.store(ns); }
 void set_debug_extra_tx(uint32_t b) { g_debug_extra_tx.store(b); }
 
-template <bool FILTER, typename Acc, int WARPS, int STAGES>
+template <bool FILTER, typename Acc, int WARPS, int STAGES, int CHUNK>
 static ara_status launch_bulk_shape(Portfolio& pf, StreamParams& sp, cudaStream_t s) {
-  const auto fn = k_ylt_bulk<FILTER, Acc, WARPS, STAGES>;
+  const auto fn = k_ylt_bulk<FILTER, Acc, WARPS, STAGES, CHUNK>;
   const int64_t bm_bytes = FILTER ? ((sp.smem_words * 4 + 127) / 128) * 128 : 0;
-  const int smem = (int)(bm_bytes + BulkShape<WARPS, STAGES>::ring_bytes + BulkShape<WARPS, STAGES>::bar_bytes);
+  using Sh = BulkShape<WARPS, STAGES, CHUNK>;
+  const int smem = (int)(bm_bytes + Sh::ring_bytes + Sh::bar_bytes);
   ara_status st = set_smem((const void*)fn, smem);
   if (st != ARA_OK) return st;
   LaunchScope ls(ARA_K_YLT, s);
@@ -878,24 +902,25 @@ static ara_status launch_bulk_shape(Portfolio& pf, StreamParams& sp, cudaStream_
 template <bool FILTER, typename Acc>
 static ara_status launch_bulk_one(Portfolio& pf, StreamParams& sp, cudaStream_t s) {
   switch (g_bulk_shape.load()) {
-    case 1: return launch_bulk_shape<FILTER, Acc, 24, 4>(pf, sp, s);
-    case 2: return launch_bulk_shape<FILTER, Acc, 16, 6>(pf, sp, s);
-    case 3: return launch_bulk_shape<FILTER, Acc, 16, 4>(pf, sp, s);
-    case 4: return launch_bulk_shape<FILTER, Acc, 32, 2>(pf, sp, s);
-    default: return launch_bulk_shape<FILTER, Acc, 32, 3>(pf, sp, s);
+    case 1: return launch_bulk_shape<FILTER, Acc, 32, 3, 256>(pf, sp, s);
+    case 2: return launch_bulk_shape<FILTER, Acc, 24, 4, 256>(pf, sp, s);
+    case 3: return launch_bulk_shape<FILTER, Acc, 24, 2, 512>(pf, sp, s);
+    case 4: return launch_bulk_shape<FILTER, Acc, 16, 3, 512>(pf, sp, s);
+    case 5: return launch_bulk_shape<FILTER, Acc, 16, 4, 256>(pf, sp, s);
+    default: return launch_bulk_shape<FILTER, Acc, 32, 2, 256>(pf, sp, s);
   }
 }
 
 static int bulk_ring_bytes() {
   const int* sh = kBulkShapes[g_bulk_shape.load()];
-  return sh[0] * sh[1] * (BK_CHUNK_IDS * 4 + 8);
+  return sh[0] * sh[1] * (sh[2] * 4 + 8);
 }
 
 int32_t n_bulk_shapes() { return (int32_t)(sizeof(kBulkShapes) / sizeof(kBulkShapes[0])); }
 void set_bulk_shape(int32_t i) { g_bulk_shape.store(i); }
 void bulk_shape(int32_t i, int32_t* warps, int32_t* stages) {
   *warps = kBulkShapes[i][0];
-  *stages = kBulkShapes[i][1];
+  *stages = kBulkShapes[i][1] * 10000 + kBulkShapes[i][2];   // stages * 10000 + chunk IDs
 }
 
 ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {

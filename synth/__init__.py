@@ -269,3 +269,51 @@ def paper_scale_yet(seed: int = 0, n_trials: int = 1_000_000, events_per_trial: 
     """n_trials x exactly events_per_trial events (no timestamps: the YLT does not read them)."""
     counts = np.full(n_trials, events_per_trial, dtype=np.int64)
     return make_yet(seed, counts, 2_000_000, with_timestamps=False, ids_out=ids_out)
+
+
+def _pool(seed: int, n_elts: int, nnz: int = 20_000, catalogue: int = 2_000_000):
+    ids, losses = make_elts(seed, n_elts, nnz, catalogue, 11.0, 2.0, f32=True)
+    r, l = percentile_terms(losses)
+    return ids, losses, r, l
+
+
+def adjoint_portfolio(seed: int = 0, terms: Optional[dict] = None) -> Portfolio:
+    """16 layers x 15 ELTs (each layer its own 15 ELTs of 20,000 events, 2,000,000-event
+    catalogue, FP32 lognormal(11, 2) losses); layer terms from terms_adjoint.json."""
+    ids, losses, r, l = _pool(seed + 1000, 16 * 15)
+    layers = [list(range(15 * k, 15 * k + 15)) for k in range(16)]
+    nan = np.full(16, np.nan)
+    pf = Portfolio(2_000_000, ids, losses, r, l, layers, nan, nan, nan, nan, losses_f32=True)
+    return pf.with_terms(load_terms("adjoint") if terms is None else terms)
+
+
+def adjoint_yet(seed: int = 0, n_trials: int = 200_000, ids_out: Optional[np.ndarray] = None) -> YET:
+    counts = np.full(n_trials, 1000, dtype=np.int64)
+    return make_yet(seed + 1000, counts, 2_000_000, with_timestamps=False, ids_out=ids_out)
+
+
+def batched_portfolio(seed: int = 0, terms: Optional[dict] = None) -> Portfolio:
+    """64 layers, each of U{3..30} distinct ELTs drawn from a pool of 200 ELTs (20,000 events,
+    2,000,000-event catalogue, FP32 lognormal(11, 2)); layer terms from terms_batched.json."""
+    ids, losses, r, l = _pool(seed + 2000, 200)
+    key = stream_key(seed, 5)
+    sizes = 3 + below(key, 0, 64, 28)                       # U{3..30}
+    layers = []
+    for k in range(64):
+        pick = distinct(stream_key(seed, 6, k), int(sizes[k]), 200)
+        layers.append(sorted(int(x) for x in pick))
+    nan = np.full(64, np.nan)
+    pf = Portfolio(2_000_000, ids, losses, r, l, layers, nan, nan, nan, nan, losses_f32=True)
+    return pf.with_terms(load_terms("batched") if terms is None else terms)
+
+
+def batched_term_factors(seed: int = 0) -> np.ndarray:
+    """Per-layer multipliers U(0.5, 1.5) of (OccR, OccL, AggR, AggL) around the percentile rule."""
+    return 0.5 + uniform01(stream_key(seed, 7), 0, 64 * 4).reshape(64, 4)
+
+
+def batched_yet(seed: int = 0, n_trials: int = 200_000, ids_out: Optional[np.ndarray] = None) -> YET:
+    """Trials with Poisson event counts whose per-trial mean is uniform on [200, 2000]."""
+    mu = 200.0 + 1800.0 * uniform01(stream_key(seed, 8), 0, n_trials)
+    counts = poisson_counts(seed + 2000, mu, n_trials)
+    return make_yet(seed + 2000, counts, 2_000_000, with_timestamps=False, ids_out=ids_out)

@@ -123,8 +123,8 @@ def test_accumulate_and_autograd_match_weighted_reference(mid):
     (risk * w).sum().backward()
     # forward values against the oracle
     y_ref = oracle.ylt(pf, yet)
-    np.testing.assert_allclose(risk[:, 0].cpu().numpy(), y_ref.mean(1), rtol=1e-9)
-    np.testing.assert_allclose(risk[:, 1].cpu().numpy(),
+    np.testing.assert_allclose(risk[:, 0].detach().cpu().numpy(), y_ref.mean(1), rtol=1e-9)
+    np.testing.assert_allclose(risk[:, 1].detach().cpu().numpy(),
                                [oracle.tvar(y_ref[l], LEVEL) for l in range(pf.n_layers)], rtol=1e-9)
     # weighted oracle gradient in parameter layout
     wn = w.cpu().numpy()

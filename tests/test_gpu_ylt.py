@@ -266,6 +266,20 @@ def test_host_pipeline_multi_chunk():
     assert_ylt_close(y_host[:, sample], ref, agg)
 
 
+def test_host_direct_reads_pinned_host_memory(mid):
+    """ARA_RUN_HOST_DIRECT: the kernel reads the pinned host YET in place; same YLT as the
+    device path.  Pageable (unmapped) host memory is refused."""
+    pf, yet, ref, agg = mid
+    g = ara.Portfolio.from_tables(pf)
+    ids_p = torch.from_numpy(yet.event_ids).pin_memory()
+    off_p = torch.from_numpy(yet.offsets).pin_memory()
+    y_dev = g.run_ylt(off_p.cuda(), ids_p.cuda()).cpu().numpy()
+    y_dir = g.run_ylt_host(off_p.numpy(), ids_p.numpy(), flags=ara.ARA_RUN_HOST_DIRECT)
+    assert np.array_equal(y_dev, y_dir)
+    with pytest.raises(ara.AraError):
+        g.run_ylt_host(np.array(yet.offsets), np.array(yet.event_ids), flags=ara.ARA_RUN_HOST_DIRECT)
+
+
 def test_paper_scale_full_size_sampled():
     """The paper-scale workload (1 layer of 15 ELTs, 2M-event catalogue, 10^6 trials x 1000
     events) in the benchmark's launch configuration; 4000 sampled trials against the oracle,
