@@ -45,7 +45,7 @@ METRIC = "event-ELT lookups/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--flags", type=int, default=0, help="ARA_RUN_* flags (measurement variants)")
@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     return ap.parse_args()
 
 
@@ -110,7 +111,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -306,16 +307,27 @@ def run_ours(args, rank, ws, local):
     e2e_steps = args.e2e_steps or max(3, min(args.steps, 10))
     ylt_h = torch.empty((1, n_trials), dtype=torch.float64, pin_memory=True)
     ids_np, off_np, ylt_np = ids_h.numpy(), off_h.numpy(), ylt_h.numpy()
-    for _ in range(2):
-        g.run_ylt_host(off_np, ids_np, out=ylt_np, return_periods=RPS, tvar_levels=LEVELS, flags=args.flags)
-    barrier(ws)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        g.run_ylt_host(off_np, ids_np, out=ylt_np, return_periods=RPS, tvar_levels=LEVELS, flags=args.flags)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
-    barrier(ws)
+    def e2e_time(flags):
+        for _ in range(2):
+            g.run_ylt_host(off_np, ids_np, out=ylt_np, return_periods=RPS, tvar_levels=LEVELS, flags=flags)
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            g.run_ylt_host(off_np, ids_np, out=ylt_np, return_periods=RPS, tvar_levels=LEVELS, flags=flags)
+        torch.cuda.synchronize()
+        t = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
+        barrier(ws)
+        return t
+
+    e2e_staged = e2e_time(args.flags)
+    try:
+        e2e_direct = e2e_time(args.flags | ara.ARA_RUN_HOST_DIRECT)
+    except ara.AraError:
+        e2e_direct = float("inf")
+    e2e_s = min(e2e_staged, e2e_direct)
+    e2e_api = ("ara_run_ylt_host, ARA_RUN_HOST_DIRECT (kernel reads the pinned host YET over the CPU-GPU link)"
+               if e2e_direct <= e2e_staged else "ara_run_ylt_host (chunked H2D copies overlapped with kernels)")
     h2d = ids_h.numel() * 4 + off_h.numel() * 8
     d2h = n_trials * 8 + 8 * (len(RPS) + len(LEVELS))
 
@@ -330,6 +342,11 @@ def run_ours(args, rank, ws, local):
             "peak_source": peak_kind, "kernel": "k_ylt_folded",
             "alg_bytes_per_launch": alg_bytes, "ms_per_launch": round(per_launch_ms, 4),
             "frac_8byte_events": round((alg_bytes + 4 * n_events) / (per_launch_ms / 1e3) / 1e9 / peak, 4)}
+
+    g.close()
+    del ids, off, ylt
+    torch.cuda.empty_cache()
+    adjoint_line = None if args.no_adjoint else measure_adjoint(rank)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -354,13 +371,58 @@ def run_ours(args, rank, ws, local):
                 "cpu_baseline": cpu,
                 "e2e": {"value": lookups_per_step * ws / e2e_s, "unit": "lookups/s",
                         "ms_per_step": e2e_s * 1e3, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h, "api": "ara_run_ylt_host (pinned host YET)"},
+                        "d2h_bytes_per_step": d2h, "api": e2e_api,
+                        "ms_per_step_staged": e2e_staged * 1e3,
+                        "ms_per_step_direct": (e2e_direct * 1e3 if e2e_direct != float("inf") else None)},
+                "adjoint": adjoint_line,
                 "gpu_launches": launches,
                 "clocks": clk.summary(),
                 "results": {"pml100": float(pml[0, 0]), "pml250": float(pml[0, 1]),
                             "tvar99": float(tvar[0, 0])}}
         print(json.dumps(line), flush=True)
+
+
+def measure_adjoint(rank: int, reps: int = 5):
+    """Adjoint/forward time ratio on the adjoint workload: 16 layers x 15 ELTs (2M catalogue),
+    2e5 trials x 1000 events.  Forward = YLT of all layers (recording regimes) + mean and
+    TVaR99; adjoint = gradients of both w.r.t. every term and ELT loss."""
+    import torch
+    import paper_1606_04473_gb300 as ara
+    import synth
+    pf = synth.adjoint_portfolio(0)
+    yet = synth.adjoint_yet(rank, n_trials=200_000)
+    g = ara.Portfolio.from_tables(pf)
+    off = torch.from_numpy(yet.offsets).cuda()
+    ids = torch.from_numpy(yet.event_ids).cuda()
+    reg = torch.empty((pf.n_layers, yet.n_trials), dtype=torch.uint8, device="cuda")
+    y = torch.empty((pf.n_layers, yet.n_trials), dtype=torch.float64, device="cuda")
+
+    def fwd():
+        g.run_ylt(off, ids, out=y, regimes=reg)
+        return ara.risk_metrics(y, [], [0.99], want_mean=True)
+
+    def adj():
+        return g.adjoint(off, ids, y, reg, 0.99)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    f_ms = timed(fwd)
+    a_ms = timed(adj)
+    g.check()
+    out = {"workload": "16 layers x 15 ELTs (2M catalogue, 20k events each), 2e5 trials x 1000 events",
+           "forward_ms": round(f_ms, 3), "adjoint_ms": round(a_ms, 3), "ratio": round(a_ms / f_ms, 3),
+           "objectives": "mean year loss and TVaR99 per layer; gradients w.r.t. every retention, "
+                         "limit and ELT loss"}
     g.close()
+    return out
 
 
 def main():
