@@ -140,14 +140,26 @@ __global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
       int64_t beg = __shfl_sync(FULLM, my_off, k);
       int64_t end = (k + 1 < 32) ? __shfl_sync(FULLM, my_off, k + 1) : last_off;
       if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; continue; }
-      for (int64_t i = beg + lane; i < end; i += 32) {
-        const int e = __ldcs(p.ids + i);
-        if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; continue; }
-        const uint32_t b = (uint32_t)e >> p.shift;
-        if (!((bm[b >> 5] >> (b & 31)) & 1u)) continue;
-        atomicAdd(p.h_mean + e, 1u);
-        if (c == 2) atomicAdd(p.h_gt + e, 1u);
-        else if (c == 3) atomicAdd(p.h_eq + e, 1u);
+      // eight independent streaming loads per lane in flight, then the filtered atomics
+      for (int64_t i0 = beg; i0 < end; i0 += 256) {
+        int ev[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t i = i0 + 32 * u + lane;
+          ev[u] = i < end ? __ldcs(p.ids + i) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t i = i0 + 32 * u + lane;
+          const int e = ev[u];
+          if (i >= end) continue;
+          if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; continue; }
+          const uint32_t b = (uint32_t)e >> p.shift;
+          if (!((bm[b >> 5] >> (b & 31)) & 1u)) continue;
+          atomicAdd(p.h_mean + e, 1u);
+          if (c == 2) atomicAdd(p.h_gt + e, 1u);
+          else if (c == 3) atomicAdd(p.h_eq + e, 1u);
+        }
       }
     }
   }
