@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-portfolio measurement")
     return ap.parse_args()
 
 
@@ -347,6 +348,7 @@ def run_ours(args, rank, ws, local):
     del ids, off, ylt
     torch.cuda.empty_cache()
     adjoint_line = None if args.no_adjoint else measure_adjoint(rank)
+    batched_line = None if args.no_batched else measure_batched(rank)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -375,6 +377,7 @@ def run_ours(args, rank, ws, local):
                         "ms_per_step_staged": e2e_staged * 1e3,
                         "ms_per_step_direct": (e2e_direct * 1e3 if e2e_direct != float("inf") else None)},
                 "adjoint": adjoint_line,
+                "batched": batched_line,
                 "gpu_launches": launches,
                 "clocks": clk.summary(),
                 "results": {"pml100": float(pml[0, 0]), "pml250": float(pml[0, 1]),
@@ -421,6 +424,59 @@ def measure_adjoint(rank: int, reps: int = 5):
            "forward_ms": round(f_ms, 3), "adjoint_ms": round(a_ms, 3), "ratio": round(a_ms / f_ms, 3),
            "objectives": "mean year loss and TVaR99 per layer; gradients w.r.t. every retention, "
                          "limit and ELT loss"}
+    g.close()
+    return out
+
+
+def measure_batched(rank: int, reps: int = 5):
+    """Batched portfolio: 64 layers of U{3..30} ELTs from a pool of 200 (2M catalogue), YET of
+    2e5 trials with Poisson counts of per-trial mean U[200, 2000]; one autotuned plan (one CUDA
+    graph: folds, event-major table, one persistent stream kernel) against 64 sequential
+    single-layer ara_run_ylt launches of the same layers."""
+    import torch
+    import paper_1606_04473_gb300 as ara
+    import synth
+    pf = synth.batched_portfolio(0)
+    yet = synth.batched_yet(rank, n_trials=200_000)
+    g = ara.Portfolio.from_tables(pf)
+    off = torch.from_numpy(yet.offsets).cuda()
+    ids = torch.from_numpy(yet.event_ids).cuda()
+    y_seq = torch.empty((pf.n_layers, yet.n_trials), dtype=torch.float64, device="cuda")
+    lookups = int(yet.n_events) * sum(len(l) for l in pf.layer_elts)
+
+    def seq():
+        for l in range(pf.n_layers):
+            g.run_ylt(off, ids, layers=[l], out=y_seq[l:l + 1])
+
+    t_plan0 = time.perf_counter()
+    plan = ara.BatchedPlan(g, off, ids, autotune=True)
+    t_plan = time.perf_counter() - t_plan0
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    seq_ms = timed(seq)
+    plan_ms = timed(plan.launch)
+    g.check()
+    identical = bool(torch.equal(plan.out, y_seq))
+    out = {"workload": "64 layers x U{3..30} ELTs from a pool of 200 (2M catalogue), 2e5 trials x "
+                       "Poisson(U[200,2000]) events",
+           "events": int(yet.n_events), "lookups_per_pass": lookups,
+           "sequential_ms": round(seq_ms, 3), "batched_ms": round(plan_ms, 3),
+           "speedup": round(seq_ms / plan_ms, 3),
+           "batched_lookups_per_s": lookups / (plan_ms / 1e3),
+           "identical_to_sequential": identical, "schedule": plan.info(),
+           "plan_build_s": round(t_plan, 3)}
+    plan.close()
     g.close()
     return out
 

@@ -169,6 +169,41 @@ ARA_API ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials,
 ARA_API ara_status ara_check(ara_portfolio* pf, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Batched portfolio: every selected layer in one pass over the YET, as one CUDA graph.
+ * --------------------------------------------------------------------------------------- */
+
+typedef struct ara_plan ara_plan;
+
+#define ARA_PLAN_AUTOTUNE 1   /* time the candidate stream schedules on these inputs, keep the
+                                 fastest */
+
+/*
+ * Build a plan for the YLT of n_layer_sel layers (<= 255) of a portfolio over one device YET
+ * (Algorithm 1's program and layer loops folded into one launch).  The plan owns its scratch
+ * (an event-major table of every layer's non-zero occurrence losses, with per-event rows) and a
+ * CUDA graph of the whole run: per-layer folds (per-ELT and occurrence terms), the table build,
+ * and one persistent stream kernel that reads every occurrence once, accumulates all layers'
+ * trial sums exactly, applies their aggregate terms and writes the YLT.  The YET, YLT and
+ * regime buffers are bound to the plan: every ara_plan_launch recomputes the YLT from their
+ * current contents.  Results equal those of ara_run_ylt bit for bit.  Synchronous.
+ *   arguments as ara_run_ylt (layer_sel must not be NULL unless n_layer_sel = 0: all layers)
+ *   flags     ARA_PLAN_AUTOTUNE or 0
+ * Errors: ARA_EINVAL, ARA_ERANGE (more than 255 layers), ARA_ENOMEM, ARA_ECUDA.
+ */
+ARA_API ara_status ara_plan_batched(ara_portfolio* pf, int64_t n_trials,
+                                    const int64_t* d_trial_offsets, int64_t n_events,
+                                    const int32_t* d_event_ids, int32_t n_layer_sel,
+                                    const int32_t* layer_sel, double* d_ylt, uint8_t* d_regimes,
+                                    int32_t flags, void* stream, ara_plan** out);
+/* Replay the plan's graph on `stream` (asynchronous; data errors via ara_check). */
+ARA_API ara_status ara_plan_launch(ara_plan* plan, void* stream);
+/* The schedule in use: warps per block, blocks per SM, trials per queue grab, and the tuned
+ * time of one stream kernel in ms (0 without ARA_PLAN_AUTOTUNE). */
+ARA_API ara_status ara_plan_info(ara_plan* plan, int32_t* warps, int32_t* blocks_per_sm,
+                                 int32_t* trials_per_grab, double* tuned_ms);
+ARA_API void ara_plan_destroy(ara_plan* plan);
+
+/* ---------------------------------------------------------------------------------------
  * Adjoint: sensitivities of the risk metrics (Section IV-A) to the financial terms and the
  * ELT losses (Section IV-B).
  * --------------------------------------------------------------------------------------- */
@@ -306,7 +341,8 @@ ARA_API ara_status ara_debug_set(int32_t key, int64_t value);
 #define ARA_K_YLT     1   /* the YET stream: trial sums, aggregate terms, YLT write */
 #define ARA_K_SELECT  2   /* PML / TVaR selection (all of its launches) */
 #define ARA_K_ADJOINT 3   /* adjoint kernels */
-#define ARA_K_COUNT   4
+#define ARA_K_BATCHED 4   /* one replay of a batched-portfolio plan (its whole CUDA graph) */
+#define ARA_K_COUNT   5
 
 /* When enabled, CUDA events are recorded on the launching stream around every launch of
  * each kernel class.  ara_timing_read synchronises those events and returns the summed

@@ -28,7 +28,8 @@ ARA_STATIC_SELECT_BYTES = 4 << 20
 ARA_LOSSES_F32, ARA_DENSE_TABLES = 1, 2
 ARA_RUN_FOLDED, ARA_RUN_PER_ELT, ARA_RUN_NO_FILTER, ARA_RUN_F64_SUM, ARA_RUN_LDG = 0, 1, 2, 4, 8
 ARA_RUN_HOST_DIRECT = 16
-ARA_K_FOLD, ARA_K_YLT, ARA_K_SELECT, ARA_K_ADJOINT = 0, 1, 2, 3
+ARA_K_FOLD, ARA_K_YLT, ARA_K_SELECT, ARA_K_ADJOINT, ARA_K_BATCHED = 0, 1, 2, 3, 4
+ARA_PLAN_AUTOTUNE = 1
 
 _lib = None
 
@@ -65,6 +66,15 @@ def lib() -> ctypes.CDLL:
     L.ara_set_stream_shape.restype = i32
     L.ara_debug_set.argtypes = [i32, i64]
     L.ara_debug_set.restype = i32
+    L.ara_plan_batched.argtypes = [P, i64, P, i64, P, i32, P, P, P, i32, P, ctypes.POINTER(P)]
+    L.ara_plan_batched.restype = i32
+    L.ara_plan_launch.argtypes = [P, P]
+    L.ara_plan_launch.restype = i32
+    L.ara_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                ctypes.POINTER(d)]
+    L.ara_plan_info.restype = i32
+    L.ara_plan_destroy.argtypes = [P]
+    L.ara_plan_destroy.restype = None
     L.ara_adjoint.argtypes = [P, i64, P, i64, P, i32, P, P, P, d, P, P, P, P, P]
     L.ara_adjoint.restype = i32
     L.ara_adjoint_accumulate.argtypes = [P, i64, P, i64, P, i32, P, P, P, d, P, P, P, P, P, P]
@@ -275,6 +285,52 @@ class Portfolio:
 
     def check(self, stream=None):
         _check(lib().ara_check(self._h, _stream_handle(stream)), "ara_check")
+
+
+class BatchedPlan:
+    """Every selected layer in one pass over a device YET, as one CUDA graph (ara_plan_batched).
+    The YET and output buffers are bound at construction; launch() recomputes the YLT."""
+
+    def __init__(self, portfolio: Portfolio, offsets, event_ids, layers=None, out=None, regimes=None,
+                 autotune: bool = True, stream=None):
+        import torch
+        n_trials = offsets.numel() - 1
+        n_sel, sel_p, n_out, _sel = portfolio._sel(layers)
+        if out is None:
+            out = torch.empty((n_out, n_trials), dtype=torch.float64, device=offsets.device)
+        self.out, self.regimes = out, regimes
+        self._keep = (portfolio, offsets, event_ids, _sel)
+        h = ctypes.c_void_p()
+        st = lib().ara_plan_batched(portfolio._h, n_trials, _dev_ptr(offsets, torch.int64, "offsets"),
+                                    event_ids.numel(), _dev_ptr(event_ids, torch.int32, "event_ids"),
+                                    n_sel, sel_p, _dev_ptr(out, torch.float64, "out"),
+                                    None if regimes is None else _dev_ptr(regimes, torch.uint8, "regimes"),
+                                    ARA_PLAN_AUTOTUNE if autotune else 0, _stream_handle(stream),
+                                    ctypes.byref(h))
+        _check(st, "ara_plan_batched")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().ara_plan_launch(self._h, _stream_handle(stream)), "ara_plan_launch")
+        return self.out
+
+    def info(self):
+        w, c, t, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib().ara_plan_info(self._h, ctypes.byref(w), ctypes.byref(c), ctypes.byref(t),
+                                   ctypes.byref(ms)), "ara_plan_info")
+        return {"warps": w.value, "blocks_per_sm": c.value, "trials_per_grab": t.value,
+                "tuned_ms": ms.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ara_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def risk_metrics(ylt, return_periods: Sequence[float] = (), tvar_levels: Sequence[float] = (),

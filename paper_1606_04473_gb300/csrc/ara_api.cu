@@ -78,6 +78,18 @@ void timing_end(int k, cudaStream_t s) {
   if (g_pending[k].size() > 4096) drain(k);
 }
 
+bool timing_suspend() {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  const bool was = g_timing;
+  g_timing = false;
+  return was;
+}
+
+void timing_resume(bool was_on) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  g_timing = was_on;
+}
+
 // ------------------------------------------------------------------------------------------
 // Validation helpers
 // ------------------------------------------------------------------------------------------
@@ -112,7 +124,7 @@ static void layer_scale(Portfolio& pf, LayerConst& lc) {
   b = b * (1.0 + 1e-9) + 1e-300;  // margin for the device's own rounding of the same sums
   int ex = 0;
   std::frexp(b, &ex);             // b < 2^ex
-  int fb = 61 - ex;               // q = o * 2^fb < 2^61
+  int fb = 55 - ex;               // q = o * 2^fb < 2^55 (8 bits free for a layer slot)
   fb = std::max(-1000, std::min(1000, fb));
   lc.frac_bits = fb;
   lc.scale = std::ldexp(1.0, fb);

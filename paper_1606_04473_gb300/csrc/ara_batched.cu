@@ -1,0 +1,536 @@
+// Batched portfolio: every selected layer of a portfolio in one pass over the YET (the program
+// and layer loops of Algorithm 1 folded into one launch).
+//
+// Preparation, per run (all on the stream, captured in the plan's CUDA graph):
+//   1. s_i(e) = sum over the ELTs of layer i, in layer order, of C(x_j(e); R_j, L_j): one
+//      scatter launch per ELT slot k (slot k of every layer at once; records of one ELT have
+//      distinct events, so no two threads of a launch touch the same entry), FP64, the same
+//      operation order as the single-layer fold and the FP64 reference.
+//   2. q_i(e) = round(C(s_i(e); OccR_i, OccL_i) * 2^f_i) in place of s_i(e) (the FP64 clamps
+//      run on block-compacted non-zero entries only), and the count of non-zero q per event.
+//   3. exclusive scan of the counts -> CSR row pointers.
+//   4. event-major CSR rows: for event e, its (layer slot, q) pairs in layer order, packed as
+//      slot << 56 | q (q < 2^55).
+// Stream (persistent, atomic trial queue for uneven trial lengths): a warp takes trials from the
+// queue; for every occurrence it walks the event's CSR row and adds each q to the warp's
+// per-layer accumulator in shared memory (exact 128-bit: 64-bit atomic add with carry); at the
+// end of a trial its lanes apply every layer's aggregate terms to the exact sums and write the
+// YLT entries.  Integer sums make the result independent of the order of the additions and
+// bitwise equal to the single-layer path.
+
+#include <algorithm>
+#include <vector>
+
+#include "ara_device.cuh"
+
+namespace ara {
+
+constexpr int BT_MAX_LAYERS = 255;          // slot fits in 8 bits (255 = no slot)
+constexpr int BT_SCAN_BLOCK = 1024;
+
+// ------------------------------------------------------------------------------------------
+// 1. scatter of one ELT slot of every selected layer
+// ------------------------------------------------------------------------------------------
+struct BtScatter {
+  int32_t n_sel;
+  int32_t elt[BT_MAX_LAYERS];   // ELT at this slot for each selected layer, -1 if none
+};
+
+template <typename LossT>
+__global__ void __launch_bounds__(256)
+k_bt_scatter(BtScatter sc, const int64_t* __restrict__ rec_off, const int32_t* __restrict__ rec_ids,
+             const LossT* __restrict__ rec_loss, const double* __restrict__ elt_ret,
+             const double* __restrict__ elt_lim, double* __restrict__ s_tab, int64_t catalogue) {
+  const int i = blockIdx.y;
+  const int j = sc.elt[i];
+  if (j < 0) return;
+  const double R = elt_ret[j], L = elt_lim[j];
+  double* s = s_tab + (int64_t)i * catalogue;
+  for (int64_t r = rec_off[j] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rec_off[j + 1];
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int e = rec_ids[r];
+    double ex = __dsub_rn((double)rec_loss[r], R);
+    if (ex < 0.0) ex = 0.0;
+    if (ex > L) ex = L;
+    s[e] = __dadd_rn(s[e], ex);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// 2. occurrence terms and fixed point in place; count of non-zero entries per event
+// ------------------------------------------------------------------------------------------
+struct BtLayers {
+  int32_t n_sel;
+  int32_t layer[BT_MAX_LAYERS];
+};
+
+__global__ void __launch_bounds__(256)
+k_bt_quantize(BtLayers bl, const LayerConst* __restrict__ layers, double* __restrict__ s_tab,
+              int64_t catalogue, uint32_t* __restrict__ cnt) {
+  __shared__ int32_t list[256];
+  __shared__ int32_t n_list;
+  const int i = blockIdx.y;
+  const LayerConst lc = layers[bl.layer[i]];
+  uint64_t* qt = reinterpret_cast<uint64_t*>(s_tab + (int64_t)i * catalogue);
+  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (threadIdx.x == 0) n_list = 0;
+  __syncthreads();
+  const double sv = e < catalogue ? s_tab[(int64_t)i * catalogue + e] : 0.0;
+  if (sv != 0.0) list[atomicAdd(&n_list, 1)] = threadIdx.x;   // compact: FP64 on full warps
+  __syncthreads();
+  if (threadIdx.x < n_list) {
+    const int64_t ee = (int64_t)blockIdx.x * 256 + list[threadIdx.x];
+    const double s = s_tab[(int64_t)i * catalogue + ee];
+    double o = __dsub_rn(s, lc.occ_ret);
+    if (o < 0.0) o = 0.0;
+    if (o > lc.occ_lim) o = lc.occ_lim;
+    const uint64_t q = __double2ull_rn(__dmul_rn(o, lc.scale));
+    qt[ee] = q;
+    if (q) atomicAdd(cnt + ee, 1u);
+  }
+  // entries that were zero stay zero (+0.0 has the bit pattern of q = 0)
+}
+
+// ------------------------------------------------------------------------------------------
+// 3. exclusive scan of the per-event counts (two levels: block sums, then their scan)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_tot[BT_SCAN_BLOCK / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;   // inclusive over warps
+  }
+  __syncthreads();
+  const uint32_t before = (w > 0 ? warp_tot[w - 1] : 0) + x - v;
+  if (total) *total = warp_tot[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void __launch_bounds__(BT_SCAN_BLOCK)
+k_bt_scan_blocks(const uint32_t* __restrict__ cnt, int64_t n, uint32_t* __restrict__ ptr,
+                 uint32_t* __restrict__ block_sums) {
+  const int64_t e = (int64_t)blockIdx.x * BT_SCAN_BLOCK + threadIdx.x;
+  const uint32_t v = e < n ? cnt[e] : 0u;
+  uint32_t tot;
+  const uint32_t ex = block_excl_scan(v, &tot);
+  if (e < n) ptr[e] = ex;
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// single block: exclusive scan of the block sums (loops for many blocks)
+__global__ void __launch_bounds__(BT_SCAN_BLOCK)
+k_bt_scan_sums(uint32_t* __restrict__ block_sums, int64_t n_blocks, uint32_t* __restrict__ total) {
+  uint32_t carry = 0;
+  for (int64_t b0 = 0; b0 < n_blocks; b0 += BT_SCAN_BLOCK) {
+    const int64_t b = b0 + threadIdx.x;
+    const uint32_t v = b < n_blocks ? block_sums[b] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(v, &tot);
+    if (b < n_blocks) block_sums[b] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_bt_scan_add(uint32_t* __restrict__ ptr, int64_t n, const uint32_t* __restrict__ block_sums,
+                              const uint32_t* __restrict__ total) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) ptr[e] += block_sums[e / BT_SCAN_BLOCK];
+  if (e == n) ptr[n] = *total;
+}
+
+// ------------------------------------------------------------------------------------------
+// 4. CSR rows: one thread per event, layers in slot order (deterministic layout)
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_bt_fill(int32_t n_sel, const double* __restrict__ s_tab, int64_t catalogue,
+          const uint32_t* __restrict__ ptr, uint64_t* __restrict__ entries) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= catalogue) return;
+  uint32_t pos = ptr[e];
+  const uint32_t end = ptr[e + 1];
+  const uint64_t* qt = reinterpret_cast<const uint64_t*>(s_tab);
+  for (int i = 0; i < n_sel && pos < end; ++i) {
+    const uint64_t q = qt[(int64_t)i * catalogue + e];
+    if (q) entries[pos++] = ((uint64_t)i << 56) | q;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Stream
+// ------------------------------------------------------------------------------------------
+struct BtStream {
+  int64_t n_trials;
+  const int64_t* offsets;
+  int64_t n_events;
+  const int32_t* ids;
+  uint32_t catalogue;
+  const uint32_t* row_ptr;     // [catalogue + 1]
+  const uint64_t* entries;
+  int32_t n_sel;
+  const LayerConst* layers;    // device, indexed by layer id
+  BtLayers sel;                // slot -> layer id
+  double* ylt;                 // [n_sel][n_trials]
+  uint8_t* regimes;            // or nullptr
+  unsigned long long* queue;   // trial counter (zeroed before the launch)
+  int32_t trials_per_grab;
+  uint32_t* err;
+};
+
+__device__ __forceinline__ void smem_add_u128(unsigned long long* lo, unsigned long long* hi, uint64_t q) {
+  const unsigned long long old = atomicAdd(lo, (unsigned long long)q);
+  if (old + q < old) atomicAdd(hi, 1ull);
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_bt_stream(BtStream p) {
+  extern __shared__ __align__(16) unsigned long long bt_acc[];   // [WARPS][2][n_sel]
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ns = p.n_sel;
+  unsigned long long* lo = bt_acc + (int64_t)wid * 2 * ns;
+  unsigned long long* hi = lo + ns;
+  for (int i = lane; i < 2 * ns; i += 32) lo[i] = 0ull;
+  __syncwarp();
+  bool bad_id = false, bad_off = false;
+  while (true) {
+    unsigned long long t0 = 0;
+    if (lane == 0) t0 = atomicAdd(p.queue, (unsigned long long)p.trials_per_grab);
+    t0 = __shfl_sync(0xffffffffu, t0, 0);
+    if (t0 >= (unsigned long long)p.n_trials) break;
+    const int64_t t1 = min((int64_t)t0 + p.trials_per_grab, p.n_trials);
+    for (int64_t t = (int64_t)t0; t < t1; ++t) {
+      int64_t beg = __ldg(p.offsets + t), end = __ldg(p.offsets + t + 1);
+      if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; beg = end = 0; }
+      for (int64_t i0 = beg; i0 < end; i0 += 128) {
+        int ev[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + 32 * u + lane;
+          ev[u] = i < end ? __ldcs(p.ids + i) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + 32 * u + lane;
+          if (i >= end) continue;
+          const uint32_t e = (uint32_t)ev[u];
+          if (e >= p.catalogue) { bad_id = true; continue; }
+          const uint32_t rb = __ldg(p.row_ptr + e), re = __ldg(p.row_ptr + e + 1);
+          for (uint32_t r = rb; r < re; ++r) {
+            const uint64_t x = __ldg(p.entries + r);
+            const int s = (int)(x >> 56);
+            smem_add_u128(&lo[s], &hi[s], x & ((1ull << 56) - 1));
+          }
+        }
+      }
+      __syncwarp();
+      // aggregate terms of every layer on the exact sums; reset the accumulators
+      for (int i = lane; i < ns; i += 32) {
+        U128 S{lo[i], hi[i]};
+        lo[i] = 0ull;
+        hi[i] = 0ull;
+        const LayerConst lc = p.layers[p.sel.layer[i]];
+        uint8_t reg;
+        const double y = AccOps<U128>::finish(S, lc, reg);
+        p.ylt[(int64_t)i * p.n_trials + t] = y;
+        if (p.regimes) p.regimes[(int64_t)i * p.n_trials + t] = reg;
+      }
+      __syncwarp();
+    }
+  }
+  if (bad_id) atomicOr(p.err, DERR_EVENT_RANGE);
+  if (bad_off) atomicOr(p.err, DERR_OFFSETS);
+}
+
+}  // namespace ara
+
+// ------------------------------------------------------------------------------------------
+// Host: plan = scratch + autotuned schedule + CUDA graph of the whole run
+// ------------------------------------------------------------------------------------------
+using namespace ara;
+
+struct ara_plan {
+  Portfolio* pf = nullptr;
+  int64_t n_trials = 0, n_events = 0;
+  const int64_t* d_off = nullptr;
+  const int32_t* d_ids = nullptr;
+  std::vector<int32_t> sel;
+  double* d_ylt = nullptr;
+  uint8_t* d_reg = nullptr;
+  uint32_t* d_cnt = nullptr;
+  uint32_t* d_ptr = nullptr;
+  uint32_t* d_bsum = nullptr;
+  uint32_t* d_total = nullptr;
+  uint64_t* d_entries = nullptr;
+  unsigned long long* d_queue = nullptr;
+  int64_t n_blocks = 0;
+  int warps = 16, ctas_per_sm = 2, tpg = 2;
+  double tuned_ms = 0.0;
+  int max_le = 0;
+  int n_kernels = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+ara_status bt_prep(ara_plan& P, cudaStream_t s, bool fill, int* n_kernels) {
+  Portfolio& pf = *P.pf;
+  const int n_sel = (int)P.sel.size();
+  const int64_t C = pf.catalogue;
+  double* s_tab = reinterpret_cast<double*>(pf.d_q);      // [n_sel][C] scratch
+  int k = 0;
+  ARA_TRY(cudaMemsetAsync(s_tab, 0, sizeof(double) * (size_t)n_sel * C, s));
+  ARA_TRY(cudaMemsetAsync(P.d_cnt, 0, sizeof(uint32_t) * (size_t)C, s));
+  for (int slot = 0; slot < P.max_le; ++slot) {
+    BtScatter sc;
+    sc.n_sel = n_sel;
+    for (int i = 0; i < n_sel; ++i) {
+      const LayerConst& lc = pf.layers[P.sel[i]];
+      sc.elt[i] = slot < lc.elt_end - lc.elt_begin ? pf.layer_elts[lc.elt_begin + slot] : -1;
+    }
+    dim3 grid(32, n_sel);
+    if (pf.d_rec_loss32)
+      k_bt_scatter<float><<<grid, 256, 0, s>>>(sc, pf.d_rec_off, pf.d_rec_ids, pf.d_rec_loss32,
+                                               pf.d_elt_ret, pf.d_elt_lim, s_tab, C);
+    else
+      k_bt_scatter<double><<<grid, 256, 0, s>>>(sc, pf.d_rec_off, pf.d_rec_ids, pf.d_rec_loss,
+                                                pf.d_elt_ret, pf.d_elt_lim, s_tab, C);
+    ++k;
+  }
+  BtLayers bl;
+  bl.n_sel = n_sel;
+  for (int i = 0; i < n_sel; ++i) bl.layer[i] = P.sel[i];
+  k_bt_quantize<<<dim3((unsigned)((C + 255) / 256), n_sel), 256, 0, s>>>(bl, pf.d_layers, s_tab, C, P.d_cnt);
+  k_bt_scan_blocks<<<(unsigned)P.n_blocks, BT_SCAN_BLOCK, 0, s>>>(P.d_cnt, C, P.d_ptr, P.d_bsum);
+  k_bt_scan_sums<<<1, BT_SCAN_BLOCK, 0, s>>>(P.d_bsum, P.n_blocks, P.d_total);
+  k_bt_scan_add<<<(unsigned)((C + 1 + 255) / 256), 256, 0, s>>>(P.d_ptr, C, P.d_bsum, P.d_total);
+  k += 4;
+  if (fill) {
+    k_bt_fill<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(n_sel, s_tab, C, P.d_ptr, P.d_entries);
+    ++k;
+  }
+  ARA_TRY(cudaGetLastError());
+  if (n_kernels) *n_kernels = k;
+  return ARA_OK;
+}
+
+template <int W>
+ara_status bt_launch_w(ara_plan& P, const BtStream& bs, cudaStream_t s) {
+  const int smem = W * 2 * (int)P.sel.size() * 8;
+  const auto fn = k_bt_stream<W>;
+  if (smem > 48 * 1024)
+    ARA_TRY(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  fn<<<P.pf->n_sms * P.ctas_per_sm, W * 32, smem, s>>>(bs);
+  ARA_TRY(cudaGetLastError());
+  return ARA_OK;
+}
+
+ara_status bt_stream(ara_plan& P, cudaStream_t s) {
+  BtStream bs{};
+  bs.n_trials = P.n_trials;
+  bs.offsets = P.d_off;
+  bs.n_events = P.n_events;
+  bs.ids = P.d_ids;
+  bs.catalogue = (uint32_t)P.pf->catalogue;
+  bs.row_ptr = P.d_ptr;
+  bs.entries = P.d_entries;
+  bs.n_sel = (int32_t)P.sel.size();
+  bs.layers = P.pf->d_layers;
+  bs.sel.n_sel = bs.n_sel;
+  for (int i = 0; i < bs.n_sel; ++i) bs.sel.layer[i] = P.sel[i];
+  bs.ylt = P.d_ylt;
+  bs.regimes = P.d_reg;
+  bs.queue = P.d_queue;
+  bs.trials_per_grab = P.tpg;
+  bs.err = P.pf->d_err;
+  ARA_TRY(cudaMemsetAsync(P.d_queue, 0, sizeof(unsigned long long), s));
+  switch (P.warps) {
+    case 8: return bt_launch_w<8>(P, bs, s);
+    case 32: return bt_launch_w<32>(P, bs, s);
+    default: return bt_launch_w<16>(P, bs, s);
+  }
+}
+
+void bt_free(ara_plan* P) {
+  if (!P) return;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  void* ptrs[] = {P->d_cnt, P->d_ptr, P->d_bsum, P->d_total, P->d_entries, P->d_queue};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete P;
+}
+
+}  // namespace
+
+extern "C" {
+
+ara_status ara_plan_batched(ara_portfolio* pf_, int64_t n_trials, const int64_t* d_off,
+                            int64_t n_events, const int32_t* d_ids, int32_t n_sel_in,
+                            const int32_t* layer_sel, double* d_ylt, uint8_t* d_reg, int32_t flags,
+                            void* stream, ara_plan** out) {
+  Portfolio* pf = static_cast<Portfolio*>(pf_);
+  if (!out) return ARA_EINVAL;
+  *out = nullptr;
+  if (!pf || n_trials < 1 || n_events < 0 || !d_off || !d_ylt || (n_events > 0 && !d_ids))
+    return ARA_EINVAL;
+  if (flags & ~ARA_PLAN_AUTOTUNE) return ARA_EINVAL;
+  if (((uintptr_t)d_ids & 3) || ((uintptr_t)d_off & 7) || ((uintptr_t)d_ylt & 7)) return ARA_EINVAL;
+  if (pf->catalogue > 0xffffffffll) return ARA_ERANGE;
+  ara_plan* P = new (std::nothrow) ara_plan();
+  if (!P) return ARA_ENOMEM;
+  P->pf = pf;
+  P->n_trials = n_trials;
+  P->n_events = n_events;
+  P->d_off = d_off;
+  P->d_ids = d_ids ? d_ids : reinterpret_cast<const int32_t*>(d_off);
+  P->d_ylt = d_ylt;
+  P->d_reg = d_reg;
+  if (n_sel_in == 0 && layer_sel == nullptr) {
+    for (int32_t l = 0; l < pf->n_layers; ++l) P->sel.push_back(l);
+  } else {
+    if (n_sel_in < 0 || !layer_sel) { bt_free(P); return ARA_EINVAL; }
+    for (int32_t i = 0; i < n_sel_in; ++i) {
+      if (layer_sel[i] < 0 || layer_sel[i] >= pf->n_layers) { bt_free(P); return ARA_EINVAL; }
+      P->sel.push_back(layer_sel[i]);
+    }
+  }
+  if (P->sel.empty()) { bt_free(P); return ARA_EINVAL; }
+  if ((int)P->sel.size() > BT_MAX_LAYERS || (int)P->sel.size() > pf->n_layers ||
+      (int64_t)P->sel.size() * pf->catalogue >= ((int64_t)1 << 32)) {   // 32-bit row pointers
+    bt_free(P);
+    return ARA_ERANGE;
+  }
+  for (int32_t l : P->sel)
+    P->max_le = std::max(P->max_le, pf->layers[l].elt_end - pf->layers[l].elt_begin);
+  DeviceGuard g(pf->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t C = pf->catalogue;
+  P->n_blocks = (C + BT_SCAN_BLOCK - 1) / BT_SCAN_BLOCK;
+  auto fail = [&](ara_status st) {
+    cudaStreamSynchronize(s);
+    bt_free(P);
+    return st;
+  };
+  if (cudaMalloc(&P->d_cnt, 4 * (size_t)C) != cudaSuccess ||
+      cudaMalloc(&P->d_ptr, 4 * (size_t)(C + 1)) != cudaSuccess ||
+      cudaMalloc(&P->d_bsum, 4 * (size_t)P->n_blocks) != cudaSuccess ||
+      cudaMalloc(&P->d_total, 4) != cudaSuccess ||
+      cudaMalloc(&P->d_queue, sizeof(unsigned long long)) != cudaSuccess)
+    return fail(ARA_ENOMEM);
+  // size the table once: the counts depend on the portfolio only
+  ara_status st = bt_prep(*P, s, false, nullptr);
+  if (st != ARA_OK) return fail(st);
+  uint32_t total = 0;
+  if (cudaMemcpyAsync(&total, P->d_total, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(ARA_ECUDA);
+  if (cudaMalloc(&P->d_entries, 8 * (size_t)std::max<uint32_t>(total, 1)) != cudaSuccess)
+    return fail(ARA_ENOMEM);
+  if ((st = bt_prep(*P, s, true, nullptr)) != ARA_OK) return fail(st);
+  // schedule: the fastest of the candidates on these inputs, or a fixed default
+  if (flags & ARA_PLAN_AUTOTUNE) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return fail(ARA_ECUDA);
+    const int cand_w[] = {8, 16, 32};
+    const int cand_c[] = {1, 2, 4};
+    const int cand_t[] = {1, 4};
+    float best = 1e30f;
+    int bw = P->warps, bc = P->ctas_per_sm, bt = P->tpg;
+    for (int w : cand_w)
+      for (int c : cand_c)
+        for (int t : cand_t) {
+          const int64_t smem = (int64_t)w * 2 * (int64_t)P->sel.size() * 8;
+          if (smem * c > (int64_t)pf->max_smem_block || w * 32 * c > 2048) continue;
+          P->warps = w;
+          P->ctas_per_sm = c;
+          P->tpg = t;
+          float ms = 0.f, tot = 0.f;
+          for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(a, s);
+            if ((st = bt_stream(*P, s)) != ARA_OK) {
+              cudaEventDestroy(a);
+              cudaEventDestroy(b);
+              return fail(st);
+            }
+            cudaEventRecord(b, s);
+            if (cudaEventSynchronize(b) != cudaSuccess) return fail(ARA_ECUDA);
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0) tot += ms;
+          }
+          if (tot / 2 < best) { best = tot / 2; bw = w; bc = c; bt = t; }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    P->warps = bw;
+    P->ctas_per_sm = bc;
+    P->tpg = bt;
+    P->tuned_ms = best;
+  }
+  // capture the whole run into a graph on a private stream
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return fail(ARA_ECUDA);
+  const bool timing_was = timing_suspend();
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  int nk = 0;
+  if (ok) ok = bt_prep(*P, cs, true, &nk) == ARA_OK;
+  if (ok) ok = bt_stream(*P, cs) == ARA_OK;
+  cudaGraph_t graph = nullptr;
+  const bool ended = cudaStreamEndCapture(cs, &graph) == cudaSuccess;
+  timing_resume(timing_was);
+  cudaStreamDestroy(cs);
+  if (!ok || !ended || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return fail(ARA_ECUDA);
+  }
+  P->graph = graph;
+  P->n_kernels = nk + 1;
+  if (cudaGraphInstantiate(&P->exec, graph, 0) != cudaSuccess) return fail(ARA_ECUDA);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(ARA_ECUDA);
+  *out = P;
+  return ARA_OK;
+}
+
+ara_status ara_plan_launch(ara_plan* P, void* stream) {
+  if (!P || !P->exec) return ARA_EINVAL;
+  DeviceGuard g(P->pf->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  LaunchScope ls(ARA_K_BATCHED, s, P->n_kernels);
+  ARA_TRY(cudaGraphLaunch(P->exec, s));
+  return ARA_OK;
+}
+
+ara_status ara_plan_info(ara_plan* P, int32_t* warps, int32_t* bpsm, int32_t* tpg, double* ms) {
+  if (!P) return ARA_EINVAL;
+  if (warps) *warps = P->warps;
+  if (bpsm) *bpsm = P->ctas_per_sm;
+  if (tpg) *tpg = P->tpg;
+  if (ms) *ms = P->tuned_ms;
+  return ARA_OK;
+}
+
+void ara_plan_destroy(ara_plan* P) {
+  if (!P) return;
+  DeviceGuard g(P->pf->device);
+  cudaDeviceSynchronize();
+  bt_free(P);
+}
+
+}  // extern "C"

@@ -34,6 +34,9 @@ enum : uint32_t { DERR_EVENT_RANGE = 1u, DERR_OFFSETS = 2u, DERR_TIMEOUT = 4u };
 extern std::atomic<int64_t> g_launches;
 void timing_begin(int kclass, cudaStream_t s);
 void timing_end(int kclass, cudaStream_t s);
+// switch event timing off (e.g. while a stream is captured into a graph); returns the old state
+bool timing_suspend();
+void timing_resume(bool was_on);
 
 // RAII helper: events around every launch of a kernel class (when timing is enabled) and
 // one count per launch.
@@ -51,7 +54,7 @@ struct LaunchScope {
 // Per-layer constants of the folded path
 // ------------------------------------------------------------------------------------------
 // Occurrence losses o(e) are kept as unsigned fixed point q(e) = round(o(e) * 2^frac_bits),
-// q(e) <= 2^61, and trial sums are exact 128-bit integer sums of q.  The aggregate terms are
+// q(e) < 2^55, and trial sums are exact 128-bit integer sums of q.  The aggregate terms are
 // applied to the exact sum in the same fixed point; only the final year loss is converted to
 // double.
 struct LayerConst {

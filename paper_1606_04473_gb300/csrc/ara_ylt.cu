@@ -12,7 +12,7 @@
 #include <atomic>
 #include <cstdio>
 
-#include "ara_internal.cuh"
+#include "ara_device.cuh"
 
 namespace ara {
 
@@ -20,21 +20,12 @@ constexpr int FOLD_TILE = 2048;
 constexpr int FOLD_THREADS = 256;
 constexpr int YLT_THREADS = 1024;
 constexpr int MAX_SEL = 256;
-constexpr unsigned FULL = 0xffffffffu;
 
 struct SelList {
   int32_t n;
   int32_t idx[MAX_SEL];
 };
 
-// Retention/limit clamp C(x; R, L) = min(max(x - R, 0), L), evaluated in the same order of
-// IEEE operations as the FP64 reference so that results agree bit for bit.
-__device__ __forceinline__ double clamp_terms(double x, double R, double L) {
-  double ex = __dsub_rn(x, R);
-  if (ex < 0.0) ex = 0.0;
-  if (ex > L) ex = L;
-  return ex;
-}
 
 __device__ __forceinline__ int64_t lower_bound_ids(const int32_t* __restrict__ ids, int64_t lo,
                                                    int64_t hi, int64_t v) {
@@ -130,80 +121,6 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ rec_off, const int32_t* __
 // ------------------------------------------------------------------------------------------
 // Stream helpers
 // ------------------------------------------------------------------------------------------
-struct U128 {
-  uint64_t lo, hi;
-};
-
-__device__ __forceinline__ void add_u64(U128& a, uint64_t v) {
-  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(a.lo), "+l"(a.hi) : "l"(v));
-}
-__device__ __forceinline__ void add_u128(U128& a, uint64_t lo, uint64_t hi) {
-  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(lo), "l"(hi));
-}
-__device__ __forceinline__ bool le_u128(uint64_t alo, uint64_t ahi, uint64_t blo, uint64_t bhi) {
-  return ahi < bhi || (ahi == bhi && alo <= blo);
-}
-
-template <typename Acc> struct AccOps;
-template <> struct AccOps<U128> {
-  static __device__ __forceinline__ U128 zero() { return U128{0ull, 0ull}; }
-  static __device__ __forceinline__ void add(U128& a, uint64_t v) { add_u64(a, v); }
-  // add lo + hi * 2^32 (the split sums of up to 16 table values; hi < 2^36)
-  template <int NV>
-  static __device__ __forceinline__ void add_split(U128& a, uint64_t lo, uint64_t hi, const uint64_t (&)[NV]) {
-    add_u64(a, lo);
-    add_u128(a, hi << 32, hi >> 32);
-  }
-  static __device__ __forceinline__ U128 warp_sum(U128 a) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const uint64_t l = __shfl_xor_sync(FULL, a.lo, o), h = __shfl_xor_sync(FULL, a.hi, o);
-      add_u128(a, l, h);
-    }
-    return a;
-  }
-  static __device__ __forceinline__ U128 shfl(U128 a, int src) {
-    return U128{__shfl_sync(FULL, a.lo, src), __shfl_sync(FULL, a.hi, src)};
-  }
-  // Aggregate terms on the exact fixed-point sum; only the result is rounded to double.
-  static __device__ __forceinline__ double finish(U128 S, const LayerConst& lc, uint8_t& reg) {
-    if (le_u128(S.lo, S.hi, lc.agg_ret_lo, lc.agg_ret_hi)) { reg = 0; return 0.0; }
-    U128 d = S;
-    asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;" : "+l"(d.lo), "+l"(d.hi)
-        : "l"(lc.agg_ret_lo), "l"(lc.agg_ret_hi));
-    if (le_u128(lc.agg_lim_lo, lc.agg_lim_hi, d.lo, d.hi)) {
-      reg = (d.lo == lc.agg_lim_lo && d.hi == lc.agg_lim_hi) ? 0 : 2;
-      return lc.agg_lim;
-    }
-    reg = 1;
-    const double v = __dadd_rn(__dmul_rn(__ull2double_rn(d.hi), 18446744073709551616.0),
-                               __ull2double_rn(d.lo));
-    return __dmul_rn(v, lc.inv_scale);
-  }
-};
-template <> struct AccOps<double> {
-  static __device__ __forceinline__ double zero() { return 0.0; }
-  static __device__ __forceinline__ void add(double& a, uint64_t v) {
-    a = __dadd_rn(a, __longlong_as_double((long long)v));
-  }
-  template <int NV>
-  static __device__ __forceinline__ void add_split(double& a, uint64_t, uint64_t, const uint64_t (&v)[NV]) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) a = __dadd_rn(a, __longlong_as_double((long long)v[i]));
-  }
-  static __device__ __forceinline__ double warp_sum(double a) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) a = __dadd_rn(a, __shfl_xor_sync(FULL, a, o));
-    return a;
-  }
-  static __device__ __forceinline__ double shfl(double a, int src) { return __shfl_sync(FULL, a, src); }
-  static __device__ __forceinline__ double finish(double S, const LayerConst& lc, uint8_t& reg) {
-    const double ex = __dsub_rn(S, lc.agg_ret);
-    reg = (ex > 0.0 && ex < lc.agg_lim) ? 1 : (ex > lc.agg_lim ? 2 : 0);
-    return clamp_terms(S, lc.agg_ret, lc.agg_lim);
-  }
-};
-
 // Coarse hit bitmap word cw: coarse bit i is the OR of the exact bits of events
 // [(32 cw + i) << shift, (32 cw + i + 1) << shift).
 __device__ __forceinline__ uint32_t coarsen_word(const uint32_t* __restrict__ src, int64_t cw,
