@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-portfolio measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-requests", type=int, default=200)
     return ap.parse_args()
 
 
@@ -349,6 +351,7 @@ def run_ours(args, rank, ws, local):
     torch.cuda.empty_cache()
     adjoint_line = None if args.no_adjoint else measure_adjoint(rank)
     batched_line = None if args.no_batched else measure_batched(rank)
+    serving_line = None if args.no_serving else measure_serving(rank, args.serving_requests)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -378,6 +381,7 @@ def run_ours(args, rank, ws, local):
                         "ms_per_step_direct": (e2e_direct * 1e3 if e2e_direct != float("inf") else None)},
                 "adjoint": adjoint_line,
                 "batched": batched_line,
+                "serving": serving_line,
                 "gpu_launches": launches,
                 "clocks": clk.summary(),
                 "results": {"pml100": float(pml[0, 0]), "pml250": float(pml[0, 1]),
@@ -478,6 +482,80 @@ def measure_batched(rank: int, reps: int = 5):
            "plan_build_s": round(t_plan, 3)}
     plan.close()
     g.close()
+    return out
+
+
+def measure_serving(rank: int, n_requests: int = 200, workers: int = 4):
+    """Serving: a seeded Poisson stream (200 requests/s, 32 tenants) of risk queries over a
+    resident pool of 500 ELTs and a resident YET of 1e6 trials x Poisson(1000) events (1-32
+    layers of 5-20 ELTs each, slices of 1e4-1e6 trials, 20 % with the adjoint), served by the
+    native server (continuous admission by device memory, requests overlapping on separate
+    streams), against the same queries run one at a time."""
+    import threading
+    import torch
+    import paper_1606_04473_gb300 as ara
+    import synth
+    pool_t = synth.serving_pool(0)
+    ids_h = None
+    yet = synth.serving_yet(rank)
+    pool = ara.Portfolio.from_tables(pool_t)
+    off = torch.from_numpy(yet.offsets).cuda()
+    ev = torch.from_numpy(yet.event_ids).cuda()
+    del yet.event_ids
+    trace = synth.serving_trace(pool_t, off.numel() - 1, n_requests, 200.0, seed=rank)
+    offs = yet.offsets
+    lookups = [sum(len(l) for l in q["layer_elts"]) * int(offs[q["trials"][1]] - offs[q["trials"][0]])
+               for q in trace]
+
+    def query_args(q):
+        return dict(layer_elts=q["layer_elts"], occ_ret=q["occ_ret"], occ_lim=q["occ_lim"],
+                    agg_ret=q["agg_ret"], agg_lim=q["agg_lim"], trials=q["trials"],
+                    return_periods=[100.0, 250.0], tvar_levels=[0.99], want_mean=True,
+                    want_adjoint=q["want_adjoint"], adjoint_level=0.99,
+                    flags=ara.ARA_RUN_BATCHED if len(q["layer_elts"]) >= 4 else 0, tenant=q["tenant"])
+
+    def serve(max_concurrent, paced):
+        srv = ara.Server(pool, off, ev, max_concurrent=max_concurrent)
+        # warm-up: one small request
+        srv.wait(srv.submit(**dict(query_args(trace[0]), trials=(0, 1000))))
+        tickets = [None] * len(trace)
+        t_start = time.perf_counter()
+
+        def feeder():
+            for k, q in enumerate(trace):
+                if paced:
+                    d = q["arrival"] - (time.perf_counter() - t_start)
+                    if d > 0:
+                        time.sleep(d)
+                tickets[k] = srv.submit(**query_args(q))
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        res = [srv.wait(t) for t in tickets]
+        makespan = time.perf_counter() - t_start
+        stats = srv.stats()
+        srv.close()
+        lat = np.array([r["latency_s"] for r in res]) * 1e3
+        return res, makespan, lat, stats
+
+    res_s, mk_s, lat_s, st_s = serve(workers, paced=True)
+    res_1, mk_1, lat_1, st_1 = serve(1, paced=True)
+    same = all(np.array_equal(a["pml"], b["pml"]) and np.array_equal(a["tvar"], b["tvar"]) and
+               np.array_equal(a["mean"], b["mean"]) for a, b in zip(res_s, res_1))
+    tot = float(sum(lookups))
+    out = {"workload": f"{n_requests} requests, Poisson 200/s, 32 tenants; 1-32 layers x 5-20 ELTs of a "
+                       "500-ELT pool; slices of 1e4-1e6 trials of a 1e6 x Poisson(1000) YET; 20% adjoint",
+           "served": {"workers": workers, "p50_ms": round(float(np.percentile(lat_s, 50)), 2),
+                      "p99_ms": round(float(np.percentile(lat_s, 99)), 2),
+                      "makespan_s": round(mk_s, 3), "lookups_per_s": tot / mk_s,
+                      "peak_running": st_s["peak_running"]},
+           "one_at_a_time": {"p50_ms": round(float(np.percentile(lat_1, 50)), 2),
+                             "p99_ms": round(float(np.percentile(lat_1, 99)), 2),
+                             "makespan_s": round(mk_1, 3), "lookups_per_s": tot / mk_1},
+           "throughput_gain": round(mk_1 / mk_s, 3), "results_identical": bool(same),
+           "total_lookups": tot}
+    pool.close()
     return out
 
 

@@ -95,8 +95,25 @@ ARA_API ara_status ara_create_portfolio(int64_t catalogue_size, int32_t n_elts,
                                 const double* agg_ret, const double* agg_lim, int32_t flags,
                                 ara_portfolio** out);
 
-/* Release every device and host resource of the portfolio (synchronises its device). */
+/* Release every device and host resource of the portfolio (synchronises its device; for a
+ * layer set, only the stream it was created on). */
 ARA_API void ara_destroy_portfolio(ara_portfolio* pf);
+
+/*
+ * A layer set: new layers (Eq. 3) over the ELTs of a resident portfolio `pool` (the ELTs and
+ * their terms stay where they are; only the layers, their terms and their fold workspace,
+ * n_layers x catalogue x ~8.3 bytes, are new).  Allocation and upload are asynchronous on
+ * `stream` (stream-ordered allocator), so building a layer set does not stall other streams.
+ * The result is used like any portfolio (ara_run_ylt, ara_adjoint, ...) and released with
+ * ara_destroy_portfolio; the pool must outlive it.  Layer arguments as in ara_create_portfolio
+ * (n_layers >= 1), ELT indices refer to the pool.
+ * Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA.
+ */
+ARA_API ara_status ara_create_layer_set(ara_portfolio* pool, int32_t n_layers,
+                                        const int32_t* layer_elt_offsets,
+                                        const int32_t* layer_elt_ids, const double* occ_ret,
+                                        const double* occ_lim, const double* agg_ret,
+                                        const double* agg_lim, void* stream, ara_portfolio** out);
 
 /* ---------------------------------------------------------------------------------------
  * YLT: Algorithm 1 (for each layer) around Algorithm 3 (for each trial, event, ELT).
@@ -113,6 +130,10 @@ ARA_API void ara_destroy_portfolio(ara_portfolio* pf);
                                  (measurement) */
 #define ARA_RUN_LDG       8   /* folded, YET read by per-trial 16-byte register loads instead of
                                  the per-warp TMA bulk-copy ring (measurement) */
+#define ARA_RUN_BATCHED  32   /* all selected layers in one YET pass (event-major table of every
+                                 layer's occurrence losses, one persistent stream kernel); same
+                                 results; at most 255 selected layers, no repeats beyond the
+                                 portfolio's layer count (ARA_ERANGE) */
 #define ARA_RUN_HOST_DIRECT 16 /* ara_run_ylt_host only: the kernel reads the (pinned, device-
                                  mapped) host YET in place over the CPU-GPU link instead of
                                  staging it with copies; ARA_EINVAL if the host arrays are not
@@ -202,6 +223,66 @@ ARA_API ara_status ara_plan_launch(ara_plan* plan, void* stream);
 ARA_API ara_status ara_plan_info(ara_plan* plan, int32_t* warps, int32_t* blocks_per_sm,
                                  int32_t* trials_per_grab, double* tuned_ms);
 ARA_API void ara_plan_destroy(ara_plan* plan);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: many risk queries over resident ELTs and a resident YET, on one GPU (the single-GPU
+ * form of the paper's multi-tenant GPUs, Section V-D).
+ * --------------------------------------------------------------------------------------- */
+
+typedef struct ara_server ara_server;
+
+/* One risk query: layers (Eq. 3) over the server pool's ELTs, evaluated on the trials
+ * [trial_begin, trial_end) of the resident YET.  All arrays are host memory, copied at submit. */
+typedef struct ara_query {
+  int32_t n_layers;                 /* >= 1 */
+  const int32_t* layer_elt_offsets; /* [n_layers + 1] */
+  const int32_t* layer_elt_ids;     /* ELT indices into the pool */
+  const double* occ_ret;            /* [n_layers] each */
+  const double* occ_lim;
+  const double* agg_ret;
+  const double* agg_lim;
+  int64_t trial_begin, trial_end;
+  int32_t n_rp;                     /* PML return periods */
+  const double* return_periods;
+  int32_t n_tvar;                   /* TVaR levels */
+  const double* tvar_levels;
+  int32_t want_mean;                /* mean year loss per layer */
+  int32_t want_adjoint;             /* layer-term gradients of mean and TVaR (adjoint_level) */
+  double adjoint_level;
+  int32_t flags;                    /* ARA_RUN_BATCHED or 0 */
+  int32_t tenant;                   /* caller's label, not interpreted */
+} ara_query;
+
+/*
+ * Start a server over a resident pool portfolio (its ELTs) and a resident device YET.  Up to
+ * max_concurrent (1..64) requests run at once, each on its own stream; a request is admitted,
+ * first come first served, when a worker is free and its estimated device memory fits
+ * memory_budget bytes together with the requests already running (<= 0: 80 % of the device's
+ * free memory now).  A request larger than the budget runs alone.  The pool and the YET must
+ * outlive the server.  Results of a request do not depend on what else runs.
+ */
+ARA_API ara_status ara_server_create(ara_portfolio* pool, int64_t n_trials,
+                                     const int64_t* d_trial_offsets, int64_t n_events,
+                                     const int32_t* d_event_ids, int32_t max_concurrent,
+                                     int64_t memory_budget, ara_server** out);
+/* Queue a query (validated and copied now; ARA_EINVAL on bad arguments); returns a ticket. */
+ARA_API ara_status ara_server_submit(ara_server* server, const ara_query* query, int64_t* ticket);
+/*
+ * Wait for a ticket and collect its results (each pointer may be NULL):
+ *   h_pml [n_layers][n_rp], h_tvar [n_layers][n_tvar], h_mean [n_layers],
+ *   h_grad_layer [2][n_layers][4] (mean / TVaR objective; d/dOccR, OccL, AggR, AggL),
+ *   h_times [3]: seconds queued, running, and from submit to completion.
+ * Returns the request's status.  A ticket can be waited for once.
+ */
+ARA_API ara_status ara_server_wait(ara_server* server, int64_t ticket, double* h_pml,
+                                   double* h_tvar, double* h_mean, double* h_grad_layer,
+                                   double* h_times);
+/* Requests queued or running now, the largest number ever running at once, the largest
+ * estimated memory ever admitted at once, and the budget. */
+ARA_API ara_status ara_server_stats(ara_server* server, int32_t* queued_or_running,
+                                    int32_t* peak_running, int64_t* peak_bytes, int64_t* budget);
+/* Finish every queued request, then stop the workers and release the server. */
+ARA_API void ara_server_destroy(ara_server* server);
 
 /* ---------------------------------------------------------------------------------------
  * Adjoint: sensitivities of the risk metrics (Section IV-A) to the financial terms and the

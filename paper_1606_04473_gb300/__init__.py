@@ -28,6 +28,20 @@ ARA_STATIC_SELECT_BYTES = 4 << 20
 ARA_LOSSES_F32, ARA_DENSE_TABLES = 1, 2
 ARA_RUN_FOLDED, ARA_RUN_PER_ELT, ARA_RUN_NO_FILTER, ARA_RUN_F64_SUM, ARA_RUN_LDG = 0, 1, 2, 4, 8
 ARA_RUN_HOST_DIRECT = 16
+ARA_RUN_BATCHED = 32
+
+
+class Query(ctypes.Structure):
+    """ara_query (include/ara.h)."""
+    _fields_ = [("n_layers", ctypes.c_int32), ("layer_elt_offsets", ctypes.c_void_p),
+                ("layer_elt_ids", ctypes.c_void_p), ("occ_ret", ctypes.c_void_p),
+                ("occ_lim", ctypes.c_void_p), ("agg_ret", ctypes.c_void_p),
+                ("agg_lim", ctypes.c_void_p), ("trial_begin", ctypes.c_int64),
+                ("trial_end", ctypes.c_int64), ("n_rp", ctypes.c_int32),
+                ("return_periods", ctypes.c_void_p), ("n_tvar", ctypes.c_int32),
+                ("tvar_levels", ctypes.c_void_p), ("want_mean", ctypes.c_int32),
+                ("want_adjoint", ctypes.c_int32), ("adjoint_level", ctypes.c_double),
+                ("flags", ctypes.c_int32), ("tenant", ctypes.c_int32)]
 ARA_K_FOLD, ARA_K_YLT, ARA_K_SELECT, ARA_K_ADJOINT, ARA_K_BATCHED = 0, 1, 2, 3, 4
 ARA_PLAN_AUTOTUNE = 1
 
@@ -75,6 +89,19 @@ def lib() -> ctypes.CDLL:
     L.ara_plan_info.restype = i32
     L.ara_plan_destroy.argtypes = [P]
     L.ara_plan_destroy.restype = None
+    L.ara_create_layer_set.argtypes = [P, i32, P, P, P, P, P, P, P, ctypes.POINTER(P)]
+    L.ara_create_layer_set.restype = i32
+    L.ara_server_create.argtypes = [P, i64, P, i64, P, i32, i64, ctypes.POINTER(P)]
+    L.ara_server_create.restype = i32
+    L.ara_server_submit.argtypes = [P, ctypes.POINTER(Query), ctypes.POINTER(i64)]
+    L.ara_server_submit.restype = i32
+    L.ara_server_wait.argtypes = [P, i64, P, P, P, P, P]
+    L.ara_server_wait.restype = i32
+    L.ara_server_stats.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                   ctypes.POINTER(i64)]
+    L.ara_server_stats.restype = i32
+    L.ara_server_destroy.argtypes = [P]
+    L.ara_server_destroy.restype = None
     L.ara_adjoint.argtypes = [P, i64, P, i64, P, i32, P, P, P, d, P, P, P, P, P]
     L.ara_adjoint.restype = i32
     L.ara_adjoint_accumulate.argtypes = [P, i64, P, i64, P, i32, P, P, P, d, P, P, P, P, P, P]
@@ -283,6 +310,25 @@ class Portfolio:
         _check(st, "ara_adjoint_accumulate")
         return out
 
+    def layer_set(self, layer_elts, occ_ret, occ_lim, agg_ret, agg_lim, stream=None) -> "Portfolio":
+        """New layers over this portfolio's resident ELTs (ara_create_layer_set)."""
+        loff = np.zeros(len(layer_elts) + 1, dtype=np.int32)
+        loff[1:] = np.cumsum([len(l) for l in layer_elts])
+        lel = np.ascontiguousarray([j for l in layer_elts for j in l], dtype=np.int32)
+        f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+        orr, ol, ar, al = f(occ_ret), f(occ_lim), f(agg_ret), f(agg_lim)
+        h = ctypes.c_void_p()
+        st = lib().ara_create_layer_set(self._h, len(layer_elts), _np_ptr(loff), _np_ptr(lel), _np_ptr(orr),
+                                        _np_ptr(ol), _np_ptr(ar), _np_ptr(al), _stream_handle(stream),
+                                        ctypes.byref(h))
+        _check(st, "ara_create_layer_set")
+        ls = Portfolio.__new__(Portfolio)
+        ls._h, ls._keep, ls._pool = h, [loff, lel], self
+        ls.catalogue, ls.n_layers, ls.n_elts = self.catalogue, len(layer_elts), self.n_elts
+        ls.layer_elts = [list(map(int, l)) for l in layer_elts]
+        ls.elt_nnz, ls.n_records = self.elt_nnz, self.n_records
+        return ls
+
     def check(self, stream=None):
         _check(lib().ara_check(self._h, _stream_handle(stream)), "ara_check")
 
@@ -324,6 +370,72 @@ class BatchedPlan:
     def close(self):
         if getattr(self, "_h", None):
             lib().ara_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Native request server over this pool's resident ELTs and a resident device YET
+    (ara_server_*).  submit() queues a query and returns a ticket; wait() returns its results."""
+
+    def __init__(self, pool: Portfolio, offsets, event_ids, max_concurrent: int = 4,
+                 memory_budget: int = 0):
+        import torch
+        self._keep = (pool, offsets, event_ids)
+        self.n_trials = offsets.numel() - 1
+        h = ctypes.c_void_p()
+        st = lib().ara_server_create(pool._h, self.n_trials, _dev_ptr(offsets, torch.int64, "offsets"),
+                                     event_ids.numel(), _dev_ptr(event_ids, torch.int32, "event_ids"),
+                                     int(max_concurrent), int(memory_budget), ctypes.byref(h))
+        _check(st, "ara_server_create")
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, layer_elts, occ_ret, occ_lim, agg_ret, agg_lim, trials, return_periods=(),
+               tvar_levels=(), want_mean=False, want_adjoint=False, adjoint_level=0.99, flags=0,
+               tenant=0) -> int:
+        loff = np.zeros(len(layer_elts) + 1, dtype=np.int32)
+        loff[1:] = np.cumsum([len(l) for l in layer_elts])
+        lel = np.ascontiguousarray([j for l in layer_elts for j in l] or [0], dtype=np.int32)
+        f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+        arrs = [loff, lel, f(occ_ret), f(occ_lim), f(agg_ret), f(agg_lim), f(return_periods or [0.0]),
+                f(tvar_levels or [0.0])]
+        q = Query(len(layer_elts), *[a.ctypes.data for a in arrs[:6]], int(trials[0]), int(trials[1]),
+                  len(return_periods), arrs[6].ctypes.data, len(tvar_levels), arrs[7].ctypes.data,
+                  int(want_mean), int(want_adjoint), float(adjoint_level), int(flags), int(tenant))
+        t = ctypes.c_int64()
+        _check(lib().ara_server_submit(self._h, ctypes.byref(q), ctypes.byref(t)), "ara_server_submit")
+        self._shapes[t.value] = (len(layer_elts), len(return_periods), len(tvar_levels), want_mean,
+                                 want_adjoint)
+        return t.value
+
+    def wait(self, ticket: int):
+        nl, nr, nt, wm, wa = self._shapes.pop(ticket)
+        pml, tvar = np.zeros((nl, nr)), np.zeros((nl, nt))
+        mean = np.zeros(nl) if wm else None
+        grad = np.zeros((2, nl, 4)) if wa else None
+        times = np.zeros(3)
+        st = lib().ara_server_wait(self._h, ticket, _np_ptr(pml), _np_ptr(tvar), _np_ptr(mean),
+                                   _np_ptr(grad), _np_ptr(times))
+        _check(st, "request")
+        return {"pml": pml, "tvar": tvar, "mean": mean, "grad_layer": grad,
+                "queued_s": times[0], "run_s": times[1], "latency_s": times[2]}
+
+    def stats(self):
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        c, d = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ara_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                      ctypes.byref(d)), "ara_server_stats")
+        return {"in_flight": a.value, "peak_running": b.value, "peak_bytes": c.value, "budget": d.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ara_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -135,12 +135,24 @@ static void layer_scale(Portfolio& pf, LayerConst& lc) {
 
 static void free_portfolio(ara_portfolio* p) {
   if (!p) return;
-  void* ptrs[] = {p->d_rec_off, p->d_rec_ids, p->d_rec_orig, p->d_rec_loss, p->d_rec_loss32, p->d_elt_ret,
-                  p->d_elt_lim, p->d_layer_elts, p->d_layers, p->d_dense, p->d_q, p->d_bits, p->d_cbits,
-                  p->d_err, p->d_stage_ids[0], p->d_stage_ids[1], p->d_stage_off[0],
-                  p->d_stage_off[1], p->d_ylt_full};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  if (p->borrowed_elts) {
+    // a layer set: its own buffers came from the stream-ordered allocator; the ELT tables
+    // belong to the pool
+    void* own[] = {p->d_layer_elts, p->d_layers, p->d_q, p->d_bits, p->d_cbits, p->d_err};
+    for (void* q : own)
+      if (q) cudaFreeAsync(q, p->owner_stream);
+    void* staged[] = {p->d_stage_ids[0], p->d_stage_ids[1], p->d_stage_off[0], p->d_stage_off[1],
+                      p->d_ylt_full};
+    for (void* q : staged)
+      if (q) cudaFree(q);
+  } else {
+    void* ptrs[] = {p->d_rec_off, p->d_rec_ids, p->d_rec_orig, p->d_rec_loss, p->d_rec_loss32,
+                    p->d_elt_ret, p->d_elt_lim, p->d_layer_elts, p->d_layers, p->d_dense, p->d_q,
+                    p->d_bits, p->d_cbits, p->d_err, p->d_stage_ids[0], p->d_stage_ids[1],
+                    p->d_stage_off[0], p->d_stage_off[1], p->d_ylt_full};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+  }
   for (int i = 0; i < 2; ++i) {
     if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
     if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
@@ -369,8 +381,103 @@ ara_status ara_create_portfolio(int64_t C, int32_t n_elts, const int64_t* rec_of
 void ara_destroy_portfolio(ara_portfolio* pf) {
   if (!pf) return;
   DeviceGuard g(pf->device);
-  cudaDeviceSynchronize();
+  if (pf->borrowed_elts) cudaStreamSynchronize(pf->owner_stream);
+  else cudaDeviceSynchronize();
   free_portfolio(pf);
+}
+
+static ara_status validate_layers(const Portfolio& pool, int32_t n_layers, const int32_t* layer_off,
+                                  const int32_t* layer_elts, const double* occ_ret,
+                                  const double* occ_lim, const double* agg_ret,
+                                  const double* agg_lim) {
+  if (n_layers < 1 || !layer_off || !occ_ret || !occ_lim || !agg_ret || !agg_lim) return ARA_EINVAL;
+  if (layer_off[0] != 0) return ARA_EINVAL;
+  for (int32_t l = 0; l < n_layers; ++l) {
+    if (layer_off[l + 1] < layer_off[l]) return ARA_EINVAL;
+    if (!finite_nonneg(occ_ret[l]) || !limit_ok(occ_lim[l]) || !finite_nonneg(agg_ret[l]) ||
+        !limit_ok(agg_lim[l]))
+      return ARA_EINVAL;
+  }
+  if (layer_off[n_layers] > 0 && !layer_elts) return ARA_EINVAL;
+  for (int32_t k = 0; k < layer_off[n_layers]; ++k)
+    if (layer_elts[k] < 0 || layer_elts[k] >= pool.n_elts) return ARA_EINVAL;
+  return ARA_OK;
+}
+
+ara_status ara_create_layer_set(ara_portfolio* pool, int32_t n_layers, const int32_t* layer_off,
+                                const int32_t* layer_elts, const double* occ_ret,
+                                const double* occ_lim, const double* agg_ret, const double* agg_lim,
+                                void* stream, ara_portfolio** out) {
+  if (!out) return ARA_EINVAL;
+  *out = nullptr;
+  if (!pool || pool->borrowed_elts) return ARA_EINVAL;
+  ara_status st = validate_layers(*pool, n_layers, layer_off, layer_elts, occ_ret, occ_lim, agg_ret, agg_lim);
+  if (st != ARA_OK) return st;
+  ara_portfolio* p = new (std::nothrow) ara_portfolio();
+  if (!p) return ARA_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  p->borrowed_elts = true;
+  p->owner_stream = s;
+  p->device = pool->device;
+  p->n_sms = pool->n_sms;
+  p->max_smem_block = pool->max_smem_block;
+  p->catalogue = pool->catalogue;
+  p->n_elts = pool->n_elts;
+  p->n_layers = n_layers;
+  p->flags = pool->flags;
+  p->n_records = pool->n_records;
+  p->rec_off = pool->rec_off;
+  p->elt_ret = pool->elt_ret;
+  p->elt_lim = pool->elt_lim;
+  p->elt_max_loss = pool->elt_max_loss;
+  p->d_rec_off = pool->d_rec_off;
+  p->d_rec_ids = pool->d_rec_ids;
+  p->d_rec_orig = pool->d_rec_orig;
+  p->d_rec_loss = pool->d_rec_loss;
+  p->d_rec_loss32 = pool->d_rec_loss32;
+  p->d_elt_ret = pool->d_elt_ret;
+  p->d_elt_lim = pool->d_elt_lim;
+  p->d_dense = pool->d_dense;
+  p->layer_off.assign(layer_off, layer_off + n_layers + 1);
+  p->layer_elts.assign(layer_elts, layer_elts + layer_off[n_layers]);
+  p->layers.resize((size_t)n_layers);
+  for (int32_t l = 0; l < n_layers; ++l) {
+    LayerConst& lc = p->layers[(size_t)l];
+    memset(&lc, 0, sizeof(lc));
+    lc.occ_ret = occ_ret[l];
+    lc.occ_lim = occ_lim[l];
+    lc.agg_ret = agg_ret[l];
+    lc.agg_lim = agg_lim[l];
+    lc.elt_begin = layer_off[l];
+    lc.elt_end = layer_off[l + 1];
+    layer_scale(*p, lc);
+  }
+  DeviceGuard g(p->device);
+  const int64_t C = p->catalogue;
+  p->bm_words = pool->bm_words;
+  p->cbits_stride = pool->cbits_stride;
+  auto fail = [&](ara_status e) {
+    free_portfolio(p);
+    return e;
+  };
+  auto amalloc = [&](void** ptr, size_t n) { return cudaMallocAsync(ptr, std::max<size_t>(n, 8), s) == cudaSuccess; };
+  if (!amalloc((void**)&p->d_layer_elts, 4 * p->layer_elts.size()) ||
+      !amalloc((void**)&p->d_layers, sizeof(LayerConst) * (size_t)n_layers) ||
+      !amalloc((void**)&p->d_q, 8 * (size_t)n_layers * C) ||
+      !amalloc((void**)&p->d_bits, 4 * (size_t)n_layers * p->bm_words) ||
+      !amalloc((void**)&p->d_cbits, 4 * (size_t)n_layers * p->cbits_stride) ||
+      !amalloc((void**)&p->d_err, 4))
+    return fail(ARA_ENOMEM);
+  if ((!p->layer_elts.empty() &&
+       cudaMemcpyAsync(p->d_layer_elts, p->layer_elts.data(), 4 * p->layer_elts.size(),
+                       cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+      cudaMemcpyAsync(p->d_layers, p->layers.data(), sizeof(LayerConst) * (size_t)n_layers,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(p->d_bits, 0, 4 * (size_t)n_layers * p->bm_words, s) != cudaSuccess ||
+      cudaMemsetAsync(p->d_err, 0, 4, s) != cudaSuccess)
+    return fail(ARA_ECUDA);
+  *out = p;
+  return ARA_OK;
 }
 
 static ara_status check_selection(const Portfolio& pf, int32_t n_sel, const int32_t* sel,
@@ -390,7 +497,10 @@ static ara_status check_selection(const Portfolio& pf, int32_t n_sel, const int3
 
 static ara_status check_flags(const Portfolio& pf, int32_t flags) {
   if (flags & ~(ARA_RUN_PER_ELT | ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG |
-                ARA_RUN_HOST_DIRECT))
+                ARA_RUN_HOST_DIRECT | ARA_RUN_BATCHED))
+    return ARA_EINVAL;
+  if ((flags & ARA_RUN_BATCHED) &&
+      (flags & (ARA_RUN_PER_ELT | ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG | ARA_RUN_HOST_DIRECT)))
     return ARA_EINVAL;
   if ((flags & ARA_RUN_PER_ELT) &&
       (flags & (ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG | ARA_RUN_HOST_DIRECT)))
@@ -415,7 +525,7 @@ ara_status ara_run_ylt(ara_portfolio* pf, int64_t n_trials, const int64_t* d_off
   if (((uintptr_t)d_ids & 3) || ((uintptr_t)d_offsets & 7) || ((uintptr_t)d_ylt & 7)) return ARA_EINVAL;
   DeviceGuard g(pf->device);
   cudaStream_t s = (cudaStream_t)stream;
-  if (!(flags & ARA_RUN_PER_ELT)) {
+  if (!(flags & (ARA_RUN_PER_ELT | ARA_RUN_BATCHED))) {
     if ((st = launch_fold(*pf, (int32_t)sel.size(), sel.data(), flags, s)) != ARA_OK) return st;
   }
   YltArgs a{};
@@ -430,17 +540,20 @@ ara_status ara_run_ylt(ara_portfolio* pf, int64_t n_trials, const int64_t* d_off
   a.regimes = d_regimes;
   a.row_stride = n_trials;
   a.flags = flags;
+  if (flags & ARA_RUN_BATCHED) return run_batched_async(*pf, a, s);
   return launch_ylt(*pf, a, s);
 }
 
 ara_status ara_check(ara_portfolio* pf, void* stream) {
   if (!pf) return ARA_EINVAL;
   DeviceGuard g(pf->device);
-  ARA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  cudaStream_t s = (cudaStream_t)stream;
   uint32_t err = 0;
-  ARA_TRY(cudaMemcpy(&err, pf->d_err, sizeof(err), cudaMemcpyDeviceToHost));
+  ARA_TRY(cudaMemcpyAsync(&err, pf->d_err, sizeof(err), cudaMemcpyDeviceToHost, s));
+  ARA_TRY(cudaStreamSynchronize(s));
   if (err) {
-    ARA_TRY(cudaMemset(pf->d_err, 0, sizeof(uint32_t)));
+    ARA_TRY(cudaMemsetAsync(pf->d_err, 0, sizeof(uint32_t), s));
+    ARA_TRY(cudaStreamSynchronize(s));
     return (err & DERR_TIMEOUT) ? ARA_ETIMEOUT : ARA_EDATA;
   }
   return ARA_OK;
@@ -494,6 +607,7 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
   if (metrics && (sel.empty() || (n_rp > 0 && !h_pml) || (n_tvar > 0 && !h_tvar) ||
                   validate_metrics(n_trials, n_rp, rps, n_tvar, levels) != ARA_OK))
     return ARA_EINVAL;
+  if (flags & ARA_RUN_BATCHED) return ARA_EINVAL;
   if (h_off[0] != 0) return ARA_EINVAL;
   for (int64_t t = 0; t < n_trials; ++t)
     if (h_off[t + 1] < h_off[t]) return ARA_EINVAL;

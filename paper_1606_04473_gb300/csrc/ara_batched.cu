@@ -379,6 +379,62 @@ void bt_free(ara_plan* P) {
 
 }  // namespace
 
+namespace ara {
+// The batched path as one asynchronous call (no graph, default schedule): scratch comes from the
+// stream-ordered allocator, the table is sized by a host-known bound (every non-zero entry of
+// layer i is an event of one of its ELTs), and nothing waits on the host.
+ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
+  ara_plan P;
+  P.pf = &pf;
+  P.n_trials = a.n_trials;
+  P.n_events = a.n_events;
+  P.d_off = a.offsets;
+  P.d_ids = a.ids;
+  P.sel.assign(a.sel, a.sel + a.n_sel);
+  P.d_ylt = a.ylt;
+  P.d_reg = a.regimes;
+  if (a.id_base != 0 || a.row_stride != a.n_trials) return ARA_EINVAL;
+  if ((int)P.sel.size() > BT_MAX_LAYERS || (int)P.sel.size() > pf.n_layers ||
+      (int64_t)P.sel.size() * pf.catalogue >= ((int64_t)1 << 32))
+    return ARA_ERANGE;
+  int64_t bound = 0;
+  for (int32_t l : P.sel) {
+    const LayerConst& lc = pf.layers[l];
+    P.max_le = std::max(P.max_le, lc.elt_end - lc.elt_begin);
+    for (int k = lc.elt_begin; k < lc.elt_end; ++k) {
+      const int j = pf.layer_elts[k];
+      bound += pf.rec_off[j + 1] - pf.rec_off[j];
+    }
+  }
+  const int64_t C = pf.catalogue;
+  P.n_blocks = (C + BT_SCAN_BLOCK - 1) / BT_SCAN_BLOCK;
+  size_t off = 0;
+  auto take = [&](size_t n) { size_t o = (off + 255) / 256 * 256; off = o + n; return o; };
+  const size_t o_cnt = take(4 * (size_t)C), o_ptr = take(4 * (size_t)(C + 1));
+  const size_t o_bsum = take(4 * (size_t)P.n_blocks), o_tot = take(4), o_q = take(8);
+  const size_t o_ent = take(8 * (size_t)std::max<int64_t>(bound, 1));
+  char* buf = nullptr;
+  ARA_TRY(cudaMallocAsync((void**)&buf, off, s));
+  P.d_cnt = (uint32_t*)(buf + o_cnt);
+  P.d_ptr = (uint32_t*)(buf + o_ptr);
+  P.d_bsum = (uint32_t*)(buf + o_bsum);
+  P.d_total = (uint32_t*)(buf + o_tot);
+  P.d_queue = (unsigned long long*)(buf + o_q);
+  P.d_entries = (uint64_t*)(buf + o_ent);
+  ara_status st = ARA_OK;
+  {
+    LaunchScope ls(ARA_K_BATCHED, s, P.max_le + 6);
+    st = bt_prep(P, s, true, nullptr);
+    if (st == ARA_OK) st = bt_stream(P, s);
+  }
+  cudaFreeAsync(buf, s);
+  P.d_cnt = P.d_ptr = P.d_bsum = P.d_total = nullptr;
+  P.d_entries = nullptr;
+  P.d_queue = nullptr;
+  return st;
+}
+}  // namespace ara
+
 extern "C" {
 
 ara_status ara_plan_batched(ara_portfolio* pf_, int64_t n_trials, const int64_t* d_off,

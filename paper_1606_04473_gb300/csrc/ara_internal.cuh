@@ -69,6 +69,8 @@ struct LayerConst {
 };
 
 struct Portfolio {
+  bool borrowed_elts = false;       // a layer set: ELT tables belong to a resident pool
+  cudaStream_t owner_stream = nullptr;  // layer sets: stream their buffers were allocated on
   int device = 0;
   int n_sms = 0;
   int max_smem_block = 0;           // opt-in shared memory per block (bytes)
@@ -138,6 +140,7 @@ struct FoldOutHost {
 ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
                           const FoldOutHost& o, cudaStream_t s);
 ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s);
+ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s);
 ara_status build_dense(Portfolio& pf, cudaStream_t s);
 // Compiled shapes (warps per block, ring stages) of the bulk-staged YET stream kernel.
 int32_t n_bulk_shapes();

@@ -317,3 +317,44 @@ def batched_yet(seed: int = 0, n_trials: int = 200_000, ids_out: Optional[np.nda
     mu = 200.0 + 1800.0 * uniform01(stream_key(seed, 8), 0, n_trials)
     counts = poisson_counts(seed + 2000, mu, n_trials)
     return make_yet(seed + 2000, counts, 2_000_000, with_timestamps=False, ids_out=ids_out)
+
+
+def serving_pool(seed: int = 0) -> Portfolio:
+    """Resident pool of 500 ELTs x 20,000 events (2,000,000-event catalogue, FP32 lognormal(11, 2)),
+    per-ELT terms by the percentile rule, no layers (queries bring their own)."""
+    ids, losses, r, l = _pool(seed + 3000, 500)
+    z = np.zeros(0)
+    return Portfolio(2_000_000, ids, losses, r, l, [], z, z, z, z, losses_f32=True)
+
+
+def serving_yet(seed: int = 0, n_trials: int = 1_000_000, ids_out: Optional[np.ndarray] = None) -> YET:
+    """Resident YET of n_trials x Poisson(1000) events."""
+    counts = poisson_counts(seed + 3000, 1000.0, n_trials)
+    return make_yet(seed + 3000, counts, 2_000_000, with_timestamps=False, ids_out=ids_out)
+
+
+def serving_trace(pool: Portfolio, n_trials: int, n_requests: int = 200, rate: float = 200.0,
+                  seed: int = 0, adjoint_share: float = 0.2):
+    """Seeded request trace: Poisson arrivals at `rate` per second from 32 tenants; each query has
+    U{1..32} layers of U{5..20} distinct pool ELTs over a contiguous slice of U[1e4, 1e6] trials
+    (clipped to the YET), 20 % with the adjoint.  Layer terms are set from the raw loss quantiles
+    of the layer's ELTs (no financial terms are evaluated here): OccR = max_j P50_j,
+    OccL = sum_j P95_j, AggR = 10 sum_j P50_j, AggL = 200 sum_j P95_j."""
+    g = np.random.Generator(np.random.Philox(key=seed + 4000))
+    p50 = np.array([np.percentile(x, 50) for x in pool.elt_losses])
+    p95 = np.array([np.percentile(x, 95) for x in pool.elt_losses])
+    t = np.cumsum(g.exponential(1.0 / rate, n_requests))
+    out = []
+    for k in range(n_requests):
+        nl = int(g.integers(1, 33))
+        layers = [sorted(g.choice(pool.n_elts, size=int(g.integers(5, 21)), replace=False).tolist())
+                  for _ in range(nl)]
+        n = int(min(n_trials, g.integers(10_000, 1_000_001)))
+        t0 = int(g.integers(0, n_trials - n + 1))
+        out.append(dict(arrival=float(t[k]), tenant=int(g.integers(0, 32)), layer_elts=layers,
+                        occ_ret=[float(p50[l].max()) for l in layers],
+                        occ_lim=[float(p95[l].sum()) for l in layers],
+                        agg_ret=[float(10 * p50[l].sum()) for l in layers],
+                        agg_lim=[float(200 * p95[l].sum()) for l in layers],
+                        trials=(t0, t0 + n), want_adjoint=bool(g.random() < adjoint_share)))
+    return out

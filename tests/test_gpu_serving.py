@@ -1,0 +1,131 @@
+"""GPU tests of serving: layer sets over a resident ELT pool and the native request server
+(continuous admission by a device-memory budget, requests overlapping on separate streams).
+Each request's results must be the same alone and in the mix (the per-request computation is
+deterministic: exact integer trial sums and an exact selection), and agree with the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_1606_04473_gb300 as ara
+
+C, POOL = 200_000, 40
+
+
+@pytest.fixture(scope="module")
+def world():
+    ids, losses = synth.make_elts(5, POOL, 3000, C, 11.0, 2.0, f32=True)
+    r, l = synth.percentile_terms(losses)
+    pool_tables = synth.Portfolio(C, ids, losses, r, l, [], np.zeros(0), np.zeros(0), np.zeros(0),
+                                  np.zeros(0), losses_f32=True)
+    counts = synth.poisson_counts(5, 300.0, 6000)
+    yet = synth.make_yet(5, counts, C, with_timestamps=False)
+    pool = ara.Portfolio.from_tables(pool_tables)
+    off = torch.from_numpy(yet.offsets).cuda()
+    ev = torch.from_numpy(yet.event_ids).cuda()
+    return pool_tables, yet, pool, off, ev
+
+
+def random_queries(n, seed, n_trials):
+    rng = np.random.default_rng(seed)
+    qs = []
+    for k in range(n):
+        nl = int(rng.integers(1, 7))
+        layers = [sorted(rng.choice(POOL, size=int(rng.integers(3, 11)), replace=False).tolist())
+                  for _ in range(nl)]
+        t0 = int(rng.integers(0, n_trials - 500))
+        t1 = int(rng.integers(t0 + 200, min(n_trials, t0 + 4000) + 1))
+        scale = rng.uniform(0.5, 2.0, (4, nl))
+        qs.append(dict(layer_elts=layers, occ_ret=2e4 * scale[0], occ_lim=2e6 * scale[1],
+                       agg_ret=5e6 * scale[2], agg_lim=2e8 * scale[3], trials=(t0, t1),
+                       return_periods=[10.0, 50.0], tvar_levels=[0.9], want_mean=True,
+                       want_adjoint=bool(k % 3 == 0), adjoint_level=0.9,
+                       flags=ara.ARA_RUN_BATCHED if k % 2 else 0, tenant=k % 5))
+    return qs
+
+
+def test_layer_set_equals_full_portfolio(world):
+    pool_tables, yet, pool, off, ev = world
+    layers = [[0, 3, 5, 7], [1, 2], [39, 10, 20]]
+    terms = dict(occ_ret=[1e4, 2e4, 3e4], occ_lim=[1e6, 3e6, 5e6], agg_ret=[1e6, 2e6, 3e6],
+                 agg_lim=[1e8, 1e8, 1e7])
+    ls = pool.layer_set(layers, **terms)
+    full_tables = synth.Portfolio(C, pool_tables.elt_ids, pool_tables.elt_losses, pool_tables.elt_ret,
+                                  pool_tables.elt_lim, layers, *[np.array(terms[k]) for k in
+                                  ["occ_ret", "occ_lim", "agg_ret", "agg_lim"]], losses_f32=True)
+    full = ara.Portfolio.from_tables(full_tables)
+    a = ls.run_ylt(off, ev)
+    b = full.run_ylt(off, ev)
+    ls.check()
+    assert torch.equal(a, b)
+    ref, agg = oracle.ylt(full_tables, yet, return_agg=True)
+    err = np.abs(a.cpu().numpy() - ref)
+    assert np.all(err <= 1e-6 * np.abs(ref) + 1e-12 * np.abs(agg))
+    ls.close()
+
+
+def test_server_results_same_alone_and_in_the_mix(world):
+    pool_tables, yet, pool, off, ev = world
+    qs = random_queries(24, 7, yet.n_trials)
+    srv = ara.Server(pool, off, ev, max_concurrent=4)
+    tickets = [srv.submit(**q) for q in qs]          # all at once: they overlap on the device
+    mixed = [srv.wait(t) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    assert stats["peak_running"] >= 2
+    alone_srv = ara.Server(pool, off, ev, max_concurrent=1)
+    for q, m in zip(qs, mixed):
+        a = alone_srv.wait(alone_srv.submit(**q))
+        for k in ("pml", "tvar", "mean", "grad_layer"):
+            if a[k] is None:
+                assert m[k] is None
+            else:
+                assert np.array_equal(a[k], m[k]), k
+    alone_srv.close()
+    # a few against the oracle
+    for q, m in list(zip(qs, mixed))[:4]:
+        t0, t1 = q["trials"]
+        sub = synth.YET(yet.offsets[t0:t1 + 1] - yet.offsets[t0],
+                        yet.event_ids[yet.offsets[t0]:yet.offsets[t1]])
+        tab = synth.Portfolio(C, pool_tables.elt_ids, pool_tables.elt_losses, pool_tables.elt_ret,
+                              pool_tables.elt_lim, q["layer_elts"], np.asarray(q["occ_ret"]),
+                              np.asarray(q["occ_lim"]), np.asarray(q["agg_ret"]),
+                              np.asarray(q["agg_lim"]))
+        y = oracle.ylt(tab, sub)
+        p, t = oracle.risk_metrics(y, q["return_periods"], q["tvar_levels"])
+        np.testing.assert_allclose(m["pml"], p, rtol=1e-6)
+        np.testing.assert_allclose(m["tvar"], t, rtol=1e-6)
+        np.testing.assert_allclose(m["mean"], y.mean(1), rtol=1e-6)
+
+
+def test_server_admission_by_memory_budget(world):
+    pool_tables, yet, pool, off, ev = world
+    qs = random_queries(8, 11, yet.n_trials)
+    srv = ara.Server(pool, off, ev, max_concurrent=4, memory_budget=1)   # every request alone
+    res = [srv.wait(t) for t in [srv.submit(**q) for q in qs]]
+    assert srv.stats()["peak_running"] == 1
+    srv.close()
+    srv = ara.Server(pool, off, ev, max_concurrent=4, memory_budget=1 << 40)
+    res2 = [srv.wait(t) for t in [srv.submit(**q) for q in qs]]
+    srv.close()
+    for a, b in zip(res, res2):
+        assert np.array_equal(a["pml"], b["pml"]) and np.array_equal(a["tvar"], b["tvar"])
+
+
+def test_server_rejects_invalid_queries(world):
+    pool_tables, yet, pool, off, ev = world
+    srv = ara.Server(pool, off, ev, max_concurrent=2)
+    good = random_queries(1, 3, yet.n_trials)[0]
+    bad = [dict(good, trials=(0, yet.n_trials + 1)), dict(good, layer_elts=[[POOL]]),
+           dict(good, return_periods=[0.5]), dict(good, tvar_levels=[1.0])]
+    for q in bad:
+        with pytest.raises(ara.AraError) as e:
+            srv.submit(**q)
+        assert e.value.status == ara.ARA_EINVAL
+    srv.wait(srv.submit(**good))
+    srv.close()
