@@ -179,15 +179,21 @@ def measured_peaks():
 
 
 def ncu_traffic_per_launch():
-    """DRAM bytes per launch of the YET-stream kernel from the committed ncu summary, scaled
-    to the benchmark's launch (null when absent or stale)."""
-    path = os.path.join(ROOT, "profiles", "ylt_stream_traffic.json")
+    """DRAM bytes per event of the YET-stream kernel from the committed ncu summary
+    (profiles/k_ylt_bulk_paper_scale.md: lines 'dram_bytes_per_event: X' and
+    'kernel_source_sha: Y'); None when absent or when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "k_ylt_bulk_paper_scale.md")
     try:
+        kv = {}
         with open(path) as f:
-            t = json.load(f)
-        if t.get("kernel_source_sha") != kernel_source_sha():
+            for line in f:
+                line = line.strip().lstrip("-* ").strip()
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip().strip("`")] = v.strip().strip("`")
+        if kv.get("kernel_source_sha") != kernel_source_sha():
             return None
-        return float(t["dram_bytes_per_event"])
+        return float(kv["dram_bytes_per_event"])
     except Exception:
         return None
 
@@ -195,8 +201,9 @@ def ncu_traffic_per_launch():
 def kernel_source_sha():
     import hashlib
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1606_04473_gb300", "csrc", "ara_ylt.cu"), "rb") as f:
-        h.update(f.read())
+    for name in ("ara_ylt.cu", "ara_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1606_04473_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 

@@ -134,6 +134,10 @@ ARA_API ara_status ara_create_layer_set(ara_portfolio* pool, int32_t n_layers,
                                  layer's occurrence losses, one persistent stream kernel); same
                                  results; at most 255 selected layers, no repeats beyond the
                                  portfolio's layer count (ARA_ERANGE) */
+#define ARA_RUN_OEP      64   /* occurrence basis: y_t = max_k o(e_{t,k}), the trial's largest
+                                 occurrence loss net of ELT and occurrence terms (the loss behind
+                                 occurrence exceedance curves); aggregate terms not applied,
+                                 regimes all 0.  Only with the default folded path */
 #define ARA_RUN_HOST_DIRECT 16 /* ara_run_ylt_host only: the kernel reads the (pinned, device-
                                  mapped) host YET in place over the CPU-GPU link instead of
                                  staging it with copies; ARA_EINVAL if the host arrays are not

@@ -66,6 +66,8 @@ def lib():
         i32, i64 = ctypes.c_int32, ctypes.c_int64
         L.orc_ylt.argtypes = [i64, i32, P, P, P, P, P, i32, P, P, P, P, P, P, i64, P, P, i64, P, P, P]
         L.orc_ylt.restype = ctypes.c_int
+        L.orc_ylt_oep.argtypes = [i64, P, P, P, P, P, i32, P, P, P, P, i64, P, P, i64, P, P]
+        L.orc_ylt_oep.restype = ctypes.c_int
         L.orc_adjoint.argtypes = [i64, P, P, P, P, P, i32, P, P, P, P, P, P, i64, P, P, P, P, P, P, P]
         L.orc_adjoint.restype = ctypes.c_int
         L.orc_max_threads.restype = ctypes.c_int
@@ -121,6 +123,27 @@ def ylt(pf, yet, trials: Optional[Sequence[int]] = None, return_agg: bool = Fals
         raise ValueError("oracle: invalid input (event ID out of range, duplicate ELT record, "
                          "bad trial index) or out of memory")
     return (out, agg) if return_agg else out
+
+
+def ylt_oep(pf, yet, trials: Optional[Sequence[int]] = None):
+    """Occurrence year losses [n_layers, n_out]: the largest occurrence loss of each trial net of
+    the ELT and occurrence terms (the loss basis of occurrence exceedance probabilities; the
+    aggregate terms do not apply)."""
+    L = lib()
+    off, ids, losses = _records(pf)
+    loff, lel = pf.layer_csr()
+    sel = None if trials is None else np.ascontiguousarray(np.asarray(trials, dtype=np.int64))
+    n_out = yet.n_trials if sel is None else sel.size
+    out = np.zeros((pf.n_layers, n_out), dtype=np.float64)
+    rc = L.orc_ylt_oep(pf.catalogue, _p(off), _p(ids), _p(losses), _p(_f64(pf.elt_ret)),
+                       _p(_f64(pf.elt_lim)), pf.n_layers, _p(loff), _p(lel), _p(_f64(pf.occ_ret)),
+                       _p(_f64(pf.occ_lim)), yet.n_trials,
+                       _p(np.ascontiguousarray(yet.offsets, dtype=np.int64)),
+                       _p(np.ascontiguousarray(yet.event_ids, dtype=np.int32)),
+                       0 if sel is None else sel.size, None if sel is None else _p(sel), _p(out))
+    if rc != 0:
+        raise ValueError("oracle: invalid input")
+    return out
 
 
 # ------------------------------------------------------------------------------------------

@@ -90,6 +90,47 @@ static double* build_tables(int64_t catalogue, int32_t n_le, const int32_t* le,
 }
 
 /*
+ * Occurrence year losses (OEP basis): for every layer and selected trial, the largest single
+ * occurrence loss of the trial net of the ELT and occurrence terms, max_k o(e_k) (0 for an
+ * empty trial); the aggregate terms, which act on the annual total, are not applied.
+ * Same arguments and layout as orc_ylt without the aggregate outputs.
+ */
+int orc_ylt_oep(int64_t catalogue, const int64_t* rec_off, const int32_t* rec_ids,
+                const double* rec_losses, const double* elt_ret, const double* elt_lim,
+                int32_t n_layers, const int32_t* layer_off, const int32_t* layer_elts,
+                const double* occ_ret, const double* occ_lim, int64_t n_trials,
+                const int64_t* trial_off, const int32_t* event_ids, int64_t n_sel,
+                const int64_t* sel, double* ylt_out) {
+    int64_t n_out = sel ? n_sel : n_trials;
+    for (int32_t l = 0; l < n_layers; ++l) {
+        const int32_t* le = layer_elts + layer_off[l];
+        int32_t n_le = layer_off[l + 1] - layer_off[l];
+        double* tab = build_tables(catalogue, n_le, le, rec_off, rec_ids, rec_losses);
+        if (!tab) return -1;
+        int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(|: bad)
+        for (int64_t i = 0; i < n_out; ++i) {
+            int64_t t = sel ? sel[i] : i;
+            if (t < 0 || t >= n_trials) { bad = 1; continue; }
+            double largest = 0.0;
+            for (int64_t k = trial_off[t]; k < trial_off[t + 1]; ++k) {
+                int32_t e = event_ids[k];
+                if (e < 0 || e >= catalogue) { bad = 1; break; }
+                double l_E = 0.0;
+                for (int32_t q = 0; q < n_le; ++q)
+                    l_E += clamp_terms(tab[(size_t)q * catalogue + e], elt_ret[le[q]], elt_lim[le[q]]);
+                double o = clamp_terms(l_E, occ_ret[l], occ_lim[l]);
+                if (o > largest) largest = o;
+            }
+            ylt_out[(size_t)l * n_out + i] = largest;
+        }
+        free(tab);
+        if (bad) return -1;
+    }
+    return 0;
+}
+
+/*
  * YLT of the selected trials for every layer.
  *   ELT records: ELT j owns records rec_off[j] .. rec_off[j+1]-1 of (rec_ids, rec_losses).
  *   Layer l covers ELTs layer_elts[layer_off[l] .. layer_off[l+1]-1], in that order.

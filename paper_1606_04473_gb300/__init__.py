@@ -29,6 +29,7 @@ ARA_LOSSES_F32, ARA_DENSE_TABLES = 1, 2
 ARA_RUN_FOLDED, ARA_RUN_PER_ELT, ARA_RUN_NO_FILTER, ARA_RUN_F64_SUM, ARA_RUN_LDG = 0, 1, 2, 4, 8
 ARA_RUN_HOST_DIRECT = 16
 ARA_RUN_BATCHED = 32
+ARA_RUN_OEP = 64
 
 
 class Query(ctypes.Structure):

@@ -497,8 +497,9 @@ static ara_status check_selection(const Portfolio& pf, int32_t n_sel, const int3
 
 static ara_status check_flags(const Portfolio& pf, int32_t flags) {
   if (flags & ~(ARA_RUN_PER_ELT | ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG |
-                ARA_RUN_HOST_DIRECT | ARA_RUN_BATCHED))
+                ARA_RUN_HOST_DIRECT | ARA_RUN_BATCHED | ARA_RUN_OEP))
     return ARA_EINVAL;
+  if ((flags & ARA_RUN_OEP) && (flags & ~ARA_RUN_OEP)) return ARA_EINVAL;   // default path only
   if ((flags & ARA_RUN_BATCHED) &&
       (flags & (ARA_RUN_PER_ELT | ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG | ARA_RUN_HOST_DIRECT)))
     return ARA_EINVAL;

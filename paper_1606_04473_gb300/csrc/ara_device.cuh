@@ -92,4 +92,32 @@ template <> struct AccOps<double> {
 };
 
 
+// Occurrence basis (OEP): the largest occurrence loss of the trial instead of the sum; the
+// aggregate terms do not apply.  The fixed-point maximum is exact; only the result is rounded.
+struct OepMax {
+  uint64_t v;
+};
+template <> struct AccOps<OepMax> {
+  static __device__ __forceinline__ OepMax zero() { return OepMax{0ull}; }
+  static __device__ __forceinline__ void add(OepMax& a, uint64_t v) { a.v = a.v > v ? a.v : v; }
+  template <int NV>
+  static __device__ __forceinline__ void add_split(OepMax& a, uint64_t, uint64_t, const uint64_t (&v)[NV]) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) a.v = a.v > v[i] ? a.v : v[i];
+  }
+  static __device__ __forceinline__ OepMax warp_sum(OepMax a) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const uint64_t b = __shfl_xor_sync(FULL, a.v, o);
+      a.v = a.v > b ? a.v : b;
+    }
+    return a;
+  }
+  static __device__ __forceinline__ OepMax shfl(OepMax a, int src) { return OepMax{__shfl_sync(FULL, a.v, src)}; }
+  static __device__ __forceinline__ double finish(OepMax S, const LayerConst& lc, uint8_t& reg) {
+    reg = 0;
+    return __dmul_rn(__ull2double_rn(S.v), lc.inv_scale);
+  }
+};
+
 }  // namespace ara

@@ -896,6 +896,8 @@ ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
     } else if (ldg) {
       if (f64) st = nof ? launch_folded_one<false, double>(pf, sp, s) : launch_folded_one<true, double>(pf, sp, s);
       else st = nof ? launch_folded_one<false, U128>(pf, sp, s) : launch_folded_one<true, U128>(pf, sp, s);
+    } else if (a.flags & ARA_RUN_OEP) {
+      st = launch_bulk_one<true, OepMax>(pf, sp, s);
     } else {
       if (f64) st = nof ? launch_bulk_one<false, double>(pf, sp, s) : launch_bulk_one<true, double>(pf, sp, s);
       else st = nof ? launch_bulk_one<false, U128>(pf, sp, s) : launch_bulk_one<true, U128>(pf, sp, s);

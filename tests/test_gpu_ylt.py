@@ -348,3 +348,15 @@ def test_bounded_copy_wait_times_out_and_reports(tiny):
     y = g.run_ylt(off, ids)
     g.check()
     assert_ylt_close(y.cpu().numpy(), ref, agg)
+
+
+def test_occurrence_basis_oep(mid):
+    """ARA_RUN_OEP: the largest occurrence loss per trial, against the oracle's OEP basis."""
+    pf, yet, ref, agg = mid
+    g = ara.Portfolio.from_tables(pf)
+    y = g.run_ylt(*dev(yet), flags=ara.ARA_RUN_OEP)
+    g.check()
+    want = oracle.ylt_oep(pf, yet)
+    np.testing.assert_allclose(y.cpu().numpy(), want, rtol=1e-12, atol=0)
+    with pytest.raises(ara.AraError):
+        g.run_ylt(*dev(yet), flags=ara.ARA_RUN_OEP | ara.ARA_RUN_LDG)

@@ -374,3 +374,33 @@ def test_tvar_weights_share_the_boundary_among_ties():
     assert float(w[0] @ y[0]) == pytest.approx(oracle.tvar(y[0], 0.6), rel=1e-15)
     w, ties = oracle.objective_weights(np.array([[10.0, 5.0, 4.0]]), "tvar", 0.5)
     assert w[0].tolist() == [0.5, 0.5, 0.0] and ties == [False]
+
+
+# ---------------------------------------------------------------------------------- OEP basis
+def test_oep_hand_worked(golden_dir):
+    pf, yet, exp = load_p1(golden_dir)
+    assert oracle.ylt_oep(pf, yet)[0].tolist() == exp["ylt_oep"]
+
+
+def test_oep_properties():
+    """max <= sum (with identity aggregate terms); one-event trials give o(e) itself; the same
+    quantity written differently (numpy over dense tables) agrees exactly."""
+    pf, yet = random_case(14)
+    oep = oracle.ylt_oep(pf, yet)
+    ident = pf.with_terms({**pf.terms_dict(), "agg_ret": [0.0] * pf.n_layers,
+                           "agg_lim": [INF] * pf.n_layers})
+    assert np.all(oep <= oracle.ylt(ident, yet) + 1e-9)
+    for l, elts in enumerate(pf.layer_elts):
+        dense = np.zeros((len(elts), pf.catalogue))
+        for q, j in enumerate(elts):
+            dense[q, pf.elt_ids[j]] = pf.elt_losses[j]
+        net = np.minimum(np.maximum(dense - pf.elt_ret[elts][:, None], 0), pf.elt_lim[elts][:, None])
+        s = np.zeros(pf.catalogue)
+        for q in range(len(elts)):          # layer order, as the definition
+            s = s + net[q]
+        o = np.minimum(np.maximum(s - pf.occ_ret[l], 0), pf.occ_lim[l])
+        want = np.array([o[yet.event_ids[yet.offsets[t]:yet.offsets[t + 1]]].max(initial=0.0)
+                         for t in range(yet.n_trials)])
+        assert np.array_equal(oep[l], want)
+    one = synth.YET(np.arange(51, dtype=np.int64), np.arange(50, dtype=np.int32) * 5)
+    assert np.all(oracle.ylt_oep(pf, one) == oracle.ylt(ident.with_terms({**ident.terms_dict()}), one))
