@@ -178,6 +178,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def stream_kernel_name(flags):
+    """The YET-stream kernel a run with these ARA_RUN_* flags launches."""
+    import paper_1606_04473_gb300 as ara
+    if flags & ara.ARA_RUN_PER_ELT:
+        return "k_ylt_per_elt"
+    if flags & (ara.ARA_RUN_LDG | ara.ARA_RUN_HOST_DIRECT):
+        return "k_ylt_folded"
+    return "k_ylt_bulk"
+
+
 def ncu_traffic_per_launch():
     """DRAM bytes per event of the YET-stream kernel from the committed ncu summary
     (profiles/k_ylt_bulk_paper_scale.md: lines 'dram_bytes_per_event: X' and
@@ -349,7 +359,7 @@ def run_ours(args, rank, ws, local):
     tpe = ncu_traffic_per_launch()
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": (tpe * n_events if tpe else None),
-            "peak_source": peak_kind, "kernel": "k_ylt_folded",
+            "peak_source": peak_kind, "kernel": stream_kernel_name(args.flags),
             "alg_bytes_per_launch": alg_bytes, "ms_per_launch": round(per_launch_ms, 4),
             "frac_8byte_events": round((alg_bytes + 4 * n_events) / (per_launch_ms / 1e3) / 1e9 / peak, 4)}
 

@@ -121,29 +121,16 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ rec_off, const int32_t* __
 // ------------------------------------------------------------------------------------------
 // Stream helpers
 // ------------------------------------------------------------------------------------------
-// Coarse hit bitmap word cw: coarse bit i is the OR of the exact bits of events
-// [(32 cw + i) << shift, (32 cw + i + 1) << shift).
+// Coarse hit bitmap word cw, interleaved: coarse bit i is the OR of bit i of the exact words
+// [cw << shift, (cw + 1) << shift), i.e. of the hit bits of the 2^shift events e with
+// e >> (5 + shift) == cw and e mod 32 == i.  A lookup therefore reads word e >> (5 + shift)
+// and tests bit e mod 32, the same bit position as in the exact bitmap.
 __device__ __forceinline__ uint32_t coarsen_word(const uint32_t* __restrict__ src, int64_t cw,
                                                  int shift, int64_t n_words) {
-  if (shift == 0) return cw < n_words ? src[cw] : 0u;
+  const int64_t w0 = cw << shift;
+  const int64_t w1 = min(w0 + ((int64_t)1 << shift), n_words);
   uint32_t out = 0;
-  if (shift <= 4) {
-    const int G = 1 << shift, per = 32 >> shift;
-    for (int w = 0; w < G; ++w) {
-      const int64_t ew = (cw << shift) + w;
-      const uint32_t x = ew < n_words ? src[ew] : 0u;
-      for (int b = 0; b < per; ++b)
-        out |= (((x >> (b * G)) & ((1u << G) - 1u)) ? 1u : 0u) << (w * per + b);
-    }
-  } else {
-    const int64_t wpb = (int64_t)1 << (shift - 5);  // exact words per coarse bit
-    for (int b = 0; b < 32; ++b) {
-      const int64_t w0 = (cw * 32 + b) * wpb;
-      uint32_t any = 0;
-      for (int64_t w = w0; w < w0 + wpb && w < n_words; ++w) any |= src[w];
-      out |= (any ? 1u : 0u) << b;
-    }
-  }
+  for (int64_t w = w0; w < w1; ++w) out |= src[w];
   return out;
 }
 
@@ -176,8 +163,7 @@ __device__ __forceinline__ void consume(int e, bool valid, const StreamParams& p
   if (!valid) return;
   if ((unsigned)e >= (unsigned)p.catalogue) { bad = true; return; }
   if (FILTER) {
-    const uint32_t b = (uint32_t)e >> p.shift;
-    if (!((bm[b >> 5] >> (b & 31)) & 1u)) return;
+    if (!((bm[(uint32_t)e >> (p.shift + 5)] >> (e & 31)) & 1u)) return;
   }
   AccOps<Acc>::add(acc, __ldg(q + e));
 }
@@ -330,7 +316,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // Coarse hit bitmap of a layer, built once per run when the exact one does not fit in shared
-// memory: coarse bit b = OR of the exact bits of events [b << shift, (b + 1) << shift).
+// memory, in the interleaved layout of coarsen_word.
 __global__ void k_coarsen(const uint32_t* __restrict__ exact, int64_t n_exact, int shift,
                           uint32_t* __restrict__ coarse, int64_t n_coarse) {
   for (int64_t cw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cw < n_coarse;
@@ -340,21 +326,21 @@ __global__ void k_coarsen(const uint32_t* __restrict__ exact, int64_t n_exact, i
 
 // Table value of one event for the bulk stream: the event index is clamped into the catalogue
 // for addressing (an out-of-range ID is caught through emax, which makes the whole run a data
-// error), the hit bit comes from the shared-memory bitmap, and the gather is predicated.
+// error), the hit bit is bit (e mod 32) of shared-memory word e >> (5 + shift) (a funnel shift
+// takes its count mod 32, so no mask is needed), and the gather is predicated, with its 64-bit
+// address formed by one wide multiply-add.
 template <bool FILTER>
-__device__ __forceinline__ uint64_t bulk_value(int e, uint32_t cat1, int shift, const uint32_t* bm,
+__device__ __forceinline__ uint64_t bulk_value(int e, uint32_t cat1, int shift5, const uint32_t* bm,
                                                const uint64_t* __restrict__ q, uint32_t& emax) {
   const uint32_t ue = (uint32_t)e;
   emax = max(emax, ue);
   const uint32_t ce = min(ue, cat1);
   uint32_t hit = 1u;
-  if (FILTER) {
-    const uint32_t b = ce >> shift;
-    hit = __funnelshift_r(bm[b >> 5], 0u, b) & 1u;   // bit (b mod 32) of the word
-  }
+  if (FILTER) hit = __funnelshift_r(bm[ce >> shift5], 0u, ce) & 1u;
   uint64_t v = 0;
-  asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p ld.global.nc.u64 %0, [%1];\n\t}"
-      : "+l"(v) : "l"(q + ce), "r"(hit));
+  asm("{\n\t.reg .pred p;\n\t.reg .u64 a;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+      "mad.wide.u32 a, %3, 8, %1;\n\t@p ld.global.nc.u64 %0, [a];\n\t}"
+      : "+l"(v) : "l"(q), "r"(hit), "r"(ce));
   return v;
 }
 
@@ -483,7 +469,7 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
   const LayerConst lc = *p.layer;
   const uint64_t* __restrict__ q = p.q;
   const uint32_t cat = (uint32_t)p.catalogue;
-  const int shift = p.shift;
+  const int shift5 = p.shift + 5;
 
   const int64_t E0 = __ldg(p.offsets + t_lo) - p.id_base;
   const int64_t E1 = __ldg(p.offsets + t_hi) - p.id_base;
@@ -507,7 +493,7 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
   uint32_t emax = 0;                 // largest event ID seen (as unsigned): >= catalogue is an error
   const uint32_t cat1 = cat - 1u;
   auto val_of = [&](int e, bool valid) -> uint64_t {
-    return valid ? bulk_value<FILTER>(e, cat1, shift, bm, q, emax) : 0ull;
+    return valid ? bulk_value<FILTER>(e, cat1, shift5, bm, q, emax) : 0ull;
   };
 
   // Frame: element i at frame position i + mis; 16-byte vectors at frame multiples of 4.
@@ -533,9 +519,10 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
     }
   __syncwarp();
   int32_t timed_out_at = -1;
+  int s = 0;                 // stage of chunk ch (ch mod BK_STAGES) and its mbarrier phase parity
+  uint32_t phase = 0;
   for (int32_t ch = 0; ch < n_chunks; ++ch) {
-    const int s = ch % BK_STAGES;
-    const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((ch / BK_STAGES) & 1), p.wait_limit_ns);
+    const bool ok = mbar_wait_bounded(&bars[s], phase, p.wait_limit_ns);
     if (__any_sync(FULL, !ok)) { timed_out_at = ch; break; }
     const int32_t rb = head + ch * BK_CHUNK_IDS;
     const int32_t n = min(BK_CHUNK_IDS, n_body - ch * BK_CHUNK_IDS);
@@ -556,10 +543,10 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
     if (n == BK_CHUNK_IDS) {        // full chunk: every slot is a real event
 #pragma unroll
       for (int u = 0; u < NQ; ++u) {
-        v[4 * u + 0] = bulk_value<FILTER>(ids4[u].x, cat1, shift, bm, q, emax);
-        v[4 * u + 1] = bulk_value<FILTER>(ids4[u].y, cat1, shift, bm, q, emax);
-        v[4 * u + 2] = bulk_value<FILTER>(ids4[u].z, cat1, shift, bm, q, emax);
-        v[4 * u + 3] = bulk_value<FILTER>(ids4[u].w, cat1, shift, bm, q, emax);
+        v[4 * u + 0] = bulk_value<FILTER>(ids4[u].x, cat1, shift5, bm, q, emax);
+        v[4 * u + 1] = bulk_value<FILTER>(ids4[u].y, cat1, shift5, bm, q, emax);
+        v[4 * u + 2] = bulk_value<FILTER>(ids4[u].z, cat1, shift5, bm, q, emax);
+        v[4 * u + 3] = bulk_value<FILTER>(ids4[u].w, cat1, shift5, bm, q, emax);
       }
     } else {
 #pragma unroll
@@ -584,6 +571,10 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) pos[4 * u + i] = rb + 128 * u + 4 * lane + i;
       walk_window<Acc, NV>(w, p, lc, t_lo, base_abs, lane, rb, rb + n, pos, v);
+    }
+    if (++s == BK_STAGES) {
+      s = 0;
+      phase ^= 1u;
     }
   }
   if (timed_out_at >= 0) {
@@ -695,10 +686,10 @@ __global__ void k_scatter_dense(int32_t n_elts, int64_t catalogue, const int64_t
 // ------------------------------------------------------------------------------------------
 // Host launchers
 // ------------------------------------------------------------------------------------------
-// 32-bit words of a hit bitmap with one bit per 2^shift catalogue events.
+// 32-bit words of the interleaved hit bitmap with one bit per 2^shift catalogue events.
 static int64_t coarse_words(int64_t catalogue, int shift) {
-  const int64_t bits = (catalogue + ((int64_t)1 << shift) - 1) >> shift;
-  return (bits + 31) / 32;
+  const int64_t exact = (catalogue + 31) / 32;
+  return (exact + ((int64_t)1 << shift) - 1) >> shift;
 }
 
 static int bitmap_shift(int64_t catalogue, int64_t max_bytes) {
