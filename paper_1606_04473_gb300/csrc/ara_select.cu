@@ -104,29 +104,78 @@ __device__ __forceinline__ double value_of(uint64_t k) {
   return __longlong_as_double((long long)b);
 }
 
+// Elements are visited in sweeps: in sweep j, thread x of block b reads the SEL_VPT elements
+// base + x + v * SEL_THREADS (v < SEL_VPT) with base = (j * gridDim.x + b) * SEL_THREADS * SEL_VPT,
+// all loads of a sweep issued together.  The loop bound is uniform across each warp, so
+// warp-collective operations see every lane.
+constexpr int SEL_VPT = 8;
+constexpr int SEL_SWEEP = SEL_THREADS * SEL_VPT;
+
+__device__ __forceinline__ void load_sweep(const double* __restrict__ row, int64_t n, int64_t base,
+                                           double (&y)[SEL_VPT], bool (&ok)[SEL_VPT]) {
+#pragma unroll
+  for (int v = 0; v < SEL_VPT; ++v) {
+    const int64_t i = base + threadIdx.x + v * SEL_THREADS;
+    ok[v] = i < n;
+    y[v] = ok[v] ? __ldcg(row + i) : 0.0;
+  }
+}
+
+// One radix pass: the digit histogram of the keys that match each target's prefix.  Targets
+// whose prefixes are equal share one histogram (in pass 0 all of them do), counted once and
+// stored under the group's first target.  Equal digits within a warp are added with one
+// shared-memory atomic (lanes grouped by __match_any_sync).
 __global__ void __launch_bounds__(SEL_THREADS)
 k_select_pass(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScratch sc, int pass) {
   __shared__ uint32_t h[SEL_MAX_T * SEL_BINS];
-  __shared__ uint64_t pre[SEL_MAX_T];
+  __shared__ uint64_t gpre[SEL_MAX_T];      // prefix of each group
+  __shared__ int32_t gldr[SEL_MAX_T];       // first target of each group
+  __shared__ int32_t tgrp[SEL_MAX_T];       // group of each target
+  __shared__ int32_t ngrp;
   __shared__ bool last;
   const int layer = blockIdx.y, nt = tg.n_t;
-  for (int i = threadIdx.x; i < nt * SEL_BINS; i += blockDim.x) h[i] = 0;
-  if (threadIdx.x < nt) pre[threadIdx.x] = pass == 0 ? 0ull : sc.state[layer * nt + threadIdx.x].prefix;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    int ng = 0;
+    for (int t = 0; t < nt; ++t) {
+      const uint64_t pr = pass == 0 ? 0ull : sc.state[layer * nt + t].prefix;
+      int g = 0;
+      while (g < ng && gpre[g] != pr) ++g;
+      if (g == ng) {
+        gpre[g] = pr;
+        gldr[g] = t;
+        ++ng;
+      }
+      tgrp[t] = g;
+    }
+    ngrp = ng;
+  }
+  __syncthreads();
+  const int ng = ngrp;
+  for (int i = threadIdx.x; i < ng * SEL_BINS; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const int shift = 64 - SEL_BITS * (pass + 1);
   const double* row = ylt + (int64_t)layer * n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t key = key_of(row[i]);
-    const uint32_t d = (uint32_t)(key >> shift) & (SEL_BINS - 1);
-    for (int t = 0; t < nt; ++t)
-      if (pass == 0 || (key >> (shift + SEL_BITS)) == (pre[t] >> (shift + SEL_BITS)))
-        atomicAdd(&h[t * SEL_BINS + d], 1u);
+  for (int64_t base = (int64_t)blockIdx.x * SEL_SWEEP; base < n; base += (int64_t)gridDim.x * SEL_SWEEP) {
+    double y[SEL_VPT];
+    bool ok[SEL_VPT];
+    load_sweep(row, n, base, y, ok);
+#pragma unroll
+    for (int v = 0; v < SEL_VPT; ++v) {
+      const uint64_t key = key_of(y[v]);
+      const uint32_t d = (uint32_t)(key >> shift) & (SEL_BINS - 1);
+      for (int g = 0; g < ng; ++g) {
+        const bool m = ok[v] && (pass == 0 || (key >> (shift + SEL_BITS)) == (gpre[g] >> (shift + SEL_BITS)));
+        if (!__any_sync(0xffffffffu, m)) continue;
+        const uint32_t peers = __match_any_sync(0xffffffffu, m ? d : 0xffffffffu);
+        if (m && lane == __ffs(peers) - 1) atomicAdd(&h[g * SEL_BINS + d], (uint32_t)__popc(peers));
+      }
+    }
   }
   __syncthreads();
   uint32_t* gh = sc.hist + ((int64_t)pass * gridDim.y + layer) * nt * SEL_BINS;
-  for (int i = threadIdx.x; i < nt * SEL_BINS; i += blockDim.x)
-    if (h[i]) atomicAdd(&gh[i], h[i]);
+  for (int i = threadIdx.x; i < ng * SEL_BINS; i += blockDim.x)
+    if (h[i]) atomicAdd(&gh[gldr[i / SEL_BINS] * SEL_BINS + (i % SEL_BINS)], h[i]);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0)
@@ -134,16 +183,17 @@ k_select_pass(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScrat
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // Last block: pick the digit of every target, scanning bins from the top (one warp each).
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // Last block: pick the digit of every target from its group's histogram, scanning bins from
+  // the top (one warp per target).
   for (int t = warp; t < nt; t += blockDim.x / 32) {
     SelState st = pass == 0 ? SelState{0ull, tg.rank[t]} : sc.state[layer * nt + t];
+    const uint32_t* th = gh + gldr[tgrp[t]] * SEL_BINS;
     // lane l owns bins [SEL_BINS - 8(l+1), SEL_BINS - 8l) (descending order overall)
     uint32_t c[SEL_BINS / 32];
     uint32_t mine = 0;
 #pragma unroll
     for (int u = 0; u < SEL_BINS / 32; ++u) {
-      c[u] = __ldcg(&gh[t * SEL_BINS + (SEL_BINS - 1 - (lane * (SEL_BINS / 32) + u))]);
+      c[u] = __ldcg(&th[SEL_BINS - 1 - (lane * (SEL_BINS / 32) + u)]);
       mine += c[u];
     }
     uint32_t incl = mine;  // inclusive prefix over lanes (from the top bins down)
@@ -171,7 +221,9 @@ k_select_pass(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScrat
 
 // Tail pass: for every target, the selected key and the counts of keys above / equal to it;
 // for TVaR targets the sum of the values strictly above it; optionally the row sum (mean).
-// The last block combines block partials in block order (deterministic).
+// Each element is read once; every thread keeps its own partial sums in a fixed order, warps
+// and blocks combine them in a fixed order, and the last block adds the block partials in
+// block order, so the result is deterministic.
 __global__ void __launch_bounds__(SEL_THREADS)
 k_select_tail(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScratch sc, int want_mean) {
   __shared__ double ssum[SEL_THREADS / 32][SEL_MAX_T + 1];
@@ -182,29 +234,51 @@ k_select_tail(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScrat
   if (threadIdx.x < nt) thr[threadIdx.x] = sc.state[layer * nt + threadIdx.x].prefix;
   __syncthreads();
   const double* row = ylt + (int64_t)layer * n;
-  for (int t = 0; t <= nt; ++t) {
-    if (t == nt && !want_mean) break;
-    double s = 0.0;
-    unsigned long long cg = 0, ce = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      const double y = row[i];
-      if (t == nt) { s = __dadd_rn(s, y); continue; }
-      const uint64_t k = key_of(y);
-      if (k > thr[t]) { ++cg; if (t >= tg.n_rp) s = __dadd_rn(s, y); }
-      else if (k == thr[t]) ++ce;
+  double s[SEL_MAX_T + 1];
+  uint32_t cg[SEL_MAX_T], ce[SEL_MAX_T];
+#pragma unroll
+  for (int t = 0; t <= SEL_MAX_T; ++t) s[t] = 0.0;
+#pragma unroll
+  for (int t = 0; t < SEL_MAX_T; ++t) cg[t] = ce[t] = 0;
+  for (int64_t base = (int64_t)blockIdx.x * SEL_SWEEP; base < n; base += (int64_t)gridDim.x * SEL_SWEEP) {
+    double y[SEL_VPT];
+    bool ok[SEL_VPT];
+    load_sweep(row, n, base, y, ok);
+#pragma unroll
+    for (int v = 0; v < SEL_VPT; ++v) {
+      if (!ok[v]) continue;
+      const uint64_t k = key_of(y[v]);
+      if (want_mean) s[SEL_MAX_T] = __dadd_rn(s[SEL_MAX_T], y[v]);
+#pragma unroll
+      for (int t = 0; t < SEL_MAX_T; ++t) {
+        if (t >= nt) break;
+        const uint64_t th = thr[t];
+        if (k > th) {
+          ++cg[t];
+          if (t >= tg.n_rp) s[t] = __dadd_rn(s[t], y[v]);
+        } else if (k == th) {
+          ++ce[t];
+        }
+      }
     }
+  }
+#pragma unroll
+  for (int t = 0; t <= SEL_MAX_T; ++t) {
+    if (t < SEL_MAX_T && t >= nt) continue;
+    if (t == SEL_MAX_T && !want_mean) continue;
+    double a = s[t];
+    unsigned long long g = t < SEL_MAX_T ? cg[t] : 0, e = t < SEL_MAX_T ? ce[t] : 0;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-      s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
-      cg += __shfl_down_sync(0xffffffffu, cg, o);
-      ce += __shfl_down_sync(0xffffffffu, ce, o);
+      a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
+      g += __shfl_down_sync(0xffffffffu, g, o);
+      e += __shfl_down_sync(0xffffffffu, e, o);
     }
     if (lane == 0) {
-      ssum[warp][t] = s;
-      if (t < nt) {
-        if (cg) atomicAdd(&sc.gt[layer * nt + t], cg);
-        if (ce) atomicAdd(&sc.eq[layer * nt + t], ce);
+      ssum[warp][t < SEL_MAX_T ? t : nt] = a;
+      if (t < SEL_MAX_T) {
+        if (g) atomicAdd(&sc.gt[layer * nt + t], g);
+        if (e) atomicAdd(&sc.eq[layer * nt + t], e);
       }
     }
   }
@@ -212,10 +286,10 @@ k_select_tail(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScrat
   if (threadIdx.x <= nt && (threadIdx.x >= tg.n_rp || threadIdx.x == nt)) {
     const int t = threadIdx.x;
     if (t < nt || want_mean) {
-      double s = 0.0;
-      for (int w = 0; w < SEL_THREADS / 32; ++w) s = __dadd_rn(s, ssum[w][t]);
-      if (t < nt) sc.psum[((int64_t)layer * nt + t) * gridDim.x + blockIdx.x] = s;
-      else sc.pmean[(int64_t)layer * gridDim.x + blockIdx.x] = s;
+      double a = 0.0;
+      for (int w = 0; w < SEL_THREADS / 32; ++w) a = __dadd_rn(a, ssum[w][t]);
+      if (t < nt) sc.psum[((int64_t)layer * nt + t) * gridDim.x + blockIdx.x] = a;
+      else sc.pmean[(int64_t)layer * gridDim.x + blockIdx.x] = a;
     }
   }
   __threadfence();
@@ -230,18 +304,18 @@ k_select_tail(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScrat
     const double v = value_of(thr[t]);
     double r = v;
     if (t >= tg.n_rp) {
-      double s = 0.0;
+      double a = 0.0;
       const int64_t base = ((int64_t)layer * nt + t) * gridDim.x;
-      for (unsigned b = 0; b < gridDim.x; ++b) s = __dadd_rn(s, __ldcg(&sc.psum[base + b]));
+      for (unsigned b = 0; b < gridDim.x; ++b) a = __dadd_rn(a, __ldcg(&sc.psum[base + b]));
       const int64_t m = tg.rank[t];
       const int64_t c = (int64_t)__ldcg(&sc.gt[layer * nt + t]);
-      r = (s + (double)(m - c) * v) / (double)m;
+      r = (a + (double)(m - c) * v) / (double)m;
     }
     sc.out[layer * nt + t] = r;
   } else if (threadIdx.x == nt && want_mean) {
-    double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s = __dadd_rn(s, __ldcg(&sc.pmean[(int64_t)layer * gridDim.x + b]));
-    sc.mean[layer] = s / (double)n;
+    double a = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) a = __dadd_rn(a, __ldcg(&sc.pmean[(int64_t)layer * gridDim.x + b]));
+    sc.mean[layer] = a / (double)n;
   }
 }
 
@@ -286,7 +360,7 @@ ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t 
 }
 
 int32_t select_blocks(int64_t n, int n_sms, int32_t n_layers) {
-  int64_t b = (n + SEL_THREADS * 8 - 1) / (SEL_THREADS * 8);
+  int64_t b = (n + SEL_SWEEP - 1) / SEL_SWEEP;
   const int64_t cap = std::max<int64_t>(1, 2 * (int64_t)n_sms / std::max(1, n_layers) + 1);
   return (int32_t)std::max<int64_t>(1, std::min(b, cap));
 }
