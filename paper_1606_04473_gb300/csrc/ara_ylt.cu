@@ -53,6 +53,9 @@ struct FoldOut {
   int bits_from_regime; // bitmap bit = (regime != 0) instead of (stored value != 0)
 };
 
+constexpr int FOLD_GROUP = 32;     // ELTs whose record ranges are searched together
+constexpr int FOLD_REC = 2048;     // records staged in shared memory per batch
+
 template <typename LossT>
 __global__ void __launch_bounds__(FOLD_THREADS)
 k_fold(int64_t catalogue, const int64_t* __restrict__ rec_off, const int32_t* __restrict__ rec_ids,
@@ -60,31 +63,66 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ rec_off, const int32_t* __
        const double* __restrict__ elt_lim, const int32_t* __restrict__ layer_elts,
        const LayerConst* __restrict__ layers, SelList sel, FoldOut out) {
   __shared__ double s[FOLD_TILE];
-  __shared__ int32_t list[FOLD_TILE];
+  __shared__ int32_t list[FOLD_TILE];        // staged record offsets, then the touched events
+  __shared__ double rx[FOLD_REC];            // staged records after the ELT terms
   __shared__ uint8_t reg[FOLD_TILE];
+  __shared__ int64_t lo[FOLD_GROUP], hi[FOLD_GROUP];
+  __shared__ int32_t cnt_off[FOLD_GROUP + 1];
+  __shared__ int32_t n_batch;
   __shared__ int32_t n_list;
-  __shared__ int64_t rng[2];
   const int layer = sel.idx[blockIdx.y];
   const int64_t slot = out.by_slot ? blockIdx.y : layer;
   const LayerConst lc = layers[layer];
   const int64_t t0 = (int64_t)blockIdx.x * FOLD_TILE;
   const int64_t t1 = min(t0 + (int64_t)FOLD_TILE, catalogue);
+  const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < FOLD_TILE; i += blockDim.x) { s[i] = 0.0; reg[i] = 0; }
   if (threadIdx.x == 0) n_list = 0;
-  for (int k = lc.elt_begin; k < lc.elt_end; ++k) {
-    const int j = layer_elts[k];
-    if (threadIdx.x == 0) {
-      int64_t a = lower_bound_ids(rec_ids, rec_off[j], rec_off[j + 1], t0);
-      rng[0] = a;
-      rng[1] = lower_bound_ids(rec_ids, a, rec_off[j + 1], t1);
+  // The layer's ELTs in order, in batches: the record ranges of up to FOLD_GROUP ELTs within
+  // this tile are found by parallel binary searches, the records of the longest prefix of them
+  // that fits FOLD_REC are loaded at once with their ELT terms applied, and then added into
+  // the tile one ELT after the other (IDs are unique within an ELT, so one ELT's records never
+  // collide), which keeps the FP64 sum in the layer's ELT order.
+  for (int k0 = lc.elt_begin; k0 < lc.elt_end;) {
+    const int G = min(FOLD_GROUP, lc.elt_end - k0);
+    if (threadIdx.x < 2 * G) {
+      const int g = threadIdx.x % G;
+      const int j = layer_elts[k0 + g];
+      const int64_t v = lower_bound_ids(rec_ids, rec_off[j], rec_off[j + 1], threadIdx.x < G ? t0 : t1);
+      if (threadIdx.x < G) lo[g] = v; else hi[g] = v;
     }
     __syncthreads();
-    const double R = elt_ret[j], L = elt_lim[j];
-    for (int64_t r = rng[0] + threadIdx.x; r < rng[1]; r += blockDim.x) {
-      const int e = (int)(rec_ids[r] - t0);
-      s[e] = __dadd_rn(s[e], clamp_terms((double)rec_loss[r], R, L));  // IDs unique per ELT
+    if (threadIdx.x < 32) {   // counts -> offsets; the batch is the longest prefix that fits
+      const int32_t c = lane < G ? (int32_t)(hi[lane] - lo[lane]) : 0;
+      int32_t incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+      }
+      cnt_off[lane + 1] = incl;
+      if (lane == 0) cnt_off[0] = 0;
+      const unsigned fit = __ballot_sync(FULL, lane < G && incl <= FOLD_REC);
+      if (lane == 0) n_batch = fit ? 32 - __clz((int)fit) : 1;  // a single ELT always fits
     }
     __syncthreads();
+    const int nb = n_batch;
+    const int32_t total = cnt_off[nb];
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      int g = 0;
+      while (cnt_off[g + 1] <= i) ++g;
+      const int j = layer_elts[k0 + g];
+      const int64_t r = lo[g] + (i - cnt_off[g]);
+      list[i] = (int32_t)(rec_ids[r] - t0);
+      rx[i] = clamp_terms((double)rec_loss[r], elt_ret[j], elt_lim[j]);
+    }
+    __syncthreads();
+    for (int g = 0; g < nb; ++g) {
+      for (int i = cnt_off[g] + threadIdx.x; i < cnt_off[g + 1]; i += blockDim.x)
+        s[list[i]] = __dadd_rn(s[list[i]], rx[i]);
+      __syncthreads();
+    }
+    k0 += nb;
   }
   // Compact the touched events so the FP64 occurrence clamp runs on full warps only.
   for (int i = threadIdx.x; i < (int)(t1 - t0); i += blockDim.x)
@@ -293,11 +331,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)),
       "l"(pol) : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+// Test a phase of an mbarrier; while it is incomplete the thread is suspended (not spinning)
+// until the phase completes or about hint_ns nanoseconds pass.  False if it is still incomplete.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
   uint32_t ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns) : "memory");
   return ok != 0;
 }
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -305,12 +345,16 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for a phase of an mbarrier for at most limit_ns nanoseconds; false on timeout.
+// Wait for a phase of an mbarrier for at most about limit_ns nanoseconds; false on timeout.
+// Each try suspends the warp for up to kWaitHintNs, so a warp whose copy is still in flight
+// leaves its issue slots to the others instead of spinning.
+constexpr uint32_t kWaitHintNs = 20000;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
+  const uint32_t hint = limit_ns < kWaitHintNs ? (uint32_t)limit_ns : kWaitHintNs;
+  if (mbar_try_wait(bar, parity, hint)) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity, hint)) return true;
     if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
