@@ -371,7 +371,7 @@ extern "C" ara_status ara_adjoint(ara_portfolio* pf_, int64_t n_trials, const in
 
   // TVaR threshold, #{y > v} and #{y == v} of every selected layer
   SelectResult sr;
-  ara_status st = select_one_rank(d_ylt, n_trials, n_sel, m, pf->n_sms, s, &sr);
+  ara_status st = select_one_rank(d_ylt, n_trials, n_sel, m, pf->n_sms, s, &sr, pf->d_err);
   if (st != ARA_OK) return st;
 
   // scratch

@@ -35,12 +35,6 @@ template <typename Acc> struct AccOps;
 template <> struct AccOps<U128> {
   static __device__ __forceinline__ U128 zero() { return U128{0ull, 0ull}; }
   static __device__ __forceinline__ void add(U128& a, uint64_t v) { add_u64(a, v); }
-  // add lo + hi * 2^32 (the split sums of up to 16 table values; hi < 2^36)
-  template <int NV>
-  static __device__ __forceinline__ void add_split(U128& a, uint64_t lo, uint64_t hi, const uint64_t (&)[NV]) {
-    add_u64(a, lo);
-    add_u128(a, hi << 32, hi >> 32);
-  }
   static __device__ __forceinline__ U128 warp_sum(U128 a) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -73,11 +67,6 @@ template <> struct AccOps<double> {
   static __device__ __forceinline__ void add(double& a, uint64_t v) {
     a = __dadd_rn(a, __longlong_as_double((long long)v));
   }
-  template <int NV>
-  static __device__ __forceinline__ void add_split(double& a, uint64_t, uint64_t, const uint64_t (&v)[NV]) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) a = __dadd_rn(a, __longlong_as_double((long long)v[i]));
-  }
   static __device__ __forceinline__ double warp_sum(double a) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) a = __dadd_rn(a, __shfl_xor_sync(FULL, a, o));
@@ -100,11 +89,6 @@ struct OepMax {
 template <> struct AccOps<OepMax> {
   static __device__ __forceinline__ OepMax zero() { return OepMax{0ull}; }
   static __device__ __forceinline__ void add(OepMax& a, uint64_t v) { a.v = a.v > v ? a.v : v; }
-  template <int NV>
-  static __device__ __forceinline__ void add_split(OepMax& a, uint64_t, uint64_t, const uint64_t (&v)[NV]) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) a.v = a.v > v[i] ? a.v : v[i];
-  }
   static __device__ __forceinline__ OepMax warp_sum(OepMax a) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -118,6 +102,48 @@ template <> struct AccOps<OepMax> {
     reg = 0;
     return __dmul_rn(__ull2double_rn(S.v), lc.inv_scale);
   }
+};
+
+// Per-lane partial of the current trial in the bulk stream (LaneOps<Acc>::T), reduced over the
+// warp into an Acc at the trial's end.
+//
+// For exact sums the partial is two 64-bit sums of the low and high 32-bit halves of the table
+// values, each added with one wide multiply-add (the FMA pipe; no carry chain per value).  A
+// lane holds at most n_t / 32 + 16 values of a trial (n_t < 2^31), each half below 2^32, so
+// neither sum nor their warp totals can overflow; the 128-bit sum lo + hi * 2^32 is formed
+// once per trial.
+template <typename Acc> struct LaneOps;
+template <> struct LaneOps<U128> {
+  struct T {
+    uint64_t lo, hi;
+  };
+  static __device__ __forceinline__ T zero() { return T{0ull, 0ull}; }
+  static __device__ __forceinline__ void add(T& a, uint64_t v) {
+    asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(a.lo) : "r"((uint32_t)v));
+    asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(a.hi) : "r"((uint32_t)(v >> 32)));
+  }
+  static __device__ __forceinline__ U128 reduce(T a) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      a.lo += __shfl_xor_sync(FULL, a.lo, o);
+      a.hi += __shfl_xor_sync(FULL, a.hi, o);
+    }
+    U128 r{a.lo, 0ull};
+    add_u128(r, a.hi << 32, a.hi >> 32);
+    return r;
+  }
+};
+template <> struct LaneOps<double> {
+  using T = double;
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ void add(T& a, uint64_t v) { AccOps<double>::add(a, v); }
+  static __device__ __forceinline__ double reduce(T a) { return AccOps<double>::warp_sum(a); }
+};
+template <> struct LaneOps<OepMax> {
+  using T = OepMax;
+  static __device__ __forceinline__ T zero() { return OepMax{0ull}; }
+  static __device__ __forceinline__ void add(T& a, uint64_t v) { AccOps<OepMax>::add(a, v); }
+  static __device__ __forceinline__ OepMax reduce(T a) { return AccOps<OepMax>::warp_sum(a); }
 };
 
 }  // namespace ara

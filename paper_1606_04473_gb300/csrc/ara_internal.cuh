@@ -148,6 +148,8 @@ void set_bulk_shape(int32_t i);
 void bulk_shape(int32_t i, int32_t* warps, int32_t* stages);
 void set_wait_limit_ns(uint64_t ns);
 void set_debug_extra_tx(uint32_t bytes);
+// Bound of every device-side wait (bulk copies, grid barriers), in nanoseconds.
+uint64_t wait_limit_ns();
 // Host check of risk-metric arguments (ranks within [1, n]); ARA_OK or ARA_EINVAL.
 ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t n_tvar,
                             const double* levels);
@@ -164,7 +166,7 @@ struct SelectResult {
   const unsigned long long* eq = nullptr;
 };
 ara_status select_one_rank(const double* d_ylt, int64_t n, int32_t n_layers, int64_t m, int n_sms,
-                           cudaStream_t s, SelectResult* out);
+                           cudaStream_t s, SelectResult* out, uint32_t* err);
 void free_select_result(SelectResult& r, cudaStream_t s);
 // PML / TVaR of n_layers device YLT rows into host arrays (synchronises s); scratch from the
 // stream-ordered allocator.

@@ -2,10 +2,11 @@
 // statistics: PML(RP) is the ceil(N/RP)-th largest year loss, TVaR(p) the mean of the
 // ceil(N(1-p)) largest.  Both come from an exact radix select on order-preserving 64-bit keys
 // of the FP64 year losses (8 passes of 8 bits), followed by one pass summing the tail above
-// the selected key.  Every block of a pass adds its shared-memory histogram into the pass's
-// global histogram; the last block to finish (ticket counter, no waiting) advances the
-// selection state.  Results are bit-exact copies of YLT entries (PML) and a deterministic
-// FP64 sum (TVaR).
+// the selected key.  One cooperative launch runs every pass: each block adds its shared-memory
+// digit histogram into the pass's global histogram, all blocks meet at a grid barrier (a
+// bounded wait), and every block then reads the histogram and advances the selection itself.
+// Results are bit-exact copies of YLT entries (PML) and deterministic FP64 sums (TVaR, mean):
+// fixed per-thread order, fixed warp and block trees, block partials combined in a fixed order.
 
 #include <cmath>
 #include <mutex>
@@ -19,7 +20,7 @@ constexpr int SEL_BITS = 8;
 constexpr int SEL_BINS = 1 << SEL_BITS;
 constexpr int SEL_PASSES = 64 / SEL_BITS;
 constexpr int SEL_MAX_T = 16;
-constexpr int SEL_THREADS = 256;
+constexpr int SEL_THREADS = 1024;
 
 struct SelTargets {
   int32_t n_t;                 // targets per layer
@@ -28,69 +29,82 @@ struct SelTargets {
 };
 
 struct SelState {
-  uint64_t prefix;             // key bits fixed so far
+  uint64_t prefix;             // key bits fixed so far (after the last pass: the selected key)
   int64_t k;                   // rank still to find among keys matching the prefix
 };
 
-// Scratch layout (one allocation, zero-filled before the first pass):
-//   hist   [SEL_PASSES][n_layers][n_t][SEL_BINS]  uint32
-//   ticket [SEL_PASSES + 1][n_layers]             uint32
+// Scratch layout (one allocation, zero-filled before the launch):
+//   hist   [n_layers][SEL_PASSES][n_t][SEL_BINS]  uint32
+//   bar    [n_layers]                             uint32 grid-barrier counter of the launch
+//                                                 whose first layer this is
+//   err    [1]                                    uint32: a grid barrier timed out
 //   state  [n_layers][n_t]                        SelState
-//   psum   [n_layers][n_t][blocks]                double
-//   pcnt   [n_layers][n_t][blocks]                int64
-//   out    [n_layers][n_t]                        double
-//   gt, eq [n_layers][n_t]                        int64: #{key > selected}, #{key == selected}
-//   pmean  [n_layers][blocks]                     double (block partial sums of the whole row)
+//   psum   [n_layers][n_t][blocks]                double   block partial: sum of y > key
+//   pgt    [n_layers][n_t][blocks]                uint64   block partial: #{y > key}
+//   peq    [n_layers][n_t][blocks]                uint64   block partial: #{y == key}
+//   out    [n_layers][n_t]                        double   PML / TVaR
+//   gt, eq [n_layers][n_t]                        uint64   totals
+//   pmean  [n_layers][blocks]                     double   block partial of the row sum
 //   mean   [n_layers]                             double
 struct SelScratch {
   uint32_t* hist;
-  uint32_t* ticket;
+  uint32_t* bar;
+  uint32_t* err;
   SelState* state;
   double* psum;
-  int64_t* pcnt;
+  unsigned long long* pgt;
+  unsigned long long* peq;
   double* out;
   unsigned long long* gt;
   unsigned long long* eq;
   double* pmean;
   double* mean;
+  uint32_t* ext_err;     // optional (nullptr): also gets DERR_TIMEOUT when a barrier times out
 };
 
-size_t select_scratch_bytes(int32_t n_layers, int32_t n_t, int32_t blocks) {
+template <typename F>
+static size_t layout(int32_t n_layers, int32_t n_t, int32_t blocks, F&& take) {
+  const size_t lt = (size_t)n_layers * n_t, ltb = lt * blocks;
   size_t b = 0;
-  auto take = [&](size_t n) { b = (b + 255) / 256 * 256 + n; };
-  take(sizeof(uint32_t) * SEL_PASSES * n_layers * n_t * SEL_BINS);
-  take(sizeof(uint32_t) * (SEL_PASSES + 1) * n_layers);
-  take(sizeof(SelState) * n_layers * n_t);
-  take(sizeof(double) * n_layers * n_t * blocks);
-  take(sizeof(int64_t) * n_layers * n_t * blocks);
-  take(sizeof(double) * n_layers * n_t);
-  take(sizeof(int64_t) * n_layers * n_t);
-  take(sizeof(int64_t) * n_layers * n_t);
-  take(sizeof(double) * n_layers * blocks);
-  take(sizeof(double) * n_layers);
+  auto t = [&](size_t n) { b = (b + 255) / 256 * 256; take(b); b += n; };
+  t(sizeof(uint32_t) * SEL_PASSES * lt * SEL_BINS);
+  t(sizeof(uint32_t) * n_layers);
+  t(sizeof(uint32_t));
+  t(sizeof(SelState) * lt);
+  t(sizeof(double) * ltb);
+  t(sizeof(uint64_t) * ltb);
+  t(sizeof(uint64_t) * ltb);
+  t(sizeof(double) * lt);
+  t(sizeof(uint64_t) * lt);
+  t(sizeof(uint64_t) * lt);
+  t(sizeof(double) * (size_t)n_layers * blocks);
+  t(sizeof(double) * n_layers);
   return (b + 255) / 256 * 256;
 }
 
+size_t select_scratch_bytes(int32_t n_layers, int32_t n_t, int32_t blocks) {
+  return layout(n_layers, n_t, blocks, [](size_t) {});
+}
+
 static SelScratch carve(void* base, int32_t n_layers, int32_t n_t, int32_t blocks) {
-  size_t b = 0;
+  size_t off[12];
+  int i = 0;
+  layout(n_layers, n_t, blocks, [&](size_t o) { off[i++] = o; });
   char* p = (char*)base;
-  auto take = [&](size_t n) {
-    b = (b + 255) / 256 * 256;
-    void* r = p + b;
-    b += n;
-    return r;
-  };
   SelScratch s;
-  s.hist = (uint32_t*)take(sizeof(uint32_t) * SEL_PASSES * n_layers * n_t * SEL_BINS);
-  s.ticket = (uint32_t*)take(sizeof(uint32_t) * (SEL_PASSES + 1) * n_layers);
-  s.state = (SelState*)take(sizeof(SelState) * n_layers * n_t);
-  s.psum = (double*)take(sizeof(double) * n_layers * n_t * blocks);
-  s.pcnt = (int64_t*)take(sizeof(int64_t) * n_layers * n_t * blocks);
-  s.out = (double*)take(sizeof(double) * n_layers * n_t);
-  s.gt = (unsigned long long*)take(sizeof(int64_t) * n_layers * n_t);
-  s.eq = (unsigned long long*)take(sizeof(int64_t) * n_layers * n_t);
-  s.pmean = (double*)take(sizeof(double) * n_layers * blocks);
-  s.mean = (double*)take(sizeof(double) * n_layers);
+  s.hist = (uint32_t*)(p + off[0]);
+  s.bar = (uint32_t*)(p + off[1]);
+  s.err = (uint32_t*)(p + off[2]);
+  s.state = (SelState*)(p + off[3]);
+  s.psum = (double*)(p + off[4]);
+  s.pgt = (unsigned long long*)(p + off[5]);
+  s.peq = (unsigned long long*)(p + off[6]);
+  s.out = (double*)(p + off[7]);
+  s.gt = (unsigned long long*)(p + off[8]);
+  s.eq = (unsigned long long*)(p + off[9]);
+  s.pmean = (double*)(p + off[10]);
+  s.mean = (double*)(p + off[11]);
+  s.ext_err = nullptr;
   return s;
 }
 
@@ -104,218 +118,275 @@ __device__ __forceinline__ double value_of(uint64_t k) {
   return __longlong_as_double((long long)b);
 }
 
-// Elements are visited in sweeps: in sweep j, thread x of block b reads the SEL_VPT elements
-// base + x + v * SEL_THREADS (v < SEL_VPT) with base = (j * gridDim.x + b) * SEL_THREADS * SEL_VPT,
-// all loads of a sweep issued together.  The loop bound is uniform across each warp, so
-// warp-collective operations see every lane.
-constexpr int SEL_VPT = 8;
-constexpr int SEL_SWEEP = SEL_THREADS * SEL_VPT;
-
-__device__ __forceinline__ void load_sweep(const double* __restrict__ row, int64_t n, int64_t base,
-                                           double (&y)[SEL_VPT], bool (&ok)[SEL_VPT]) {
-#pragma unroll
-  for (int v = 0; v < SEL_VPT; ++v) {
-    const int64_t i = base + threadIdx.x + v * SEL_THREADS;
-    ok[v] = i < n;
-    y[v] = ok[v] ? __ldcg(row + i) : 0.0;
-  }
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t sel_globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-// One radix pass: the digit histogram of the keys that match each target's prefix.  Targets
-// whose prefixes are equal share one histogram (in pass 0 all of them do), counted once and
-// stored under the group's first target.  Equal digits within a warp are added with one
-// shared-memory atomic (lanes grouped by __match_any_sync).
-__global__ void __launch_bounds__(SEL_THREADS)
-k_select_pass(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScratch sc, int pass) {
+// Grid barrier of a cooperative launch: every block adds one to *bar, then waits until it
+// reaches `target` (the number of blocks times the barrier's ordinal).  The wait is bounded by
+// limit_ns; on timeout the block sets *err (and DERR_TIMEOUT in *ext_err) and the whole block
+// returns false.
+__device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t target, uint64_t limit_ns,
+                                             uint32_t* err, uint32_t* ext_err, int* ok_s) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    if (ld_acquire_gpu(bar) < target) {
+      const uint64_t t0 = sel_globaltimer();
+      while (ld_acquire_gpu(bar) < target) {
+        if (sel_globaltimer() - t0 > limit_ns) {
+          ok = 0;
+          atomicOr(err, 1u);
+          if (ext_err) atomicOr(ext_err, DERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    *ok_s = ok;
+  }
+  __syncthreads();
+  return *ok_s != 0;
+}
+
+constexpr int SEL_WARPS = SEL_THREADS / 32;
+// Values of a block's slice kept in shared memory across the passes (when the slice fits).
+constexpr int SEL_SMEM_VALUES = 24000;
+
+// The whole selection of the layers [l0, l0 + gridDim.y): 8 radix passes and the tail pass.
+// Block b of a layer owns the contiguous slice [b n / B, (b + 1) n / B) of the layer's row;
+// when it fits, the slice is read once into shared memory and every pass reads it there.
+//
+// Pass: the digit histogram of the keys that match each target's prefix.  Targets whose
+// prefixes are equal share one histogram (in pass 0 all of them do), counted once and stored
+// under the group's first target.  Equal digits within a warp are added with one
+// shared-memory atomic (lanes grouped by __match_any_sync).  After the grid barrier every
+// block picks each target's digit from the global histogram (one warp per target, bins
+// scanned from the top) and keeps the selection state in shared memory.
+//
+// Tail: per target, #{key > selected}, #{key == selected} and (TVaR) the sum of the values
+// above the selected key; optionally the row sum.  Every thread sums its own values in index
+// order, warps and blocks combine in a fixed order, and after a last grid barrier block 0 of
+// each layer combines the block partials in a fixed order: the sums are deterministic.
+__global__ void __launch_bounds__(SEL_THREADS, 1)
+k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, SelScratch sc,
+         int want_mean, uint64_t limit_ns, int64_t smem_values) {
+  extern __shared__ double vals[];
   __shared__ uint32_t h[SEL_MAX_T * SEL_BINS];
+  __shared__ uint64_t pre[SEL_MAX_T];
+  __shared__ int64_t kk[SEL_MAX_T];
   __shared__ uint64_t gpre[SEL_MAX_T];      // prefix of each group
   __shared__ int32_t gldr[SEL_MAX_T];       // first target of each group
   __shared__ int32_t tgrp[SEL_MAX_T];       // group of each target
   __shared__ int32_t ngrp;
-  __shared__ bool last;
-  const int layer = blockIdx.y, nt = tg.n_t;
+  __shared__ int bar_ok;
+  __shared__ double wsum[SEL_WARPS];
+  __shared__ unsigned long long wgt[SEL_WARPS], weq[SEL_WARPS];
+  const int layer = l0 + blockIdx.y, nt = tg.n_t;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    int ng = 0;
-    for (int t = 0; t < nt; ++t) {
-      const uint64_t pr = pass == 0 ? 0ull : sc.state[layer * nt + t].prefix;
-      int g = 0;
-      while (g < ng && gpre[g] != pr) ++g;
-      if (g == ng) {
-        gpre[g] = pr;
-        gldr[g] = t;
-        ++ng;
+  const uint32_t nblk = gridDim.x * gridDim.y;
+  uint32_t* bar = sc.bar + l0;
+  const int64_t i0 = (int64_t)blockIdx.x * n / gridDim.x;
+  const int64_t cnt = ((int64_t)blockIdx.x + 1) * n / gridDim.x - i0;
+  const double* src = ylt + (int64_t)layer * n + i0;
+  const bool resident = cnt <= smem_values;   // smem_values: doubles of dynamic shared memory
+  if (resident) {
+    constexpr int U = 8;   // independent loads in flight per thread
+    for (int64_t j = 0; j < cnt; j += (int64_t)U * SEL_THREADS) {
+      double y[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = j + u * SEL_THREADS + threadIdx.x;
+        y[u] = i < cnt ? __ldcg(src + i) : 0.0;
       }
-      tgrp[t] = g;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = j + u * SEL_THREADS + threadIdx.x;
+        if (i < cnt) vals[i] = y[u];
+      }
     }
-    ngrp = ng;
+  }
+  if (threadIdx.x < nt) {
+    pre[threadIdx.x] = 0ull;
+    kk[threadIdx.x] = tg.rank[threadIdx.x];
   }
   __syncthreads();
-  const int ng = ngrp;
-  for (int i = threadIdx.x; i < ng * SEL_BINS; i += blockDim.x) h[i] = 0;
-  __syncthreads();
-  const int shift = 64 - SEL_BITS * (pass + 1);
-  const double* row = ylt + (int64_t)layer * n;
-  for (int64_t base = (int64_t)blockIdx.x * SEL_SWEEP; base < n; base += (int64_t)gridDim.x * SEL_SWEEP) {
-    double y[SEL_VPT];
-    bool ok[SEL_VPT];
-    load_sweep(row, n, base, y, ok);
-#pragma unroll
-    for (int v = 0; v < SEL_VPT; ++v) {
-      const uint64_t key = key_of(y[v]);
+  auto value = [&](int64_t i) -> double { return resident ? vals[i] : __ldcg(src + i); };
+
+  const int passes = nt > 0 ? SEL_PASSES : 0;
+  for (int pass = 0; pass < passes; ++pass) {
+    if (threadIdx.x == 0) {
+      int ng = 0;
+      for (int t = 0; t < nt; ++t) {
+        int g = 0;
+        while (g < ng && gpre[g] != pre[t]) ++g;
+        if (g == ng) {
+          gpre[g] = pre[t];
+          gldr[g] = t;
+          ++ng;
+        }
+        tgrp[t] = g;
+      }
+      ngrp = ng;
+    }
+    __syncthreads();
+    const int ng = ngrp;
+    for (int i = threadIdx.x; i < ng * SEL_BINS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int shift = 64 - SEL_BITS * (pass + 1);
+    for (int64_t j = 0; j < cnt; j += SEL_THREADS) {   // bound uniform over the block
+      const int64_t i = j + threadIdx.x;
+      const bool ok = i < cnt;
+      const uint64_t key = key_of(ok ? value(i) : 0.0);
       const uint32_t d = (uint32_t)(key >> shift) & (SEL_BINS - 1);
       for (int g = 0; g < ng; ++g) {
-        const bool m = ok[v] && (pass == 0 || (key >> (shift + SEL_BITS)) == (gpre[g] >> (shift + SEL_BITS)));
+        const bool m = ok && (pass == 0 || (key >> (shift + SEL_BITS)) == (gpre[g] >> (shift + SEL_BITS)));
         if (!__any_sync(0xffffffffu, m)) continue;
         const uint32_t peers = __match_any_sync(0xffffffffu, m ? d : 0xffffffffu);
         if (m && lane == __ffs(peers) - 1) atomicAdd(&h[g * SEL_BINS + d], (uint32_t)__popc(peers));
       }
     }
-  }
-  __syncthreads();
-  uint32_t* gh = sc.hist + ((int64_t)pass * gridDim.y + layer) * nt * SEL_BINS;
-  for (int i = threadIdx.x; i < ng * SEL_BINS; i += blockDim.x)
-    if (h[i]) atomicAdd(&gh[gldr[i / SEL_BINS] * SEL_BINS + (i % SEL_BINS)], h[i]);
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0)
-    last = atomicAdd(&sc.ticket[pass * gridDim.y + layer], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  // Last block: pick the digit of every target from its group's histogram, scanning bins from
-  // the top (one warp per target).
-  for (int t = warp; t < nt; t += blockDim.x / 32) {
-    SelState st = pass == 0 ? SelState{0ull, tg.rank[t]} : sc.state[layer * nt + t];
-    const uint32_t* th = gh + gldr[tgrp[t]] * SEL_BINS;
-    // lane l owns bins [SEL_BINS - 8(l+1), SEL_BINS - 8l) (descending order overall)
-    uint32_t c[SEL_BINS / 32];
-    uint32_t mine = 0;
+    __syncthreads();
+    uint32_t* gh = sc.hist + ((int64_t)layer * SEL_PASSES + pass) * nt * SEL_BINS;
+    for (int i = threadIdx.x; i < ng * SEL_BINS; i += blockDim.x)
+      if (h[i]) atomicAdd(&gh[gldr[i / SEL_BINS] * SEL_BINS + (i % SEL_BINS)], h[i]);
+    if (!grid_barrier(bar, (uint32_t)(pass + 1) * nblk, limit_ns, sc.err, sc.ext_err, &bar_ok)) return;
+    for (int t = warp; t < nt; t += SEL_WARPS) {
+      const int64_t k = kk[t];
+      const uint32_t* th = gh + gldr[tgrp[t]] * SEL_BINS;
+      // lane l owns bins [SEL_BINS - 8(l+1), SEL_BINS - 8l) (descending order overall)
+      uint32_t c[SEL_BINS / 32];
+      uint32_t mine = 0;
 #pragma unroll
-    for (int u = 0; u < SEL_BINS / 32; ++u) {
-      c[u] = __ldcg(&th[SEL_BINS - 1 - (lane * (SEL_BINS / 32) + u)]);
-      mine += c[u];
-    }
-    uint32_t incl = mine;  // inclusive prefix over lanes (from the top bins down)
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    const uint32_t excl = incl - mine;
-    const bool here = (int64_t)excl < st.k && st.k <= (int64_t)incl;
-    if (here) {
-      int64_t before = excl;
-      int u = 0;
-      for (; u < SEL_BINS / 32; ++u) {
-        if (before + c[u] >= st.k) break;
-        before += c[u];
+      for (int u = 0; u < SEL_BINS / 32; ++u) {
+        c[u] = __ldcg(&th[SEL_BINS - 1 - (lane * (SEL_BINS / 32) + u)]);
+        mine += c[u];
       }
-      const uint32_t bin = SEL_BINS - 1 - (lane * (SEL_BINS / 32) + u);
-      st.k -= before;
-      st.prefix |= (uint64_t)bin << shift;
-      sc.state[layer * nt + t] = st;
-    }
-  }
-}
-
-// Tail pass: for every target, the selected key and the counts of keys above / equal to it;
-// for TVaR targets the sum of the values strictly above it; optionally the row sum (mean).
-// Each element is read once; every thread keeps its own partial sums in a fixed order, warps
-// and blocks combine them in a fixed order, and the last block adds the block partials in
-// block order, so the result is deterministic.
-__global__ void __launch_bounds__(SEL_THREADS)
-k_select_tail(const double* __restrict__ ylt, int64_t n, SelTargets tg, SelScratch sc, int want_mean) {
-  __shared__ double ssum[SEL_THREADS / 32][SEL_MAX_T + 1];
-  __shared__ uint64_t thr[SEL_MAX_T];
-  __shared__ bool last;
-  const int layer = blockIdx.y, nt = tg.n_t;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x < nt) thr[threadIdx.x] = sc.state[layer * nt + threadIdx.x].prefix;
-  __syncthreads();
-  const double* row = ylt + (int64_t)layer * n;
-  double s[SEL_MAX_T + 1];
-  uint32_t cg[SEL_MAX_T], ce[SEL_MAX_T];
+      uint32_t incl = mine;  // inclusive prefix over lanes (from the top bins down)
 #pragma unroll
-  for (int t = 0; t <= SEL_MAX_T; ++t) s[t] = 0.0;
-#pragma unroll
-  for (int t = 0; t < SEL_MAX_T; ++t) cg[t] = ce[t] = 0;
-  for (int64_t base = (int64_t)blockIdx.x * SEL_SWEEP; base < n; base += (int64_t)gridDim.x * SEL_SWEEP) {
-    double y[SEL_VPT];
-    bool ok[SEL_VPT];
-    load_sweep(row, n, base, y, ok);
-#pragma unroll
-    for (int v = 0; v < SEL_VPT; ++v) {
-      if (!ok[v]) continue;
-      const uint64_t k = key_of(y[v]);
-      if (want_mean) s[SEL_MAX_T] = __dadd_rn(s[SEL_MAX_T], y[v]);
-#pragma unroll
-      for (int t = 0; t < SEL_MAX_T; ++t) {
-        if (t >= nt) break;
-        const uint64_t th = thr[t];
-        if (k > th) {
-          ++cg[t];
-          if (t >= tg.n_rp) s[t] = __dadd_rn(s[t], y[v]);
-        } else if (k == th) {
-          ++ce[t];
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const uint32_t excl = incl - mine;
+      if ((int64_t)excl < k && k <= (int64_t)incl) {
+        int64_t before = excl;
+        int u = 0;
+        for (; u < SEL_BINS / 32; ++u) {
+          if (before + c[u] >= k) break;
+          before += c[u];
         }
+        const uint32_t bin = SEL_BINS - 1 - (lane * (SEL_BINS / 32) + u);
+        kk[t] = k - before;
+        pre[t] |= (uint64_t)bin << shift;
       }
     }
+    __syncthreads();
   }
+
+  // ---- tail pass: one target (t == nt: the row sum) at a time ----
+  for (int t = 0; t <= nt; ++t) {
+    if (t == nt && !want_mean) break;
+    const uint64_t thr = t < nt ? pre[t] : 0ull;
+    const bool tvar = t < nt && t >= tg.n_rp;
+    double a = 0.0;
+    uint32_t g = 0, e = 0;
+    for (int64_t i = threadIdx.x; i < cnt; i += SEL_THREADS) {
+      const double y = value(i);
+      if (t == nt) {
+        a = __dadd_rn(a, y);
+        continue;
+      }
+      const uint64_t k = key_of(y);
+      if (k > thr) {
+        ++g;
+        if (tvar) a = __dadd_rn(a, y);
+      } else if (k == thr) {
+        ++e;
+      }
+    }
+    unsigned long long gg = g, ee = e;
 #pragma unroll
-  for (int t = 0; t <= SEL_MAX_T; ++t) {
-    if (t < SEL_MAX_T && t >= nt) continue;
-    if (t == SEL_MAX_T && !want_mean) continue;
-    double a = s[t];
-    unsigned long long g = t < SEL_MAX_T ? cg[t] : 0, e = t < SEL_MAX_T ? ce[t] : 0;
+    for (int o = 16; o; o >>= 1) {
+      a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
+      gg += __shfl_down_sync(0xffffffffu, gg, o);
+      ee += __shfl_down_sync(0xffffffffu, ee, o);
+    }
+    if (lane == 0) {
+      wsum[warp] = a;
+      wgt[warp] = gg;
+      weq[warp] = ee;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      unsigned long long sg = 0, se = 0;
+      for (int w = 0; w < SEL_WARPS; ++w) {
+        s = __dadd_rn(s, wsum[w]);
+        sg += wgt[w];
+        se += weq[w];
+      }
+      if (t < nt) {
+        const int64_t at = ((int64_t)layer * nt + t) * gridDim.x + blockIdx.x;
+        sc.psum[at] = s;
+        sc.pgt[at] = sg;
+        sc.peq[at] = se;
+      } else {
+        sc.pmean[(int64_t)layer * gridDim.x + blockIdx.x] = s;
+      }
+    }
+    __syncthreads();
+  }
+  if (!grid_barrier(bar, (uint32_t)(passes + 1) * nblk, limit_ns, sc.err, sc.ext_err, &bar_ok)) return;
+  if (blockIdx.x != 0) return;
+  // Block 0 of the layer: one warp per target (and one for the mean) combines the block
+  // partials: lane l adds blocks l, l + 32, ... in order, then a fixed shuffle tree.
+  const unsigned B = gridDim.x;
+  for (int t = warp; t <= nt; t += SEL_WARPS) {
+    if (t == nt && !want_mean) continue;
+    double a = 0.0;
+    unsigned long long g = 0, e = 0;
+    if (t < nt) {
+      const int64_t base = ((int64_t)layer * nt + t) * B;
+      for (unsigned b = lane; b < B; b += 32) {
+        a = __dadd_rn(a, __ldcg(&sc.psum[base + b]));
+        g += __ldcg(&sc.pgt[base + b]);
+        e += __ldcg(&sc.peq[base + b]);
+      }
+    } else {
+      for (unsigned b = lane; b < B; b += 32) a = __dadd_rn(a, __ldcg(&sc.pmean[(int64_t)layer * B + b]));
+    }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
       g += __shfl_down_sync(0xffffffffu, g, o);
       e += __shfl_down_sync(0xffffffffu, e, o);
     }
-    if (lane == 0) {
-      ssum[warp][t < SEL_MAX_T ? t : nt] = a;
-      if (t < SEL_MAX_T) {
-        if (g) atomicAdd(&sc.gt[layer * nt + t], g);
-        if (e) atomicAdd(&sc.eq[layer * nt + t], e);
-      }
+    if (lane != 0) continue;
+    if (t == nt) {
+      sc.mean[layer] = a / (double)n;
+      continue;
     }
-  }
-  __syncthreads();
-  if (threadIdx.x <= nt && (threadIdx.x >= tg.n_rp || threadIdx.x == nt)) {
-    const int t = threadIdx.x;
-    if (t < nt || want_mean) {
-      double a = 0.0;
-      for (int w = 0; w < SEL_THREADS / 32; ++w) a = __dadd_rn(a, ssum[w][t]);
-      if (t < nt) sc.psum[((int64_t)layer * nt + t) * gridDim.x + blockIdx.x] = a;
-      else sc.pmean[(int64_t)layer * gridDim.x + blockIdx.x] = a;
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0)
-    last = atomicAdd(&sc.ticket[SEL_PASSES * gridDim.y + layer], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  if (threadIdx.x < nt) {
-    const int t = threadIdx.x;
-    const double v = value_of(thr[t]);
+    const double v = value_of(pre[t]);
     double r = v;
     if (t >= tg.n_rp) {
-      double a = 0.0;
-      const int64_t base = ((int64_t)layer * nt + t) * gridDim.x;
-      for (unsigned b = 0; b < gridDim.x; ++b) a = __dadd_rn(a, __ldcg(&sc.psum[base + b]));
       const int64_t m = tg.rank[t];
-      const int64_t c = (int64_t)__ldcg(&sc.gt[layer * nt + t]);
-      r = (a + (double)(m - c) * v) / (double)m;
+      r = (a + (double)(m - (int64_t)g) * v) / (double)m;
     }
     sc.out[layer * nt + t] = r;
-  } else if (threadIdx.x == nt && want_mean) {
-    double a = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) a = __dadd_rn(a, __ldcg(&sc.pmean[(int64_t)layer * gridDim.x + b]));
-    sc.mean[layer] = a / (double)n;
+    sc.gt[layer * nt + t] = g;
+    sc.eq[layer * nt + t] = e;
+    sc.state[layer * nt + t] = SelState{pre[t], kk[t]};
   }
 }
 
@@ -359,25 +430,61 @@ ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t 
   return select_targets(n, n_rp, rps, n_tvar, levels, tg);
 }
 
+constexpr int SEL_DYN_SMEM = SEL_SMEM_VALUES * (int)sizeof(double);
+
+// Co-resident blocks of k_select on this device (cached per device); 0 on failure.
+static int select_resident_blocks() {
+  static std::mutex mu;
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cached[dev]) {
+    int per_sm = 0, sms = 0;
+    if (cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, SEL_DYN_SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_select, SEL_THREADS, SEL_DYN_SMEM) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+      return 0;
+    cached[dev] = per_sm * sms;
+  }
+  return cached[dev];
+}
+
+// Blocks per layer: one per SM for a single layer, fewer per layer when several share a
+// launch, and never more than one per SEL_THREADS values.
 int32_t select_blocks(int64_t n, int n_sms, int32_t n_layers) {
-  int64_t b = (n + SEL_SWEEP - 1) / SEL_SWEEP;
-  const int64_t cap = std::max<int64_t>(1, 2 * (int64_t)n_sms / std::max(1, n_layers) + 1);
+  const int64_t b = (n + SEL_THREADS - 1) / SEL_THREADS;
+  const int64_t cap = std::max<int64_t>(1, (int64_t)n_sms / std::max(1, n_layers));
   return (int32_t)std::max<int64_t>(1, std::min(b, cap));
 }
 
 // Launch the whole selection into `scratch` (zero-filled here); results land in scratch.out.
+// Layers are split into cooperative launches whose blocks are all co-resident.
 ara_status launch_select(const double* d_ylt, int64_t n, int32_t n_layers, const SelTargets& tg,
                          void* scratch, size_t scratch_bytes, int32_t blocks, int want_mean,
-                         cudaStream_t s, SelScratch* out) {
+                         cudaStream_t s, SelScratch* out, uint32_t* ext_err = nullptr) {
   SelScratch sc = carve(scratch, n_layers, tg.n_t, blocks);
+  sc.ext_err = ext_err;
   ARA_TRY(cudaMemsetAsync(scratch, 0, scratch_bytes, s));
-  {
-    LaunchScope ls(ARA_K_SELECT, s, tg.n_t > 0 ? SEL_PASSES + 1 : 1);
-    dim3 grid(blocks, n_layers);
-    if (tg.n_t > 0)
-      for (int p = 0; p < SEL_PASSES; ++p) k_select_pass<<<grid, SEL_THREADS, 0, s>>>(d_ylt, n, tg, sc, p);
-    k_select_tail<<<grid, SEL_THREADS, 0, s>>>(d_ylt, n, tg, sc, want_mean);
-    ARA_TRY(cudaGetLastError());
+  const int resident = select_resident_blocks();
+  if (resident < blocks) return ARA_ECUDA;
+  const int32_t per_launch = std::max(1, resident / blocks);
+  const uint64_t limit = wait_limit_ns();
+  const int64_t slice = (n + blocks - 1) / blocks;
+  const int dyn = slice <= SEL_SMEM_VALUES ? (int)(slice * sizeof(double)) : 0;
+  for (int32_t l0 = 0; l0 < n_layers; l0 += per_launch) {
+    const int32_t nl = std::min(per_launch, n_layers - l0);
+    LaunchScope ls(ARA_K_SELECT, s);
+    int64_t nn = n;
+    int32_t ll0 = l0;
+    SelTargets t2 = tg;
+    SelScratch s2 = sc;
+    int wm = want_mean;
+    uint64_t lim = limit;
+    int64_t cap = dyn / (int)sizeof(double);
+    void* args[] = {(void*)&d_ylt, &nn, &ll0, &t2, &s2, &wm, &lim, &cap};
+    ARA_TRY(cudaLaunchCooperativeKernel((const void*)k_select, dim3(blocks, nl), dim3(SEL_THREADS),
+                                        args, (size_t)dyn, s));
   }
   *out = sc;
   return ARA_OK;
@@ -390,7 +497,7 @@ using namespace ara;
 namespace ara {
 
 ara_status select_one_rank(const double* d_ylt, int64_t n, int32_t n_layers, int64_t m, int n_sms,
-                           cudaStream_t s, SelectResult* out) {
+                           cudaStream_t s, SelectResult* out, uint32_t* err) {
   SelTargets tg;
   tg.n_t = 1;
   tg.n_rp = 0;
@@ -400,7 +507,7 @@ ara_status select_one_rank(const double* d_ylt, int64_t n, int32_t n_layers, int
   void* scratch = nullptr;
   ARA_TRY(cudaMallocAsync(&scratch, bytes, s));
   SelScratch sc;
-  ara_status st = launch_select(d_ylt, n, n_layers, tg, scratch, bytes, blocks, 0, s, &sc);
+  ara_status st = launch_select(d_ylt, n, n_layers, tg, scratch, bytes, blocks, 0, s, &sc, err);
   if (st != ARA_OK) {
     cudaFreeAsync(scratch, s);
     return st;
@@ -439,16 +546,20 @@ ara_status risk_metrics_device(const double* d_ylt, int64_t n_trials, int32_t n_
   SelScratch sc;
   st = launch_select(d_ylt, n_trials, n_layers, tg, scratch, bytes, blocks, h_mean != nullptr, s, &sc);
   std::vector<double> out((size_t)n_layers * tg.n_t);
+  uint32_t timed_out = 0;
   if (st == ARA_OK) {
     cudaError_t e = cudaMemcpyAsync(out.data(), sc.out, sizeof(double) * out.size(),
                                     cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && h_mean)
       e = cudaMemcpyAsync(h_mean, sc.mean, sizeof(double) * n_layers, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&timed_out, sc.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) st = ARA_ECUDA;
   }
   cudaFreeAsync(scratch, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && st == ARA_OK) st = ARA_ECUDA;
   if (st != ARA_OK) return st;
+  if (timed_out) return ARA_ETIMEOUT;
   for (int32_t l = 0; l < n_layers; ++l) {
     for (int i = 0; i < n_rp; ++i) h_pml[(size_t)l * n_rp + i] = out[(size_t)l * tg.n_t + i];
     for (int i = 0; i < n_tvar; ++i) h_tvar[(size_t)l * n_tvar + i] = out[(size_t)l * tg.n_t + n_rp + i];
@@ -532,6 +643,8 @@ extern "C" ara_status ara_risk_metrics_static(const double* d_ylt, int64_t n_tri
                               sizeof(double) * n_tvar, (size_t)n_layers, cudaMemcpyDeviceToHost, s));
   if (h_mean)
     ARA_TRY(cudaMemcpyAsync(h_mean, sc.mean, sizeof(double) * n_layers, cudaMemcpyDeviceToHost, s));
+  uint32_t timed_out = 0;
+  ARA_TRY(cudaMemcpyAsync(&timed_out, sc.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   ARA_TRY(cudaStreamSynchronize(s));
-  return ARA_OK;
+  return timed_out ? ARA_ETIMEOUT : ARA_OK;
 }

@@ -400,7 +400,8 @@ struct Walk {
   int32_t bbase;    // trial whose end is in lane 0 of nxt
   int32_t nxt;      // lane i: relative end of trial bbase + i
   bool bad;
-  Acc acc, res;
+  typename LaneOps<Acc>::T acc;   // this lane's partial of trial k
+  Acc res;                        // lane (t - gbase): the sum of trial t of the current group
 };
 
 template <typename Acc>
@@ -420,9 +421,9 @@ __device__ __forceinline__ void walk_load_ends(Walk<Acc>& w, const StreamParams&
 template <typename Acc>
 __device__ __forceinline__ void walk_finish(Walk<Acc>& w, const StreamParams& p, const LayerConst& lc,
                                          int64_t t_lo, int64_t base_abs, int lane) {
-  const Acc r = AccOps<Acc>::warp_sum(w.acc);
+  const Acc r = LaneOps<Acc>::reduce(w.acc);
   if (lane == w.k - w.gbase) w.res = r;
-  w.acc = AccOps<Acc>::zero();
+  w.acc = LaneOps<Acc>::zero();
   const int32_t prev = w.end;
   ++w.k;
   if (w.k - w.gbase == 32 || w.k == w.nk) {
@@ -462,25 +463,10 @@ __device__ __forceinline__ void walk_window(Walk<Acc>& w, const StreamParams& p,
     const int32_t seg = min(w.end, re);
 #pragma unroll
     for (int i = 0; i < K; ++i)
-      if (pos[i] >= done && pos[i] < seg) AccOps<Acc>::add(w.acc, val[i]);
+      if (pos[i] >= done && pos[i] < seg) LaneOps<Acc>::add(w.acc, val[i]);
     done = seg;
     if (done >= re) return;
   }
-}
-
-// Sum of the table values of one lane's slots of a chunk, as two exact 64-bit sums of the
-// 32-bit halves (lo + hi * 2^32), accumulated with wide multiply-adds on the FMA pipe.
-template <int NV>
-__device__ __forceinline__ void sum_values(const uint64_t (&v)[NV], uint64_t& lo_sum, uint64_t& hi_sum) {
-  uint64_t lo = 0, hi = 0;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    const uint32_t vl = (uint32_t)v[i], vh = (uint32_t)(v[i] >> 32);
-    asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(lo) : "r"(vl));
-    asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(hi) : "r"(vh));
-  }
-  lo_sum = lo;
-  hi_sum = hi;
 }
 
 template <bool FILTER, typename Acc, int BK_WARPS, int BK_STAGES, int BK_CHUNK_IDS>
@@ -529,7 +515,7 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
   w.gbase = 0;
   w.bbase = 0;
   w.bad = false;
-  w.acc = AccOps<Acc>::zero();
+  w.acc = LaneOps<Acc>::zero();
   w.res = AccOps<Acc>::zero();
   walk_load_ends(w, p, t_lo, base_abs, lane);
   w.end = __shfl_sync(FULL, w.nxt, 0);
@@ -605,9 +591,8 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
     while (w.k < w.nk && w.end <= rb) walk_finish(w, p, lc, t_lo, base_abs, lane);
     if (w.k < w.nk && w.end >= rb + n) {
       // fast path: the whole chunk belongs to the current trial
-      uint64_t lo, hi;
-      sum_values<NV>(v, lo, hi);
-      AccOps<Acc>::add_split(w.acc, lo, hi, v);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) LaneOps<Acc>::add(w.acc, v[i]);
     } else {
       int32_t pos[NV];
 #pragma unroll
@@ -835,6 +820,7 @@ static std::atomic<uint64_t> g_wait_limit_ns{1000000000ull};
 static std::atomic<uint32_t> g_debug_extra_tx{0};
 
 void set_wait_limit_ns(uint64_t ns) { g_wait_limit_ns.store(ns); }
+uint64_t wait_limit_ns() { return g_wait_limit_ns.load(); }
 void set_debug_extra_tx(uint32_t b) { g_debug_extra_tx.store(b); }
 
 template <bool FILTER, typename Acc, int WARPS, int STAGES, int CHUNK>
