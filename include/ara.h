@@ -361,13 +361,35 @@ ARA_API ara_status ara_adjoint_accumulate(ara_portfolio* pf, int64_t n_trials,
  *   h_pml         host [n_layers][n_rp];  h_tvar host [n_layers][n_tvar]
  *   h_mean        host [n_layers] or NULL: the mean year loss (1/N) sum_t y_t of each row
  * n_rp + n_tvar <= 16 (at least one metric requested), n_trials >= 1.  Allocates its scratch
- * with the stream-ordered allocator (cudaMallocAsync) on `stream`.
- * Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA.
+ * with the stream-ordered allocator (cudaMallocAsync) on `stream`.  The selection is one
+ * cooperative launch whose blocks meet at device-side barriers, each wait bounded like the
+ * bulk copies' (ara_debug_set ARA_DBG_WAIT_LIMIT_NS).
+ * Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA, ARA_ETIMEOUT (a barrier wait ran out).
  */
 ARA_API ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, int32_t n_layers,
                             int32_t n_rp, const double* return_periods, int32_t n_tvar,
                             const double* tvar_levels, double* h_pml, double* h_tvar,
                             double* h_mean, void* stream);
+
+/*
+ * ara_risk_metrics, stream-ordered: the results are written to device memory when the work
+ * queued on `stream` completes, and the call returns without waiting, so a caller can queue
+ * the next run behind it (the paper has no counterpart; it is the pipelined form of the same
+ * computation).  Arguments as ara_risk_metrics, except:
+ *   d_pml        device [n_layers][n_rp] double (NULL when n_rp = 0)
+ *   d_tvar       device [n_layers][n_tvar] double (NULL when n_tvar = 0)
+ *   d_mean       device [n_layers] double or NULL
+ *   d_status     device uint32: set to 0 when the work starts; ARA_DEVICE_TIMEOUT is OR-ed
+ *                in when a device-side wait runs out (the other outputs are then undefined)
+ * Scratch comes from the stream-ordered allocator and is released in stream order.  Argument
+ * errors are returned at once (ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA) and nothing is queued.
+ */
+#define ARA_DEVICE_TIMEOUT 4u
+ARA_API ara_status ara_risk_metrics_async(const double* d_ylt, int64_t n_trials, int32_t n_layers,
+                                          int32_t n_rp, const double* return_periods,
+                                          int32_t n_tvar, const double* tvar_levels, double* d_pml,
+                                          double* d_tvar, double* d_mean, uint32_t* d_status,
+                                          void* stream);
 
 /*
  * ara_risk_metrics for callers that cannot allocate device memory.  The paper has no
@@ -409,16 +431,21 @@ ARA_API int32_t ara_stream_shapes(int32_t* warps, int32_t* stages, int32_t max);
 ARA_API ara_status ara_set_stream_shape(int32_t index);
 
 /* Failure-detection hooks (process-wide; for tests).
- *   ARA_DBG_WAIT_LIMIT_NS  bound of every device-side wait for a bulk copy, in ns
- *                          (default 1e9; >= 1000).  A wait that runs out makes the kernel
- *                          record a timeout, wait (bounded) for its own copies in flight and
- *                          return; ara_check then reports ARA_ETIMEOUT.
+ *   ARA_DBG_WAIT_LIMIT_NS  bound of every device-side wait (bulk copies, the risk metrics'
+ *                          grid barriers), in ns (default 1e9; >= 1000).  A bulk-copy wait
+ *                          that runs out makes the kernel record a timeout, wait (bounded) for
+ *                          its own copies in flight and return; ara_check then reports
+ *                          ARA_ETIMEOUT.  A barrier wait that runs out ends the selection;
+ *                          the risk-metrics call reports ARA_ETIMEOUT.
  *   ARA_DBG_STARVE_COPIES  announce this many bytes more than each bulk copy delivers (a
  *                          multiple of 16, <= 4096; 0 = normal): every wait then runs out,
  *                          which exercises the timeout path without any fault.
+ *   ARA_DBG_SKIP_BARRIER_ARRIVAL  1: the selection's blocks do not arrive at its grid
+ *                          barriers, so every barrier wait runs out (0 = normal).
  * ARA_EINVAL for an unknown key or value. */
 #define ARA_DBG_WAIT_LIMIT_NS  1
 #define ARA_DBG_STARVE_COPIES  2
+#define ARA_DBG_SKIP_BARRIER_ARRIVAL 3
 ARA_API ara_status ara_debug_set(int32_t key, int64_t value);
 
 /* kernel classes for timing */

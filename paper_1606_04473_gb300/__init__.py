@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
     L.ara_check.argtypes = [P, P]
     L.ara_risk_metrics.argtypes = [P, i64, i32, i32, P, i32, P, P, P, P, P]
     L.ara_risk_metrics_static.argtypes = [P, i64, i32, i32, P, i32, P, P, P, P, P]
+    L.ara_risk_metrics_async.argtypes = [P, i64, i32, i32, P, i32, P, P, P, P, P, P]
     L.ara_launch_count.restype = i64
     L.ara_stream_shapes.argtypes = [P, P, i32]
     L.ara_stream_shapes.restype = i32
@@ -465,6 +466,35 @@ def risk_metrics(ylt, return_periods: Sequence[float] = (), tvar_levels: Sequenc
     return (pml, tvar, mean) if want_mean else (pml, tvar)
 
 
+ARA_DEVICE_TIMEOUT = 4
+
+
+def risk_metrics_async(ylt, return_periods: Sequence[float], tvar_levels: Sequence[float],
+                       pml, tvar, status, mean=None, stream=None):
+    """Stream-ordered risk metrics (ara_risk_metrics_async): queues the selection on `stream`
+    and returns at once.  pml [n_layers, n_rp], tvar [n_layers, n_tvar], mean [n_layers] (or
+    None) are float64 CUDA tensors and status a 1-element int32 CUDA tensor, all written when
+    the queued work completes (status & ARA_DEVICE_TIMEOUT: a device-side wait ran out)."""
+    import torch
+    ylt2 = ylt if ylt.dim() == 2 else ylt.reshape(1, -1)
+    nl, n = ylt2.shape
+    rp = np.ascontiguousarray(return_periods, dtype=np.float64)
+    lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
+    if tuple(pml.shape) != (nl, rp.size) or tuple(tvar.shape) != (nl, lv.size):
+        raise ValueError("pml / tvar must be [n_layers, n_rp] / [n_layers, n_tvar]")
+    if mean is not None and tuple(mean.shape) != (nl,):
+        raise ValueError("mean must be [n_layers]")
+    if status.numel() != 1 or status.dtype != torch.int32 or not status.is_cuda:
+        raise ValueError("status must be a 1-element int32 CUDA tensor")
+    st = lib().ara_risk_metrics_async(
+        _dev_ptr(ylt2, torch.float64, "ylt"), n, nl, rp.size, _np_ptr(rp), lv.size, _np_ptr(lv),
+        _dev_ptr(pml, torch.float64, "pml") if rp.size else None,
+        _dev_ptr(tvar, torch.float64, "tvar") if lv.size else None,
+        _dev_ptr(mean, torch.float64, "mean") if mean is not None else None,
+        ctypes.c_void_p(status.data_ptr()), _stream_handle(stream))
+    _check(st, "ara_risk_metrics_async")
+
+
 def risk_metrics_static(ylt, return_periods: Sequence[float] = (), tvar_levels: Sequence[float] = (),
                         stream=None, want_mean: bool = False):
     """risk_metrics() without any device allocation (ara_risk_metrics_static), for callers whose
@@ -502,7 +532,7 @@ def set_stream_shape(index: int):
     _check(lib().ara_set_stream_shape(int(index)), "ara_set_stream_shape")
 
 
-ARA_DBG_WAIT_LIMIT_NS, ARA_DBG_STARVE_COPIES = 1, 2
+ARA_DBG_WAIT_LIMIT_NS, ARA_DBG_STARVE_COPIES, ARA_DBG_SKIP_BARRIER_ARRIVAL = 1, 2, 3
 
 
 def debug_set(key: int, value: int):

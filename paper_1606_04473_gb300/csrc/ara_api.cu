@@ -207,6 +207,10 @@ ara_status ara_debug_set(int32_t key, int64_t value) {
       if (value < 0 || value > 4096 || (value & 15)) return ARA_EINVAL;
       set_debug_extra_tx((uint32_t)value);
       return ARA_OK;
+    case ARA_DBG_SKIP_BARRIER_ARRIVAL:
+      if (value != 0 && value != 1) return ARA_EINVAL;
+      set_debug_skip_arrival((int32_t)value);
+      return ARA_OK;
     default:
       return ARA_EINVAL;
   }

@@ -150,6 +150,9 @@ void set_wait_limit_ns(uint64_t ns);
 void set_debug_extra_tx(uint32_t bytes);
 // Bound of every device-side wait (bulk copies, grid barriers), in nanoseconds.
 uint64_t wait_limit_ns();
+// Test hook: the selection's blocks skip their grid-barrier arrivals (every wait runs out).
+void set_debug_skip_arrival(int32_t on);
+int32_t debug_skip_arrival();
 // Host check of risk-metric arguments (ranks within [1, n]); ARA_OK or ARA_EINVAL.
 ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t n_tvar,
                             const double* levels);

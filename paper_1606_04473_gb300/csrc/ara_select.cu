@@ -134,11 +134,12 @@ __device__ __forceinline__ uint64_t sel_globaltimer() {
 // limit_ns; on timeout the block sets *err (and DERR_TIMEOUT in *ext_err) and the whole block
 // returns false.
 __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t target, uint64_t limit_ns,
-                                             uint32_t* err, uint32_t* ext_err, int* ok_s) {
+                                             uint32_t* err, uint32_t* ext_err, int skip_arrival,
+                                             int* ok_s) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(bar, 1u);
+    if (!skip_arrival) atomicAdd(bar, 1u);
     int ok = 1;
     if (ld_acquire_gpu(bar) < target) {
       const uint64_t t0 = sel_globaltimer();
@@ -180,7 +181,7 @@ constexpr int SEL_SMEM_VALUES = 24000;
 // each layer combines the block partials in a fixed order: the sums are deterministic.
 __global__ void __launch_bounds__(SEL_THREADS, 1)
 k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, SelScratch sc,
-         int want_mean, uint64_t limit_ns, int64_t smem_values) {
+         int want_mean, uint64_t limit_ns, int64_t smem_values, int skip_arrival) {
   extern __shared__ double vals[];
   __shared__ uint32_t h[SEL_MAX_T * SEL_BINS];
   __shared__ uint64_t pre[SEL_MAX_T];
@@ -260,7 +261,7 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
     uint32_t* gh = sc.hist + ((int64_t)layer * SEL_PASSES + pass) * nt * SEL_BINS;
     for (int i = threadIdx.x; i < ng * SEL_BINS; i += blockDim.x)
       if (h[i]) atomicAdd(&gh[gldr[i / SEL_BINS] * SEL_BINS + (i % SEL_BINS)], h[i]);
-    if (!grid_barrier(bar, (uint32_t)(pass + 1) * nblk, limit_ns, sc.err, sc.ext_err, &bar_ok)) return;
+    if (!grid_barrier(bar, (uint32_t)(pass + 1) * nblk, limit_ns, sc.err, sc.ext_err, skip_arrival, &bar_ok)) return;
     for (int t = warp; t < nt; t += SEL_WARPS) {
       const int64_t k = kk[t];
       const uint32_t* th = gh + gldr[tgrp[t]] * SEL_BINS;
@@ -347,7 +348,7 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
     }
     __syncthreads();
   }
-  if (!grid_barrier(bar, (uint32_t)(passes + 1) * nblk, limit_ns, sc.err, sc.ext_err, &bar_ok)) return;
+  if (!grid_barrier(bar, (uint32_t)(passes + 1) * nblk, limit_ns, sc.err, sc.ext_err, skip_arrival, &bar_ok)) return;
   if (blockIdx.x != 0) return;
   // Block 0 of the layer: one warp per target (and one for the mean) combines the block
   // partials: lane l adds blocks l, l + 32, ... in order, then a fixed shuffle tree.
@@ -482,7 +483,8 @@ ara_status launch_select(const double* d_ylt, int64_t n, int32_t n_layers, const
     int wm = want_mean;
     uint64_t lim = limit;
     int64_t cap = dyn / (int)sizeof(double);
-    void* args[] = {(void*)&d_ylt, &nn, &ll0, &t2, &s2, &wm, &lim, &cap};
+    int skip = debug_skip_arrival();
+    void* args[] = {(void*)&d_ylt, &nn, &ll0, &t2, &s2, &wm, &lim, &cap, &skip};
     ARA_TRY(cudaLaunchCooperativeKernel((const void*)k_select, dim3(blocks, nl), dim3(SEL_THREADS),
                                         args, (size_t)dyn, s));
   }
@@ -568,6 +570,50 @@ ara_status risk_metrics_device(const double* d_ylt, int64_t n_trials, int32_t n_
 }
 
 }  // namespace ara
+
+extern "C" ara_status ara_risk_metrics_async(const double* d_ylt, int64_t n_trials,
+                                             int32_t n_layers, int32_t n_rp, const double* rps,
+                                             int32_t n_tvar, const double* levels, double* d_pml,
+                                             double* d_tvar, double* d_mean, uint32_t* d_status,
+                                             void* stream) {
+  SelTargets tg;
+  if (!d_ylt || n_layers < 1 || !d_status) return ARA_EINVAL;
+  if ((n_rp > 0 && !d_pml) || (n_tvar > 0 && !d_tvar)) return ARA_EINVAL;
+  if ((uintptr_t)d_ylt & 7) return ARA_EINVAL;
+  ara_status st = select_targets(n_trials, n_rp, rps, n_tvar, levels, tg);
+  if (st != ARA_OK) return st;
+  if (tg.n_t == 0 && !d_mean) return ARA_EINVAL;
+  static_assert(ARA_DEVICE_TIMEOUT == DERR_TIMEOUT, "device timeout flag");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  ARA_TRY(cudaGetDevice(&dev));
+  ARA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int32_t blocks = select_blocks(n_trials, sms, n_layers);
+  const size_t bytes = select_scratch_bytes(n_layers, tg.n_t, blocks);
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) return ARA_ENOMEM;
+  ara_status r = ARA_OK;
+  SelScratch sc;
+  if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s) != cudaSuccess) r = ARA_ECUDA;
+  if (r == ARA_OK)
+    r = launch_select(d_ylt, n_trials, n_layers, tg, scratch, bytes, blocks, d_mean != nullptr, s,
+                      &sc, d_status);
+  if (r == ARA_OK) {
+    const size_t row = sizeof(double) * (size_t)tg.n_t;
+    cudaError_t e = cudaSuccess;
+    if (n_rp > 0)
+      e = cudaMemcpy2DAsync(d_pml, sizeof(double) * n_rp, sc.out, row, sizeof(double) * n_rp,
+                            (size_t)n_layers, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && n_tvar > 0)
+      e = cudaMemcpy2DAsync(d_tvar, sizeof(double) * n_tvar, sc.out + n_rp, row,
+                            sizeof(double) * n_tvar, (size_t)n_layers, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && d_mean)
+      e = cudaMemcpyAsync(d_mean, sc.mean, sizeof(double) * n_layers, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) r = ARA_ECUDA;
+  }
+  cudaFreeAsync(scratch, s);
+  return r;
+}
 
 extern "C" ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, int32_t n_layers,
                                        int32_t n_rp, const double* rps, int32_t n_tvar,

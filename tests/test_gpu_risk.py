@@ -74,3 +74,56 @@ def test_end_to_end_tiny_workload():
     rp, rt = oracle.risk_metrics(ref, [100.0, 250.0], [0.99])
     np.testing.assert_allclose(p, rp, rtol=1e-6)
     np.testing.assert_allclose(t, rt, rtol=1e-6)
+
+
+def test_many_layers_several_launches_and_slices_beyond_shared_memory():
+    """200 layers: one block per layer, so the layers are split over more than one cooperative
+    launch, and each block's slice (30k values) is larger than the shared-memory cache, so the
+    passes read the row from global memory."""
+    rng = np.random.default_rng(5)
+    y = rng.lognormal(12, 1.5, (200, 30_000))
+    y[:, :5_000] = 0.0
+    y[7, 100:400] = 3e9                                  # ties at the top of one row
+    check(y, rps=[10.0, 100.0, 250.0], levels=[0.99, 0.5])
+
+
+def test_async_metrics_equal_synchronous_bitwise():
+    rng = np.random.default_rng(6)
+    y = torch.from_numpy(rng.lognormal(13, 2, (3, 50_001))).cuda()
+    rps, lv = [100.0, 250.0], [0.99, 0.9]
+    p, t, m = ara.risk_metrics(y, rps, lv, want_mean=True)
+    pd = torch.full((3, 2), -1.0, dtype=torch.float64, device="cuda")
+    td = torch.full((3, 2), -1.0, dtype=torch.float64, device="cuda")
+    md = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+    sd = torch.full((1,), 123, dtype=torch.int32, device="cuda")
+    ara.risk_metrics_async(y, rps, lv, pd, td, sd, mean=md)
+    torch.cuda.synchronize()
+    assert int(sd.item()) == 0
+    assert np.array_equal(pd.cpu().numpy(), p) and np.array_equal(td.cpu().numpy(), t)
+    assert np.array_equal(md.cpu().numpy(), m)
+    with pytest.raises(ValueError):
+        ara.risk_metrics_async(y, rps, lv, pd[:2], td, sd)
+
+
+def test_grid_barrier_timeout_is_reported():
+    """The selection's blocks skip their barrier arrivals (test hook): every bounded wait runs
+    out, the call reports ARA_ETIMEOUT (sync) or sets the device status (async), and the next
+    call is correct again.  No fault, no hang: the waits end after 2 ms."""
+    rng = np.random.default_rng(8)
+    y = torch.from_numpy(rng.lognormal(13, 2, (1, 20_000))).cuda()
+    try:
+        ara.debug_set(ara.ARA_DBG_WAIT_LIMIT_NS, 2_000_000)
+        ara.debug_set(ara.ARA_DBG_SKIP_BARRIER_ARRIVAL, 1)
+        with pytest.raises(ara.AraError) as e:
+            ara.risk_metrics(y, [100.0], [0.99])
+        assert e.value.status == ara.ARA_ETIMEOUT
+        pd = torch.zeros((1, 1), dtype=torch.float64, device="cuda")
+        td = torch.zeros((1, 1), dtype=torch.float64, device="cuda")
+        sd = torch.zeros((1,), dtype=torch.int32, device="cuda")
+        ara.risk_metrics_async(y, [100.0], [0.99], pd, td, sd)
+        torch.cuda.synchronize()
+        assert int(sd.item()) & ara.ARA_DEVICE_TIMEOUT
+    finally:
+        ara.debug_set(ara.ARA_DBG_SKIP_BARRIER_ARRIVAL, 0)
+        ara.debug_set(ara.ARA_DBG_WAIT_LIMIT_NS, 1_000_000_000)
+    check(y.cpu().numpy(), rps=[100.0], levels=[0.99])
