@@ -191,6 +191,7 @@ struct StreamParams {
   uint32_t* err;
   uint64_t wait_limit_ns;  // bound of every mbarrier wait
   uint32_t debug_extra_tx; // test hook: bytes announced but never copied (0 in normal use)
+  uint32_t word_bytes;     // 4 (bytes per bitmap word), passed at run time for the address IMAD
 };
 
 // One event ID: range check, hit filter, gather, accumulate.
@@ -368,19 +369,32 @@ __global__ void k_coarsen(const uint32_t* __restrict__ exact, int64_t n_exact, i
     coarse[cw] = coarsen_word(exact, cw, shift, n_exact);
 }
 
-// Table value of one event for the bulk stream: the event index is clamped into the catalogue
-// for addressing (an out-of-range ID is caught through emax, which makes the whole run a data
-// error), the hit bit is bit (e mod 32) of shared-memory word e >> (5 + shift) (a funnel shift
-// takes its count mod 32, so no mask is needed), and the gather is predicated, with its 64-bit
+// Table value of one event for the bulk stream.  The event index is clamped into the catalogue
+// for addressing (an out-of-range ID is caught by the caller's running maximum, which makes the
+// whole run a data error).  The hit bit is bit (e mod 32) of shared-memory word
+// e >> (5 + shift) (a funnel shift takes its count mod 32, so no mask is needed); the word's
+// byte address floor(e * 2^(32 - 5 - shift) / 2^32) * 4 + base is formed with a high multiply
+// and a multiply-add whose factors are run-time parameters, which keeps it on the FMA pipe
+// (the integer ALU pipe is this kernel's busiest).  The gather is predicated, with its 64-bit
 // address formed by one wide multiply-add.
+struct BitmapAddr {
+  uint32_t base;   // shared-memory address of word 0
+  uint32_t mul;    // 2^(32 - 5 - shift)
+  uint32_t four;   // 4, bytes per word
+};
+
 template <bool FILTER>
-__device__ __forceinline__ uint64_t bulk_value(int e, uint32_t cat1, int shift5, const uint32_t* bm,
-                                               const uint64_t* __restrict__ q, uint32_t& emax) {
-  const uint32_t ue = (uint32_t)e;
-  emax = max(emax, ue);
-  const uint32_t ce = min(ue, cat1);
+__device__ __forceinline__ uint64_t bulk_value(int e, uint32_t cat1, const BitmapAddr& ba,
+                                               const uint64_t* __restrict__ q) {
+  const uint32_t ce = min((uint32_t)e, cat1);
   uint32_t hit = 1u;
-  if (FILTER) hit = __funnelshift_r(bm[ce >> shift5], 0u, ce) & 1u;
+  if (FILTER) {
+    uint32_t word;
+    asm("{\n\t.reg .u32 w, a;\n\tmul.hi.u32 w, %1, %2;\n\tmad.lo.u32 a, w, %3, %4;\n\t"
+        "ld.shared.u32 %0, [a];\n\t}"
+        : "=r"(word) : "r"(ce), "r"(ba.mul), "r"(ba.four), "r"(ba.base));
+    hit = __funnelshift_r(word, 0u, ce) & 1u;
+  }
   uint64_t v = 0;
   asm("{\n\t.reg .pred p;\n\t.reg .u64 a;\n\tsetp.ne.u32 p, %2, 0;\n\t"
       "mad.wide.u32 a, %3, 8, %1;\n\t@p ld.global.nc.u64 %0, [a];\n\t}"
@@ -499,7 +513,10 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
   const LayerConst lc = *p.layer;
   const uint64_t* __restrict__ q = p.q;
   const uint32_t cat = (uint32_t)p.catalogue;
-  const int shift5 = p.shift + 5;
+  BitmapAddr ba;
+  ba.base = smem_u32(bm);
+  ba.mul = 1u << (32 - 5 - p.shift);   // shift <= 26: the coarse bitmap always has >= 2 words
+  ba.four = p.word_bytes;
 
   const int64_t E0 = __ldg(p.offsets + t_lo) - p.id_base;
   const int64_t E1 = __ldg(p.offsets + t_hi) - p.id_base;
@@ -523,7 +540,9 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
   uint32_t emax = 0;                 // largest event ID seen (as unsigned): >= catalogue is an error
   const uint32_t cat1 = cat - 1u;
   auto val_of = [&](int e, bool valid) -> uint64_t {
-    return valid ? bulk_value<FILTER>(e, cat1, shift5, bm, q, emax) : 0ull;
+    if (!valid) return 0ull;
+    emax = max(emax, (uint32_t)e);
+    return bulk_value<FILTER>(e, cat1, ba, q);
   };
 
   // Frame: element i at frame position i + mis; 16-byte vectors at frame multiples of 4.
@@ -573,10 +592,12 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
     if (n == BK_CHUNK_IDS) {        // full chunk: every slot is a real event
 #pragma unroll
       for (int u = 0; u < NQ; ++u) {
-        v[4 * u + 0] = bulk_value<FILTER>(ids4[u].x, cat1, shift5, bm, q, emax);
-        v[4 * u + 1] = bulk_value<FILTER>(ids4[u].y, cat1, shift5, bm, q, emax);
-        v[4 * u + 2] = bulk_value<FILTER>(ids4[u].z, cat1, shift5, bm, q, emax);
-        v[4 * u + 3] = bulk_value<FILTER>(ids4[u].w, cat1, shift5, bm, q, emax);
+        emax = __vimax3_u32(emax, (uint32_t)ids4[u].x, (uint32_t)ids4[u].y);
+        emax = __vimax3_u32(emax, (uint32_t)ids4[u].z, (uint32_t)ids4[u].w);
+        v[4 * u + 0] = bulk_value<FILTER>(ids4[u].x, cat1, ba, q);
+        v[4 * u + 1] = bulk_value<FILTER>(ids4[u].y, cat1, ba, q);
+        v[4 * u + 2] = bulk_value<FILTER>(ids4[u].z, cat1, ba, q);
+        v[4 * u + 3] = bulk_value<FILTER>(ids4[u].w, cat1, ba, q);
       }
     } else {
 #pragma unroll
@@ -821,6 +842,9 @@ static std::atomic<uint32_t> g_debug_extra_tx{0};
 
 void set_wait_limit_ns(uint64_t ns) { g_wait_limit_ns.store(ns); }
 uint64_t wait_limit_ns() { return g_wait_limit_ns.load(); }
+static std::atomic<int32_t> g_skip_arrival{0};
+void set_debug_skip_arrival(int32_t on) { g_skip_arrival.store(on); }
+int32_t debug_skip_arrival() { return g_skip_arrival.load(); }
 void set_debug_extra_tx(uint32_t b) { g_debug_extra_tx.store(b); }
 
 template <bool FILTER, typename Acc, int WARPS, int STAGES, int CHUNK>
@@ -875,6 +899,7 @@ ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   sp.mis = (int32_t)(((uintptr_t)a.ids >> 2) & 3);
   sp.catalogue = pf.catalogue;
   sp.shift = bitmap_shift(pf.catalogue, max_smem_bitmap);
+  if (sp.shift > 26) return ARA_EINVAL;   // the bulk lookup's multiplier is 2^(27 - shift)
   sp.smem_words = coarse_words(pf.catalogue, sp.shift);
   sp.bm_words = pf.bm_words;
   sp.err = pf.d_err;
@@ -882,6 +907,7 @@ ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   const int64_t cwords_pad = (sp.smem_words + 3) / 4 * 4;
   sp.wait_limit_ns = g_wait_limit_ns.load();
   sp.debug_extra_tx = g_debug_extra_tx.load();
+  sp.word_bytes = 4;
   const bool per_elt = (a.flags & ARA_RUN_PER_ELT) != 0;
   const bool nof = (a.flags & ARA_RUN_NO_FILTER) != 0;
   const bool f64 = (a.flags & ARA_RUN_F64_SUM) != 0;
