@@ -164,6 +164,11 @@ constexpr int SEL_WARPS = SEL_THREADS / 32;
 // Values of a block's slice kept in shared memory across the passes (when the slice fits).
 constexpr int SEL_SMEM_VALUES = 24000;
 
+// Sub-histograms per block: S = SEL_SUBH / ng copies of each group's histogram, warp w adding
+// into copy w mod S, so warps whose keys share a digit (in the first passes, nearly all) do not
+// contend for one shared-memory word.
+constexpr int SEL_SUBH = 32;
+
 // The whole selection of the layers [l0, l0 + gridDim.y): 8 radix passes and the tail pass.
 // Block b of a layer owns the contiguous slice [b n / B, (b + 1) n / B) of the layer's row;
 // when it fits, the slice is read once into shared memory and every pass reads it there.
@@ -173,26 +178,28 @@ constexpr int SEL_SMEM_VALUES = 24000;
 // under the group's first target.  Equal digits within a warp are added with one
 // shared-memory atomic (lanes grouped by __match_any_sync).  After the grid barrier every
 // block picks each target's digit from the global histogram (one warp per target, bins
-// scanned from the top) and keeps the selection state in shared memory.
+// scanned from the top) and keeps the selection state in shared memory.  The counts of the
+// bins above the chosen one add up, over the passes, to #{key > selected key}; the chosen
+// bin's count in the last pass is #{key == selected key}.
 //
-// Tail: per target, #{key > selected}, #{key == selected} and (TVaR) the sum of the values
-// above the selected key; optionally the row sum.  Every thread sums its own values in index
-// order, warps and blocks combine in a fixed order, and after a last grid barrier block 0 of
-// each layer combines the block partials in a fixed order: the sums are deterministic.
+// Tail (TVaR targets and the row sum only): the sum of the values above the selected key.
+// Every thread sums its own values in index order, warps and blocks combine with fixed trees,
+// and after a last grid barrier block 0 of each layer combines the block partials in a fixed
+// order: the sums are deterministic.
 __global__ void __launch_bounds__(SEL_THREADS, 1)
 k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, SelScratch sc,
          int want_mean, uint64_t limit_ns, int64_t smem_values, int skip_arrival) {
   extern __shared__ double vals[];
-  __shared__ uint32_t h[SEL_MAX_T * SEL_BINS];
+  __shared__ uint32_t h[SEL_SUBH * SEL_BINS];
   __shared__ uint64_t pre[SEL_MAX_T];
   __shared__ int64_t kk[SEL_MAX_T];
+  __shared__ unsigned long long cgt[SEL_MAX_T], ceq[SEL_MAX_T];
   __shared__ uint64_t gpre[SEL_MAX_T];      // prefix of each group
   __shared__ int32_t gldr[SEL_MAX_T];       // first target of each group
   __shared__ int32_t tgrp[SEL_MAX_T];       // group of each target
   __shared__ int32_t ngrp;
   __shared__ int bar_ok;
   __shared__ double wsum[SEL_WARPS];
-  __shared__ unsigned long long wgt[SEL_WARPS], weq[SEL_WARPS];
   const int layer = l0 + blockIdx.y, nt = tg.n_t;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t nblk = gridDim.x * gridDim.y;
@@ -220,6 +227,8 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
   if (threadIdx.x < nt) {
     pre[threadIdx.x] = 0ull;
     kk[threadIdx.x] = tg.rank[threadIdx.x];
+    cgt[threadIdx.x] = 0ull;
+    ceq[threadIdx.x] = 0ull;
   }
   __syncthreads();
   auto value = [&](int64_t i) -> double { return resident ? vals[i] : __ldcg(src + i); };
@@ -242,9 +251,12 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
     }
     __syncthreads();
     const int ng = ngrp;
-    for (int i = threadIdx.x; i < ng * SEL_BINS; i += blockDim.x) h[i] = 0;
+    int S = SEL_SUBH / ng;                 // sub-histograms per group (a power of two)
+    S = 1 << (31 - __clz(S));
+    for (int i = threadIdx.x; i < ng * S * SEL_BINS; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const int shift = 64 - SEL_BITS * (pass + 1);
+    uint32_t* hw = h + (warp & (S - 1)) * SEL_BINS;   // this warp's copy (group g: + g S BINS)
     for (int64_t j = 0; j < cnt; j += SEL_THREADS) {   // bound uniform over the block
       const int64_t i = j + threadIdx.x;
       const bool ok = i < cnt;
@@ -254,13 +266,17 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
         const bool m = ok && (pass == 0 || (key >> (shift + SEL_BITS)) == (gpre[g] >> (shift + SEL_BITS)));
         if (!__any_sync(0xffffffffu, m)) continue;
         const uint32_t peers = __match_any_sync(0xffffffffu, m ? d : 0xffffffffu);
-        if (m && lane == __ffs(peers) - 1) atomicAdd(&h[g * SEL_BINS + d], (uint32_t)__popc(peers));
+        if (m && lane == __ffs(peers) - 1) atomicAdd(&hw[g * S * SEL_BINS + d], (uint32_t)__popc(peers));
       }
     }
     __syncthreads();
     uint32_t* gh = sc.hist + ((int64_t)layer * SEL_PASSES + pass) * nt * SEL_BINS;
-    for (int i = threadIdx.x; i < ng * SEL_BINS; i += blockDim.x)
-      if (h[i]) atomicAdd(&gh[gldr[i / SEL_BINS] * SEL_BINS + (i % SEL_BINS)], h[i]);
+    for (int i = threadIdx.x; i < ng * SEL_BINS; i += blockDim.x) {
+      const int g = i / SEL_BINS, d = i % SEL_BINS;
+      uint32_t c = 0;
+      for (int k = 0; k < S; ++k) c += h[(g * S + k) * SEL_BINS + d];
+      if (c) atomicAdd(&gh[gldr[g] * SEL_BINS + d], c);
+    }
     if (!grid_barrier(bar, (uint32_t)(pass + 1) * nblk, limit_ns, sc.err, sc.ext_err, skip_arrival, &bar_ok)) return;
     for (int t = warp; t < nt; t += SEL_WARPS) {
       const int64_t k = kk[t];
@@ -290,60 +306,33 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
         const uint32_t bin = SEL_BINS - 1 - (lane * (SEL_BINS / 32) + u);
         kk[t] = k - before;
         pre[t] |= (uint64_t)bin << shift;
+        cgt[t] += (unsigned long long)before;           // keys above, with this prefix
+        if (pass == SEL_PASSES - 1) ceq[t] = c[u];      // keys equal to the selected key
       }
     }
     __syncthreads();
   }
 
-  // ---- tail pass: one target (t == nt: the row sum) at a time ----
-  for (int t = 0; t <= nt; ++t) {
+  // ---- tail pass: sums above the selected key (TVaR targets) and the row sum ----
+  for (int t = tg.n_rp; t <= nt; ++t) {
     if (t == nt && !want_mean) break;
     const uint64_t thr = t < nt ? pre[t] : 0ull;
-    const bool tvar = t < nt && t >= tg.n_rp;
     double a = 0.0;
-    uint32_t g = 0, e = 0;
     for (int64_t i = threadIdx.x; i < cnt; i += SEL_THREADS) {
       const double y = value(i);
-      if (t == nt) {
-        a = __dadd_rn(a, y);
-        continue;
-      }
-      const uint64_t k = key_of(y);
-      if (k > thr) {
-        ++g;
-        if (tvar) a = __dadd_rn(a, y);
-      } else if (k == thr) {
-        ++e;
-      }
+      if (t == nt || key_of(y) > thr) a = __dadd_rn(a, y);
     }
-    unsigned long long gg = g, ee = e;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
-      gg += __shfl_down_sync(0xffffffffu, gg, o);
-      ee += __shfl_down_sync(0xffffffffu, ee, o);
-    }
-    if (lane == 0) {
-      wsum[warp] = a;
-      wgt[warp] = gg;
-      weq[warp] = ee;
-    }
+    for (int o = 16; o; o >>= 1) a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
+    if (lane == 0) wsum[warp] = a;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      unsigned long long sg = 0, se = 0;
-      for (int w = 0; w < SEL_WARPS; ++w) {
-        s = __dadd_rn(s, wsum[w]);
-        sg += wgt[w];
-        se += weq[w];
-      }
-      if (t < nt) {
-        const int64_t at = ((int64_t)layer * nt + t) * gridDim.x + blockIdx.x;
-        sc.psum[at] = s;
-        sc.pgt[at] = sg;
-        sc.peq[at] = se;
-      } else {
-        sc.pmean[(int64_t)layer * gridDim.x + blockIdx.x] = s;
+    if (warp == 0) {   // the warps' sums, combined by a fixed tree
+      double s = wsum[lane];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
+      if (lane == 0) {
+        if (t < nt) sc.psum[((int64_t)layer * nt + t) * gridDim.x + blockIdx.x] = s;
+        else sc.pmean[(int64_t)layer * gridDim.x + blockIdx.x] = s;
       }
     }
     __syncthreads();
@@ -356,23 +345,14 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
   for (int t = warp; t <= nt; t += SEL_WARPS) {
     if (t == nt && !want_mean) continue;
     double a = 0.0;
-    unsigned long long g = 0, e = 0;
-    if (t < nt) {
-      const int64_t base = ((int64_t)layer * nt + t) * B;
-      for (unsigned b = lane; b < B; b += 32) {
-        a = __dadd_rn(a, __ldcg(&sc.psum[base + b]));
-        g += __ldcg(&sc.pgt[base + b]);
-        e += __ldcg(&sc.peq[base + b]);
-      }
-    } else {
+    if (t == nt) {
       for (unsigned b = lane; b < B; b += 32) a = __dadd_rn(a, __ldcg(&sc.pmean[(int64_t)layer * B + b]));
+    } else if (t >= tg.n_rp) {
+      const int64_t base = ((int64_t)layer * nt + t) * B;
+      for (unsigned b = lane; b < B; b += 32) a = __dadd_rn(a, __ldcg(&sc.psum[base + b]));
     }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
-      g += __shfl_down_sync(0xffffffffu, g, o);
-      e += __shfl_down_sync(0xffffffffu, e, o);
-    }
+    for (int o = 16; o; o >>= 1) a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
     if (lane != 0) continue;
     if (t == nt) {
       sc.mean[layer] = a / (double)n;
@@ -382,11 +362,11 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
     double r = v;
     if (t >= tg.n_rp) {
       const int64_t m = tg.rank[t];
-      r = (a + (double)(m - (int64_t)g) * v) / (double)m;
+      r = (a + (double)(m - (int64_t)cgt[t]) * v) / (double)m;
     }
     sc.out[layer * nt + t] = r;
-    sc.gt[layer * nt + t] = g;
-    sc.eq[layer * nt + t] = e;
+    sc.gt[layer * nt + t] = cgt[t];
+    sc.eq[layer * nt + t] = ceq[t];
     sc.state[layer * nt + t] = SelState{pre[t], kk[t]};
   }
 }
