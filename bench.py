@@ -220,25 +220,39 @@ def kernel_source_sha():
 # ------------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # ------------------------------------------------------------------------------------------
-def oracle_sample_rate(pf, yet_fn, target_s: float):
-    """Time the oracle (all host cores) on the first K trials, K sized for ~target_s."""
+def oracle_sample_rate(pf, yet_fn, target_s: float, max_trials: int = N_TRIALS, single_core=True):
+    """Time the oracle on the first K trials (K sized for ~target_s on all host cores, at most the
+    whole workload), and on one core over a sample 1/16 of that size."""
     import oracle
-    import synth
     calib = 2000
     y = yet_fn(calib)
     oracle.ylt(pf, y)  # warm (builds the direct-access tables once per call; part of the work)
     t0 = time.perf_counter()
     oracle.ylt(pf, y)
     dt = time.perf_counter() - t0
-    k = int(max(calib, min(200_000, calib * target_s / max(dt, 1e-3))))
+    k = int(max(calib, min(max_trials, calib * target_s / max(dt, 1e-3))))
     y = yet_fn(k)
     t0 = time.perf_counter()
     oracle.ylt(pf, y)
     dt = time.perf_counter() - t0
     lookups = k * EVENTS_PER_TRIAL * N_ELTS
-    return {"value": lookups / dt, "unit": "lookups/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"first {k} trials of the paper-scale YET ({k * EVENTS_PER_TRIAL} occurrences x "
-                      f"{N_ELTS} ELTs), FP64 C oracle, {dt:.1f} s", "trials": k}
+    out = {"value": lookups / dt, "unit": "lookups/s", "cores": oracle.threads(), "kind": "oracle",
+           "sample": f"first {k} trials of the paper-scale YET ({k * EVENTS_PER_TRIAL} occurrences x "
+                     f"{N_ELTS} ELTs), FP64 C oracle, {dt:.1f} s", "trials": k}
+    if single_core:
+        k1 = max(calib, k // 16)
+        y1 = yet_fn(k1)
+        cores = oracle.threads()
+        oracle.set_threads(1)
+        try:
+            t0 = time.perf_counter()
+            oracle.ylt(pf, y1)
+            dt1 = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(cores)
+        out["single_core"] = {"value": k1 * EVENTS_PER_TRIAL * N_ELTS / dt1, "cores": 1,
+                              "sample": f"first {k1} trials, {dt1:.1f} s"}
+    return out
 
 
 def run_reference(args, rank, ws):
@@ -248,7 +262,8 @@ def run_reference(args, rank, ws):
     import oracle
     import synth
     pf = synth.paper_scale_portfolio(0)
-    base = oracle_sample_rate(pf, lambda k: synth.paper_scale_yet(0, n_trials=k), 2.0)
+    base = oracle_sample_rate(pf, lambda k: synth.paper_scale_yet(0, n_trials=k), 2.0,
+                              single_core=False)
     k = base["trials"]
     yet = synth.paper_scale_yet(0, n_trials=k)
     for _ in range(args.warmup):
@@ -391,7 +406,9 @@ def run_ours(args, rank, ws, local):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample_rate(pf, lambda k: synth.paper_scale_yet(rank, n_trials=k), args.cpu_seconds)
+        cpu = oracle_sample_rate(
+            pf, lambda k: synth.YET(yet.offsets[:k + 1], yet.event_ids[:int(yet.offsets[k])]),
+            args.cpu_seconds, max_trials=n_trials)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "lookups/s", "n_gpus": ws,
