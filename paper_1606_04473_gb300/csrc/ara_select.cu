@@ -60,6 +60,10 @@ struct SelScratch {
   double* pmean;
   double* mean;
   uint32_t* ext_err;     // optional (nullptr): also gets DERR_TIMEOUT when a barrier times out
+  // optional caller outputs, written directly (nullptr: results stay in out / mean only)
+  double* user_pml;      // [n_layers][n_rp]
+  double* user_tvar;     // [n_layers][n_t - n_rp]
+  double* user_mean;     // [n_layers]
 };
 
 template <typename F>
@@ -105,6 +109,7 @@ static SelScratch carve(void* base, int32_t n_layers, int32_t n_t, int32_t block
   s.pmean = (double*)(p + off[10]);
   s.mean = (double*)(p + off[11]);
   s.ext_err = nullptr;
+  s.user_pml = s.user_tvar = s.user_mean = nullptr;
   return s;
 }
 
@@ -356,6 +361,7 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
     if (lane != 0) continue;
     if (t == nt) {
       sc.mean[layer] = a / (double)n;
+      if (sc.user_mean) sc.user_mean[layer] = a / (double)n;
       continue;
     }
     const double v = value_of(pre[t]);
@@ -365,6 +371,11 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
       r = (a + (double)(m - (int64_t)cgt[t]) * v) / (double)m;
     }
     sc.out[layer * nt + t] = r;
+    if (t < tg.n_rp) {
+      if (sc.user_pml) sc.user_pml[(int64_t)layer * tg.n_rp + t] = r;
+    } else if (sc.user_tvar) {
+      sc.user_tvar[(int64_t)layer * (nt - tg.n_rp) + (t - tg.n_rp)] = r;
+    }
     sc.gt[layer * nt + t] = cgt[t];
     sc.eq[layer * nt + t] = ceq[t];
     sc.state[layer * nt + t] = SelState{pre[t], kk[t]};
@@ -443,9 +454,14 @@ int32_t select_blocks(int64_t n, int n_sms, int32_t n_layers) {
 // Layers are split into cooperative launches whose blocks are all co-resident.
 ara_status launch_select(const double* d_ylt, int64_t n, int32_t n_layers, const SelTargets& tg,
                          void* scratch, size_t scratch_bytes, int32_t blocks, int want_mean,
-                         cudaStream_t s, SelScratch* out, uint32_t* ext_err = nullptr) {
+                         cudaStream_t s, SelScratch* out, uint32_t* ext_err = nullptr,
+                         double* user_pml = nullptr, double* user_tvar = nullptr,
+                         double* user_mean = nullptr) {
   SelScratch sc = carve(scratch, n_layers, tg.n_t, blocks);
   sc.ext_err = ext_err;
+  sc.user_pml = user_pml;
+  sc.user_tvar = user_tvar;
+  sc.user_mean = user_mean;
   ARA_TRY(cudaMemsetAsync(scratch, 0, scratch_bytes, s));
   const int resident = select_resident_blocks();
   if (resident < blocks) return ARA_ECUDA;
@@ -575,22 +591,10 @@ extern "C" ara_status ara_risk_metrics_async(const double* d_ylt, int64_t n_tria
   ara_status r = ARA_OK;
   SelScratch sc;
   if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s) != cudaSuccess) r = ARA_ECUDA;
-  if (r == ARA_OK)
+  if (r == ARA_OK)   // the kernel writes the results straight into d_pml / d_tvar / d_mean
     r = launch_select(d_ylt, n_trials, n_layers, tg, scratch, bytes, blocks, d_mean != nullptr, s,
-                      &sc, d_status);
-  if (r == ARA_OK) {
-    const size_t row = sizeof(double) * (size_t)tg.n_t;
-    cudaError_t e = cudaSuccess;
-    if (n_rp > 0)
-      e = cudaMemcpy2DAsync(d_pml, sizeof(double) * n_rp, sc.out, row, sizeof(double) * n_rp,
-                            (size_t)n_layers, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess && n_tvar > 0)
-      e = cudaMemcpy2DAsync(d_tvar, sizeof(double) * n_tvar, sc.out + n_rp, row,
-                            sizeof(double) * n_tvar, (size_t)n_layers, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess && d_mean)
-      e = cudaMemcpyAsync(d_mean, sc.mean, sizeof(double) * n_layers, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) r = ARA_ECUDA;
-  }
+                      &sc, d_status, n_rp > 0 ? d_pml : nullptr, n_tvar > 0 ? d_tvar : nullptr,
+                      d_mean);
   cudaFreeAsync(scratch, s);
   return r;
 }

@@ -127,3 +127,12 @@ def test_grid_barrier_timeout_is_reported():
         ara.debug_set(ara.ARA_DBG_SKIP_BARRIER_ARRIVAL, 0)
         ara.debug_set(ara.ARA_DBG_WAIT_LIMIT_NS, 1_000_000_000)
     check(y.cpu().numpy(), rps=[100.0], levels=[0.99])
+
+
+def test_large_tie_group_at_the_targets():
+    """A tie group of 200k values (two thirds of the row) where the PML ranks and a TVaR
+    boundary fall: the selected key is the tied value and the TVaR mean shares it."""
+    rng = np.random.default_rng(9)
+    y = rng.lognormal(12, 1, 300_000)
+    y[:200_000] = 123456.0
+    check(y, rps=[2.0, 3.0, 100.0], levels=[0.5, 0.99])
