@@ -85,28 +85,15 @@ struct AdjHistParams {
   uint32_t* err;
 };
 
+// Coarse regime bitmap word cw, interleaved: bit i is the OR of bit i of the exact words
+// [cw << shift, (cw + 1) << shift), so event e is tested at bit (e mod 32) of word
+// e >> (5 + shift).
 __device__ __forceinline__ uint32_t adj_coarsen(const uint32_t* __restrict__ src, int64_t cw,
                                                 int shift, int64_t n_words) {
-  if (shift == 0) return cw < n_words ? src[cw] : 0u;
+  const int64_t w0 = cw << shift;
+  const int64_t w1 = min(w0 + ((int64_t)1 << shift), n_words);
   uint32_t out = 0;
-  const int G = 1 << shift;
-  if (shift <= 4) {
-    const int per = 32 >> shift;
-    for (int w = 0; w < G; ++w) {
-      const int64_t ew = (cw << shift) + w;
-      const uint32_t x = ew < n_words ? src[ew] : 0u;
-      for (int b = 0; b < per; ++b)
-        out |= (((x >> (b * G)) & ((1u << G) - 1u)) ? 1u : 0u) << (w * per + b);
-    }
-  } else {
-    const int64_t wpb = (int64_t)1 << (shift - 5);
-    for (int b = 0; b < 32; ++b) {
-      const int64_t w0 = (cw * 32 + b) * wpb;
-      uint32_t any = 0;
-      for (int64_t w = w0; w < w0 + wpb && w < n_words; ++w) any |= src[w];
-      out |= (any ? 1u : 0u) << b;
-    }
-  }
+  for (int64_t w = w0; w < w1; ++w) out |= src[w];
   return out;
 }
 
@@ -120,6 +107,7 @@ __global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t n_groups = (p.n_trials + 31) >> 5;
   const uint64_t thr = *p.thr_key;
+  const int shift5 = p.shift + 5;
   bool bad_id = false, bad_off = false;
   for (int64_t g = warp; g < n_groups; g += nwarps) {
     const int64_t t0 = g << 5;
@@ -140,22 +128,21 @@ __global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
       int64_t beg = __shfl_sync(FULLM, my_off, k);
       int64_t end = (k + 1 < 32) ? __shfl_sync(FULLM, my_off, k + 1) : last_off;
       if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; continue; }
-      // eight independent streaming loads per lane in flight, then the filtered atomics
-      for (int64_t i0 = beg; i0 < end; i0 += 256) {
-        int ev[8];
+      // sixteen independent streaming loads per lane in flight, then the filtered atomics
+      for (int64_t i0 = beg; i0 < end; i0 += 512) {
+        int ev[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 16; ++u) {
           const int64_t i = i0 + 32 * u + lane;
           ev[u] = i < end ? __ldcs(p.ids + i) : -1;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 16; ++u) {
           const int64_t i = i0 + 32 * u + lane;
           const int e = ev[u];
           if (i >= end) continue;
           if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; continue; }
-          const uint32_t b = (uint32_t)e >> p.shift;
-          if (!((bm[b >> 5] >> (b & 31)) & 1u)) continue;
+          if (!((bm[(uint32_t)e >> shift5] >> (e & 31)) & 1u)) continue;
           atomicAdd(p.h_mean + e, 1u);
           if (c == 2) atomicAdd(p.h_gt + e, 1u);
           else if (c == 3) atomicAdd(p.h_eq + e, 1u);
@@ -398,7 +385,7 @@ extern "C" ara_status ara_adjoint(ara_portfolio* pf_, int64_t n_trials, const in
 
   // shared-memory bitmap for the histogram pass
   int shift = 0;
-  auto cw = [&](int sh) { return (((C + ((int64_t)1 << sh) - 1) >> sh) + 31) / 32; };
+  auto cw = [&](int sh) { return ((C + 31) / 32 + ((int64_t)1 << sh) - 1) >> sh; };   // interleaved words
   const int64_t bm_budget = std::min<int64_t>(pf->max_smem_block, 200 * 1024);
   while (cw(shift) * 4 > bm_budget) ++shift;
   const int smem = (int)(cw(shift) * 4);
