@@ -549,7 +549,7 @@ def measure_batched(rank: int, reps: int = 5):
     return out
 
 
-def measure_serving(rank: int, n_requests: int = 200, workers: int = 4):
+def measure_serving(rank: int, n_requests: int = 200, workers: int = 2):
     """Serving: a seeded Poisson stream (200 requests/s, 32 tenants) of risk queries over a
     resident pool of 500 ELTs and a resident YET of 1e6 trials x Poisson(1000) events (1-32
     layers of 5-20 ELTs each, slices of 1e4-1e6 trials, 20 % with the adjoint), served by the
@@ -604,9 +604,12 @@ def measure_serving(rank: int, n_requests: int = 200, workers: int = 4):
         return res, makespan, lat, stats
 
     res_s, mk_s, lat_s, st_s = serve(workers, paced=True)
+    res_2, mk_2, lat_2, st_2 = serve(4, paced=True)
     res_1, mk_1, lat_1, st_1 = serve(1, paced=True)
     same = all(np.array_equal(a["pml"], b["pml"]) and np.array_equal(a["tvar"], b["tvar"]) and
-               np.array_equal(a["mean"], b["mean"]) for a, b in zip(res_s, res_1))
+               np.array_equal(a["mean"], b["mean"]) and np.array_equal(c["pml"], b["pml"]) and
+               np.array_equal(c["tvar"], b["tvar"]) and np.array_equal(c["mean"], b["mean"])
+               for a, c, b in zip(res_s, res_2, res_1))
     tot = float(sum(lookups))
     out = {"workload": f"{n_requests} requests, Poisson 200/s, 32 tenants; 1-32 layers x 5-20 ELTs of a "
                        "500-ELT pool; slices of 1e4-1e6 trials of a 1e6 x Poisson(1000) YET; 20% adjoint",
@@ -614,6 +617,9 @@ def measure_serving(rank: int, n_requests: int = 200, workers: int = 4):
                       "p99_ms": round(float(np.percentile(lat_s, 99)), 2),
                       "makespan_s": round(mk_s, 3), "lookups_per_s": tot / mk_s,
                       "peak_running": st_s["peak_running"]},
+           "served_4_workers": {"p50_ms": round(float(np.percentile(lat_2, 50)), 2),
+                                "p99_ms": round(float(np.percentile(lat_2, 99)), 2),
+                                "makespan_s": round(mk_2, 3), "lookups_per_s": tot / mk_2},
            "one_at_a_time": {"p50_ms": round(float(np.percentile(lat_1, 50)), 2),
                              "p99_ms": round(float(np.percentile(lat_1, 99)), 2),
                              "makespan_s": round(mk_1, 3), "lookups_per_s": tot / mk_1},
