@@ -615,12 +615,40 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
 #pragma unroll
       for (int i = 0; i < NV; ++i) LaneOps<Acc>::add(w.acc, v[i]);
     } else {
-      int32_t pos[NV];
+      // A trial ends inside the chunk, at relative slot r (0 < r < n).  Lane l's values sit in
+      // runs of four consecutive slots 128u + 4l + j, so the end splits run u at
+      // js = clamp(r - 128u - 4l, 0, 4): values j < js finish the current trial, the others
+      // start the next one.  More than one end in the chunk takes the general walk.
+      int32_t done = rb;
+      if (w.k < w.nk) {
+        const int32_t r = w.end - rb;
+        int32_t js[NQ];
 #pragma unroll
-      for (int u = 0; u < NQ; ++u)
+        for (int u = 0; u < NQ; ++u) js[u] = min(max(r - 128 * u - 4 * lane, 0), 4);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) pos[4 * u + i] = rb + 128 * u + 4 * lane + i;
-      walk_window<Acc, NV>(w, p, lc, t_lo, base_abs, lane, rb, rb + n, pos, v);
+        for (int u = 0; u < NQ; ++u)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j < js[u]) LaneOps<Acc>::add(w.acc, v[4 * u + j]);
+        walk_finish(w, p, lc, t_lo, base_abs, lane);
+        done = rb + r;
+        if (w.k < w.nk && w.end >= rb + n) {
+#pragma unroll
+          for (int u = 0; u < NQ; ++u)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (j >= js[u]) LaneOps<Acc>::add(w.acc, v[4 * u + j]);
+          done = rb + n;
+        }
+      }
+      if (done < rb + n) {
+        int32_t pos[NV];
+#pragma unroll
+        for (int u = 0; u < NQ; ++u)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) pos[4 * u + i] = rb + 128 * u + 4 * lane + i;
+        walk_window<Acc, NV>(w, p, lc, t_lo, base_abs, lane, done, rb + n, pos, v);
+      }
     }
     if (++s == BK_STAGES) {
       s = 0;
