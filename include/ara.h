@@ -147,7 +147,10 @@ ARA_API ara_status ara_create_layer_set(ara_portfolio* pool, int32_t n_layers,
  * YLT of n_trials trials for the selected layers.  Asynchronous on `stream`.
  *   d_trial_offsets  device [n_trials + 1] int64: trial t owns events
  *                    d_trial_offsets[t] .. d_trial_offsets[t+1]-1 of d_event_ids
- *                    (0 <= offsets non-decreasing <= n_events, else ARA_EDATA later)
+ *                    (0 <= offsets non-decreasing <= n_events, else ARA_EDATA later).
+ *                    The default stream kernel splits the trials into one contiguous range
+ *                    per warp (n_trials / (SMs x 28) trials each); a range of 2^31 - 512 or
+ *                    more events is reported as ARA_EDATA (ARA_RUN_LDG has no such limit)
  *   n_events         number of elements of d_event_ids
  *   d_event_ids      device [n_events] int32, 4-byte aligned: each trial's event IDs in time
  *                    order (Eq. 1)

@@ -109,9 +109,15 @@ template <> struct AccOps<OepMax> {
 //
 // For exact sums the partial is two 64-bit sums of the low and high 32-bit halves of the table
 // values, each added with one wide multiply-add (the FMA pipe; no carry chain per value).  A
-// lane holds at most n_t / 32 + 16 values of a trial (n_t < 2^31), each half below 2^32, so
-// neither sum nor their warp totals can overflow; the 128-bit sum lo + hi * 2^32 is formed
-// once per trial.
+// chunk that lies inside one trial first sums its K values in 64 bits (K <= 512 values of
+// < 2^55 cannot overflow) and adds that sum once.
+//
+// At the trial's end the lane partial P = lo + hi * 2^32 is split into three 27-bit limbs;
+// each limb is summed over the warp by one redux.sync (32 limbs of < 2^27 sum below 2^32) and
+// the three sums are recombined into 128 bits.  This needs P < 2^81.  The stream kernel takes a
+// warp's event range only below 2^31 - 512 events, so a lane holds fewer than 2^26 values of any
+// trial (at most 8 per 256-event chunk, 16 per 512-event chunk, plus one head and one tail
+// value), each below 2^55.
 template <typename Acc> struct LaneOps;
 template <> struct LaneOps<U128> {
   struct T {
@@ -122,14 +128,24 @@ template <> struct LaneOps<U128> {
     asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(a.lo) : "r"((uint32_t)v));
     asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(a.hi) : "r"((uint32_t)(v >> 32)));
   }
-  static __device__ __forceinline__ U128 reduce(T a) {
+  template <int K>
+  static __device__ __forceinline__ void add_all(T& a, const uint64_t (&v)[K]) {
+    static_assert(K <= 512, "a 64-bit sum holds at most 512 values below 2^55");
+    uint64_t s = 0;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      a.lo += __shfl_xor_sync(FULL, a.lo, o);
-      a.hi += __shfl_xor_sync(FULL, a.hi, o);
-    }
-    U128 r{a.lo, 0ull};
-    add_u128(r, a.hi << 32, a.hi >> 32);
+    for (int i = 0; i < K; ++i) s += v[i];
+    add(a, s);
+  }
+  static __device__ __forceinline__ U128 reduce(T a) {
+    const uint64_t p0 = a.lo + (a.hi << 32);                               // bits 0..63 of P
+    const uint32_t p1 = (uint32_t)(a.hi >> 32) + (p0 < a.lo ? 1u : 0u);    // bits 64..80
+    constexpr uint32_t M = (1u << 27) - 1u;
+    const uint32_t s0 = __reduce_add_sync(FULL, (uint32_t)p0 & M);
+    const uint32_t s1 = __reduce_add_sync(FULL, (uint32_t)(p0 >> 27) & M);
+    const uint32_t s2 = __reduce_add_sync(FULL, (uint32_t)(p0 >> 54) | (p1 << 10));
+    U128 r{(uint64_t)s0, 0ull};
+    add_u128(r, (uint64_t)s1 << 27, 0ull);
+    add_u128(r, (uint64_t)s2 << 54, (uint64_t)(s2 >> 10));
     return r;
   }
 };
@@ -137,12 +153,22 @@ template <> struct LaneOps<double> {
   using T = double;
   static __device__ __forceinline__ T zero() { return 0.0; }
   static __device__ __forceinline__ void add(T& a, uint64_t v) { AccOps<double>::add(a, v); }
+  template <int K>
+  static __device__ __forceinline__ void add_all(T& a, const uint64_t (&v)[K]) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) add(a, v[i]);
+  }
   static __device__ __forceinline__ double reduce(T a) { return AccOps<double>::warp_sum(a); }
 };
 template <> struct LaneOps<OepMax> {
   using T = OepMax;
   static __device__ __forceinline__ T zero() { return OepMax{0ull}; }
   static __device__ __forceinline__ void add(T& a, uint64_t v) { AccOps<OepMax>::add(a, v); }
+  template <int K>
+  static __device__ __forceinline__ void add_all(T& a, const uint64_t (&v)[K]) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) add(a, v[i]);
+  }
   static __device__ __forceinline__ OepMax reduce(T a) { return AccOps<OepMax>::warp_sum(a); }
 };
 

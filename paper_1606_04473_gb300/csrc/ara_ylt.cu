@@ -520,7 +520,11 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
 
   const int64_t E0 = __ldg(p.offsets + t_lo) - p.id_base;
   const int64_t E1 = __ldg(p.offsets + t_hi) - p.id_base;
-  if (!(0 <= E0 && E0 <= E1 && E1 <= p.n_events && E1 - E0 < ((int64_t)1 << 31))) {
+  // A warp's range stays below 2^31 - 512 events: relative positions fit in int32, and no lane
+  // holds 2^26 or more values of one trial, the bound the warp reduction of the split partials
+  // relies on.
+  constexpr int64_t kMaxWarpSpan = ((int64_t)1 << 31) - 512;
+  if (!(0 <= E0 && E0 <= E1 && E1 <= p.n_events && E1 - E0 < kMaxWarpSpan)) {
     if (lane == 0) atomicOr(p.err, DERR_OFFSETS);
     return;
   }
@@ -612,8 +616,7 @@ __global__ void __launch_bounds__(BK_WARPS * 32, 1) k_ylt_bulk(StreamParams p) {
     while (w.k < w.nk && w.end <= rb) walk_finish(w, p, lc, t_lo, base_abs, lane);
     if (w.k < w.nk && w.end >= rb + n) {
       // fast path: the whole chunk belongs to the current trial
-#pragma unroll
-      for (int i = 0; i < NV; ++i) LaneOps<Acc>::add(w.acc, v[i]);
+      LaneOps<Acc>::add_all(w.acc, v);
     } else {
       // A trial ends inside the chunk, at relative slot r (0 < r < n).  Lane l's values sit in
       // runs of four consecutive slots 128u + 4l + j, so the end splits run u at

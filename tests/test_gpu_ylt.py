@@ -191,6 +191,33 @@ def test_identity_terms_give_raw_loss_sums():
         np.testing.assert_allclose(y[l], expect, rtol=1e-12, atol=0)
 
 
+def test_warp_reduction_of_large_partials_is_exact():
+    """Table values near the fixed point's maximum (every lane partial has all three 27-bit
+    limbs of the warp reduction in use) and trials of up to 3e5 events: the bulk stream's YLT
+    equals, bit for bit, the register-staged kernel's, which adds every value with carries and
+    reduces differently; both equal the correctly rounded sums of the losses."""
+    import math
+    catalogue = 4096
+    ids = [np.arange(catalogue, dtype=np.int32)] * 2
+    rng = np.random.default_rng(11)
+    losses = [(1e6 * (0.9 + 0.1 * rng.random(catalogue))).astype(np.float32).astype(np.float64)
+              for _ in range(2)]
+    pf = synth.Portfolio(catalogue, ids, losses, np.zeros(2), np.full(2, INF), [[0, 1]],
+                         np.zeros(1), np.full(1, INF), np.zeros(1), np.full(1, INF), losses_f32=True)
+    counts = np.array([300_000, 0, 1, 250_000, 31, 32, 33, 4096, 123_457, 7], dtype=np.int64)
+    yet = synth.make_yet(12, counts, catalogue, with_timestamps=False)
+    g = ara.Portfolio.from_tables(pf)
+    off, ev = dev(yet)
+    y_bulk = g.run_ylt(off, ev)
+    y_ldg = g.run_ylt(off, ev, flags=ara.ARA_RUN_LDG)
+    g.check()
+    assert torch.equal(y_bulk, y_ldg)
+    dense = losses[0] + losses[1]
+    expect = [math.fsum(dense[yet.event_ids[yet.offsets[t]:yet.offsets[t + 1]]].tolist())
+              for t in range(yet.n_trials)]
+    np.testing.assert_allclose(y_bulk.cpu().numpy()[0], expect, rtol=1e-14, atol=0)
+
+
 def test_edge_cases_empty_inputs(tiny):
     pf, yet, ref, agg = tiny
     g = ara.Portfolio.from_tables(pf)
