@@ -1,10 +1,11 @@
 // PML and TVaR (Section IV-A names both as metrics derived from the YLT) as empirical order
 // statistics: PML(RP) is the ceil(N/RP)-th largest year loss, TVaR(p) the mean of the
 // ceil(N(1-p)) largest.  Both come from an exact radix select on order-preserving 64-bit keys
-// of the FP64 year losses (8 passes of 8 bits), followed by one pass summing the tail above
-// the selected key.  One cooperative launch runs every pass: each block adds its shared-memory
-// digit histogram into the pass's global histogram, all blocks meet at a grid barrier (a
-// bounded wait), and every block then reads the histogram and advances the selection itself.
+// of the FP64 year losses (up to 8 passes of 8 bits), followed by one pass summing the tail
+// above the selected key.  One cooperative launch runs every pass: each block adds its
+// shared-memory digit histogram into the pass's global histogram, the layer's blocks meet at a
+// grid barrier (a bounded wait), and every block then reads the histogram and advances the
+// selection itself.
 // Results are bit-exact copies of YLT entries (PML) and deterministic FP64 sums (TVaR, mean):
 // fixed per-thread order, fixed warp and block trees, block partials combined in a fixed order.
 
@@ -29,14 +30,13 @@ struct SelTargets {
 };
 
 struct SelState {
-  uint64_t prefix;             // key bits fixed so far (after the last pass: the selected key)
+  uint64_t prefix;             // written at the end: the selected key
   int64_t k;                   // rank still to find among keys matching the prefix
 };
 
 // Scratch layout (one allocation, zero-filled before the launch):
 //   hist   [n_layers][SEL_PASSES][n_t][SEL_BINS]  uint32
-//   bar    [n_layers]                             uint32 grid-barrier counter of the launch
-//                                                 whose first layer this is
+//   bar    [n_layers]                             uint32 grid-barrier counter of the layer
 //   err    [1]                                    uint32: a grid barrier timed out
 //   state  [n_layers][n_t]                        SelState
 //   psum   [n_layers][n_t][blocks]                double   block partial: sum of y > key
@@ -185,7 +185,9 @@ constexpr int SEL_SUBH = 32;
 // block picks each target's digit from the global histogram (one warp per target, bins
 // scanned from the top) and keeps the selection state in shared memory.  The counts of the
 // bins above the chosen one add up, over the passes, to #{key > selected key}; the chosen
-// bin's count in the last pass is #{key == selected key}.
+// bin's count in the last pass is #{key == selected key}.  The passes stop early once every
+// target's chosen bin holds a single key (distinct values near the targets, the usual case);
+// one scan of the slice then finds those keys.
 //
 // Tail (TVaR targets and the row sum only): the sum of the values above the selected key.
 // Every thread sums its own values in index order, warps and blocks combine with fixed trees,
@@ -207,8 +209,9 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
   __shared__ double wsum[SEL_WARPS];
   const int layer = l0 + blockIdx.y, nt = tg.n_t;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t nblk = gridDim.x * gridDim.y;
-  uint32_t* bar = sc.bar + l0;
+  // The blocks of a layer depend only on one another: each layer has its own barrier counter.
+  const uint32_t nblk = gridDim.x;
+  uint32_t* bar = sc.bar + layer;
   const int64_t i0 = (int64_t)blockIdx.x * n / gridDim.x;
   const int64_t cnt = ((int64_t)blockIdx.x + 1) * n / gridDim.x - i0;
   const double* src = ylt + (int64_t)layer * n + i0;
@@ -239,6 +242,7 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
   auto value = [&](int64_t i) -> double { return resident ? vals[i] : __ldcg(src + i); };
 
   const int passes = nt > 0 ? SEL_PASSES : 0;
+  int done = passes;            // passes run
   for (int pass = 0; pass < passes; ++pass) {
     if (threadIdx.x == 0) {
       int ng = 0;
@@ -312,10 +316,32 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
         kk[t] = k - before;
         pre[t] |= (uint64_t)bin << shift;
         cgt[t] += (unsigned long long)before;           // keys above, with this prefix
-        if (pass == SEL_PASSES - 1) ceq[t] = c[u];      // keys equal to the selected key
+        ceq[t] = c[u];                                  // keys with the new prefix
       }
     }
     __syncthreads();
+    // When every target's prefix matches exactly one key, that key is the selected one and
+    // the remaining passes would change no count: stop.  Every block of the layer read the
+    // same histogram, so all of them stop after the same pass.
+    bool unique = true;
+    for (int t = 0; t < nt; ++t) unique = unique && ceq[t] == 1ull;
+    if (unique) {
+      done = pass + 1;
+      break;
+    }
+  }
+  // Key bits fixed by the passes run: [sh, 64).  Keys above the selected key are the keys whose
+  // fixed bits are above its prefix (after a full selection sh = 0, the plain comparison).
+  const int sh = done > 0 ? 64 - SEL_BITS * done : 0;
+  auto above = [&](uint64_t key, uint64_t prefix) -> bool {
+    return sh == 0 ? key > prefix : (key >> sh) > (prefix >> sh);
+  };
+  if (sh > 0) {   // stopped early: the one key under each target's prefix is its selected key
+    for (int64_t i = threadIdx.x; i < cnt; i += SEL_THREADS) {
+      const uint64_t key = key_of(value(i));
+      for (int t = 0; t < nt; ++t)
+        if ((key >> sh) == (pre[t] >> sh)) sc.state[(int64_t)layer * nt + t].prefix = key;
+    }
   }
 
   // ---- tail pass: sums above the selected key (TVaR targets) and the row sum ----
@@ -325,7 +351,7 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
     double a = 0.0;
     for (int64_t i = threadIdx.x; i < cnt; i += SEL_THREADS) {
       const double y = value(i);
-      if (t == nt || key_of(y) > thr) a = __dadd_rn(a, y);
+      if (t == nt || above(key_of(y), thr)) a = __dadd_rn(a, y);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
@@ -342,7 +368,7 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
     }
     __syncthreads();
   }
-  if (!grid_barrier(bar, (uint32_t)(passes + 1) * nblk, limit_ns, sc.err, sc.ext_err, skip_arrival, &bar_ok)) return;
+  if (!grid_barrier(bar, (uint32_t)(done + 1) * nblk, limit_ns, sc.err, sc.ext_err, skip_arrival, &bar_ok)) return;
   if (blockIdx.x != 0) return;
   // Block 0 of the layer: one warp per target (and one for the mean) combines the block
   // partials: lane l adds blocks l, l + 32, ... in order, then a fixed shuffle tree.
@@ -364,7 +390,8 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
       if (sc.user_mean) sc.user_mean[layer] = a / (double)n;
       continue;
     }
-    const double v = value_of(pre[t]);
+    const uint64_t key = sh > 0 ? __ldcg(&sc.state[(int64_t)layer * nt + t].prefix) : pre[t];
+    const double v = value_of(key);
     double r = v;
     if (t >= tg.n_rp) {
       const int64_t m = tg.rank[t];
@@ -378,7 +405,7 @@ k_select(const double* __restrict__ ylt, int64_t n, int32_t l0, SelTargets tg, S
     }
     sc.gt[layer * nt + t] = cgt[t];
     sc.eq[layer * nt + t] = ceq[t];
-    sc.state[layer * nt + t] = SelState{pre[t], kk[t]};
+    sc.state[layer * nt + t] = SelState{key, kk[t]};
   }
 }
 

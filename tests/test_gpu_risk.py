@@ -136,3 +136,16 @@ def test_large_tie_group_at_the_targets():
     y = rng.lognormal(12, 1, 300_000)
     y[:200_000] = 123456.0
     check(y, rps=[2.0, 3.0, 100.0], levels=[0.5, 0.99])
+
+
+def test_layers_stopping_after_different_passes():
+    """In one launch, layers whose targets fall on distinct values (the selection stops once
+    each target's bin holds one key) next to layers with a tie group at the targets (all 8
+    passes) and a layer of one repeated value: each layer's result is exact."""
+    rng = np.random.default_rng(21)
+    n = 50_000
+    rows = [rng.lognormal(14, 2, n), rng.lognormal(14, 2, n), rng.lognormal(14, 2, n),
+            np.full(n, 7.25)]
+    rows[1][: n // 2] = 4.5e6                     # tie group holding every target
+    rows[2][::2] = np.nextafter(rows[2][1::2], 0)  # near-equal pairs: unique only in the last bits
+    check(np.stack(rows), rps=[1.0, 2.0, 100.0, 250.0, float(n)], levels=[0.0, 0.5, 0.99])
