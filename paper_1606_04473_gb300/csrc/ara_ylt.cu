@@ -376,7 +376,8 @@ __global__ void k_coarsen(const uint32_t* __restrict__ exact, int64_t n_exact, i
 // byte address floor(e * 2^(32 - 5 - shift) / 2^32) * 4 + base is formed with a high multiply
 // and a multiply-add whose factors are run-time parameters, which keeps it on the FMA pipe
 // (the integer ALU pipe is this kernel's busiest).  The gather is predicated, with its 64-bit
-// address formed by one wide multiply-add.
+// address formed by one wide multiply-add, and cached in L2 only (.cg): random table entries are
+// almost never reused from L1.
 struct BitmapAddr {
   uint32_t base;   // shared-memory address of word 0
   uint32_t mul;    // 2^(32 - 5 - shift)
@@ -397,7 +398,7 @@ __device__ __forceinline__ uint64_t bulk_value(int e, uint32_t cat1, const Bitma
   }
   uint64_t v = 0;
   asm("{\n\t.reg .pred p;\n\t.reg .u64 a;\n\tsetp.ne.u32 p, %2, 0;\n\t"
-      "mad.wide.u32 a, %3, 8, %1;\n\t@p ld.global.nc.u64 %0, [a];\n\t}"
+      "mad.wide.u32 a, %3, 8, %1;\n\t@p ld.global.cg.u64 %0, [a];\n\t}"
       : "+l"(v) : "l"(q), "r"(hit), "r"(ce));
   return v;
 }
