@@ -64,8 +64,8 @@ __device__ __forceinline__ void block_add(unsigned long long (&v)[K], unsigned l
 
 // ------------------------------------------------------------------------------------------
 // Histogram of the events of interior trials, restricted to events whose occurrence clamp is
-// not in its zero regime (hit bitmap in shared memory).  One warp per trial of a 32-trial
-// group; trials outside the aggregate interior are skipped without reading their events.
+// not in its zero regime (hit bitmap in shared memory).  One warp per trial; trials outside the
+// aggregate interior are skipped without reading their events.
 // ------------------------------------------------------------------------------------------
 struct AdjHistParams {
   int64_t n_trials;
@@ -105,48 +105,36 @@ __global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t n_groups = (p.n_trials + 31) >> 5;
   const uint64_t thr = *p.thr_key;
   const int shift5 = p.shift + 5;
   bool bad_id = false, bad_off = false;
-  for (int64_t g = warp; g < n_groups; g += nwarps) {
-    const int64_t t0 = g << 5;
-    const int nt = (int)min((int64_t)32, p.n_trials - t0);
-    int cls = 0;
-    if (lane < nt && p.regimes[t0 + lane] == 1) {
-      const uint64_t k = adj_key(p.ylt[t0 + lane]);
-      cls = k > thr ? 2 : (k == thr ? 3 : 1);
-    }
-    unsigned todo = __ballot_sync(FULLM, cls != 0);
-    if (!todo) continue;
-    const int64_t my_off = (lane <= nt) ? __ldg(p.offsets + t0 + lane) : 0;
-    const int64_t last_off = (nt == 32) ? __ldg(p.offsets + t0 + 32) : 0;
-    while (todo) {
-      const int k = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const int c = __shfl_sync(FULLM, cls, k);
-      int64_t beg = __shfl_sync(FULLM, my_off, k);
-      int64_t end = (k + 1 < 32) ? __shfl_sync(FULLM, my_off, k + 1) : last_off;
-      if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; continue; }
-      // sixteen independent streaming loads per lane in flight, then the filtered atomics
-      for (int64_t i0 = beg; i0 < end; i0 += 512) {
-        int ev[16];
+  // Trials are dealt one at a time, round-robin over every warp of the grid, so each warp gets
+  // n_trials / warps of them (a 32-trial unit left most warps idle or doubly loaded).  The
+  // trial's class and range are read by the whole warp (one broadcast load each).
+  for (int64_t t = warp; t < p.n_trials; t += nwarps) {
+    if (p.regimes[t] != 1) continue;
+    const uint64_t key = adj_key(p.ylt[t]);
+    const int c = key > thr ? 2 : (key == thr ? 3 : 1);
+    const int64_t beg = __ldg(p.offsets + t), end = __ldg(p.offsets + t + 1);
+    if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; continue; }
+    // sixteen independent streaming loads per lane in flight, then the filtered atomics
+    for (int64_t i0 = beg; i0 < end; i0 += 512) {
+      int ev[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int64_t i = i0 + 32 * u + lane;
-          ev[u] = i < end ? __ldcs(p.ids + i) : -1;
-        }
+      for (int u = 0; u < 16; ++u) {
+        const int64_t i = i0 + 32 * u + lane;
+        ev[u] = i < end ? __ldcs(p.ids + i) : -1;
+      }
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int64_t i = i0 + 32 * u + lane;
-          const int e = ev[u];
-          if (i >= end) continue;
-          if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; continue; }
-          if (!((bm[(uint32_t)e >> shift5] >> (e & 31)) & 1u)) continue;
-          atomicAdd(p.h_mean + e, 1u);
-          if (c == 2) atomicAdd(p.h_gt + e, 1u);
-          else if (c == 3) atomicAdd(p.h_eq + e, 1u);
-        }
+      for (int u = 0; u < 16; ++u) {
+        const int64_t i = i0 + 32 * u + lane;
+        const int e = ev[u];
+        if (i >= end) continue;
+        if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; continue; }
+        if (!((bm[(uint32_t)e >> shift5] >> (e & 31)) & 1u)) continue;
+        atomicAdd(p.h_mean + e, 1u);
+        if (c == 2) atomicAdd(p.h_gt + e, 1u);
+        else if (c == 3) atomicAdd(p.h_eq + e, 1u);
       }
     }
   }
