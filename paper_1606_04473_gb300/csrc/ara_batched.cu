@@ -231,10 +231,17 @@ k_bt_stream(BtStream p) {
           const uint32_t e = (uint32_t)ev[u];
           if (e >= p.catalogue) { bad_id = true; continue; }
           const uint32_t rb = __ldg(p.row_ptr + e), re = __ldg(p.row_ptr + e + 1);
-          for (uint32_t r = rb; r < re; ++r) {
+          // Rows list layers in slot order, so the lanes' k-th entries would crowd onto the same
+          // few slots and their shared-memory atomics onto the same words.  Each lane starts at
+          // its own place in the row (floor(lane * len / 32)) and wraps around; integer sums do
+          // not depend on the order.
+          const uint32_t len = re - rb;
+          uint32_t r = rb + (((uint32_t)lane * len) >> 5);
+          for (uint32_t k = 0; k < len; ++k) {
             const uint64_t x = __ldg(p.entries + r);
             const int s = (int)(x >> 56);
             smem_add_u128(&lo[s], &hi[s], x & ((1ull << 56) - 1));
+            if (++r == re) r = rb;
           }
         }
       }
