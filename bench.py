@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-portfolio measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-oep", action="store_true", help="skip the occurrence-basis measurement")
     ap.add_argument("--serving-requests", type=int, default=200)
     return ap.parse_args()
 
@@ -403,6 +404,7 @@ def run_ours(args, rank, ws, local):
             "alg_bytes_per_launch": alg_bytes, "ms_per_launch": round(per_launch_ms, 4),
             "frac_8byte_events": round((alg_bytes + 4 * n_events) / (per_launch_ms / 1e3) / 1e9 / peak, 4)}
 
+    oep_line = None if args.no_oep else measure_oep(g, off, ids, ylt, lookups_per_step)
     g.close()
     del ids, off, ylt
     torch.cuda.empty_cache()
@@ -443,6 +445,7 @@ def run_ours(args, rank, ws, local):
                         "d2h_bytes_per_step": d2h, "api": e2e_api,
                         "ms_per_step_staged": e2e_staged * 1e3,
                         "ms_per_step_direct": (e2e_direct * 1e3 if e2e_direct != float("inf") else None)},
+                "oep": oep_line,
                 "adjoint": adjoint_line,
                 "batched": batched_line,
                 "serving": serving_line,
@@ -451,6 +454,26 @@ def run_ours(args, rank, ws, local):
                 "results": {"pml100": float(pml[0, 0]), "pml250": float(pml[0, 1]),
                             "tvar99": float(tvar[0, 0])}}
         print(json.dumps(line), flush=True)
+
+
+def measure_oep(g, off, ids, ylt, lookups: int, reps: int = 20):
+    """Occurrence basis (ARA_RUN_OEP: y_t = the largest net occurrence loss of trial t) on the
+    resident paper-scale YET: the same stream with an exact fixed-point max per trial."""
+    import torch
+    import paper_1606_04473_gb300 as ara
+    for _ in range(3):
+        g.run_ylt(off, ids, out=ylt, flags=ara.ARA_RUN_OEP)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.run_ylt(off, ids, out=ylt, flags=ara.ARA_RUN_OEP)
+    e1.record()
+    torch.cuda.synchronize()
+    g.check()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": "paper scale, occurrence basis (largest net occurrence loss per trial)",
+            "ms_per_run": round(ms, 4), "lookups_per_s": lookups / (ms / 1e3)}
 
 
 def measure_adjoint(rank: int, reps: int = 5):
