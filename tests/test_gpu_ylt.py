@@ -251,6 +251,28 @@ def test_device_side_data_errors_are_reported_and_recoverable(tiny):
     assert_ylt_close(y.cpu().numpy(), ref, agg)
 
 
+def test_warp_range_at_the_stream_limit_is_a_data_error(tiny):
+    """One trial of 2^31 - 256 events: the default stream kernel gives each warp a contiguous
+    trial range and accepts ranges below 2^31 - 512 events only.  Its range check runs before any
+    event ID is read (the 8 GB ID buffer is left uninitialised), the run reports ARA_EDATA, and
+    the next run is unaffected."""
+    pf, yet, ref, agg = tiny
+    g = ara.Portfolio.from_tables(pf)
+    n = (1 << 31) - 256
+    big = torch.empty(n, dtype=torch.int32, device="cuda")
+    off1 = torch.tensor([0, n], dtype=torch.int64, device="cuda")
+    g.run_ylt(off1, big)
+    with pytest.raises(ara.AraError) as e:
+        g.check()
+    assert e.value.status == ara.ARA_EDATA
+    del big
+    torch.cuda.empty_cache()
+    off, ids = dev(yet)
+    y = g.run_ylt(off, ids)
+    g.check()
+    assert_ylt_close(y.cpu().numpy(), ref, agg)
+
+
 def test_repeatable_bitwise(mid):
     pf, yet, ref, agg = mid
     g = ara.Portfolio.from_tables(pf)
