@@ -97,6 +97,18 @@ __device__ __forceinline__ uint32_t adj_coarsen(const uint32_t* __restrict__ src
   return out;
 }
 
+// Hint that bytes [a, b) of the ID array will be read soon: one bulk prefetch into L2 of the
+// 16-byte-aligned part of the range that lies inside the array (a hint; nothing is loaded into
+// registers or shared memory).
+__device__ __forceinline__ void prefetch_ids_l2(const int32_t* ids, int64_t n_events, int64_t b0,
+                                                int64_t b1) {
+  const uintptr_t base = (uintptr_t)ids, lo = base + 4 * (uintptr_t)max(b0, (int64_t)0);
+  const uintptr_t hi = base + 4 * (uintptr_t)min(b1, n_events);
+  const uintptr_t a = (lo + 15) & ~(uintptr_t)15, e = hi & ~(uintptr_t)15;
+  if (e > a)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
+}
+
 __global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
   extern __shared__ uint32_t bm[];
   for (int64_t cw = threadIdx.x; cw < p.smem_words; cw += blockDim.x)
@@ -110,31 +122,51 @@ __global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
   bool bad_id = false, bad_off = false;
   // Trials are dealt one at a time, round-robin over every warp of the grid, so each warp gets
   // n_trials / warps of them (a 32-trial unit left most warps idle or doubly loaded).  The
-  // trial's class and range are read by the whole warp (one broadcast load each).
-  for (int64_t t = warp; t < p.n_trials; t += nwarps) {
-    if (p.regimes[t] != 1) continue;
-    const uint64_t key = adj_key(p.ylt[t]);
-    const int c = key > thr ? 2 : (key == thr ? 3 : 1);
-    const int64_t beg = __ldg(p.offsets + t), end = __ldg(p.offsets + t + 1);
-    if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; continue; }
-    // sixteen independent streaming loads per lane in flight, then the filtered atomics
-    for (int64_t i0 = beg; i0 < end; i0 += 512) {
-      int ev[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int64_t i = i0 + 32 * u + lane;
-        ev[u] = i < end ? __ldcs(p.ids + i) : -1;
+  // class and range of the warp's next 32 trials are loaded at once, one trial per lane, so the
+  // chain regime -> year loss -> offsets is paid once per 32 trials; while a trial is processed,
+  // the IDs of the warp's next interior trial are fetched into L2.
+  for (int64_t tb = warp; tb < p.n_trials; tb += 32 * nwarps) {
+    const int64_t tl = tb + (int64_t)lane * nwarps;
+    int cls = 0;
+    int64_t mb = 0, me = 0;
+    if (tl < p.n_trials && p.regimes[tl] == 1) {
+      const uint64_t key = adj_key(p.ylt[tl]);
+      cls = key > thr ? 2 : (key == thr ? 3 : 1);
+      mb = __ldg(p.offsets + tl);
+      me = __ldg(p.offsets + tl + 1);
+    }
+    unsigned todo = __ballot_sync(FULLM, cls != 0);
+    while (todo) {
+      const int k = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int c = __shfl_sync(FULLM, cls, k);
+      const int64_t beg = __shfl_sync(FULLM, mb, k), end = __shfl_sync(FULLM, me, k);
+      if (todo) {   // the next interior trial of this batch
+        const int kn = __ffs(todo) - 1;
+        const int64_t nb = __shfl_sync(FULLM, mb, kn), ne = __shfl_sync(FULLM, me, kn);
+        if (lane == 0 && 0 <= nb && nb <= ne && ne <= p.n_events)
+          prefetch_ids_l2(p.ids, p.n_events, nb, ne);
       }
+      if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; continue; }
+      // sixteen independent streaming loads per lane in flight, then the filtered atomics
+      for (int64_t i0 = beg; i0 < end; i0 += 512) {
+        int ev[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int64_t i = i0 + 32 * u + lane;
-        const int e = ev[u];
-        if (i >= end) continue;
-        if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; continue; }
-        if (!((bm[(uint32_t)e >> shift5] >> (e & 31)) & 1u)) continue;
-        atomicAdd(p.h_mean + e, 1u);
-        if (c == 2) atomicAdd(p.h_gt + e, 1u);
-        else if (c == 3) atomicAdd(p.h_eq + e, 1u);
+        for (int u = 0; u < 16; ++u) {
+          const int64_t i = i0 + 32 * u + lane;
+          ev[u] = i < end ? __ldcs(p.ids + i) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int64_t i = i0 + 32 * u + lane;
+          const int e = ev[u];
+          if (i >= end) continue;
+          if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; continue; }
+          if (!((bm[(uint32_t)e >> shift5] >> (e & 31)) & 1u)) continue;
+          atomicAdd(p.h_mean + e, 1u);
+          if (c == 2) atomicAdd(p.h_gt + e, 1u);
+          else if (c == 3) atomicAdd(p.h_eq + e, 1u);
+        }
       }
     }
   }
