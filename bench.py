@@ -210,11 +210,17 @@ def ncu_traffic_per_launch():
 
 
 def kernel_source_sha():
+    """Hash of the stream kernel's sources with line comments, trailing blanks and empty lines
+    removed: a change of the code voids the recorded traffic, a change of a comment does not."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in ("ara_ylt.cu", "ara_device.cuh"):
-        with open(os.path.join(ROOT, "paper_1606_04473_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1606_04473_gb300", "csrc", name)) as f:
+            for line in f:
+                code = re.sub(r"//.*$", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -295,7 +295,8 @@ __global__ void __launch_bounds__(YLT_THREADS, 1) k_ylt_folded(StreamParams p) {
 // one is processed, across trial boundaries.  The unaligned head and tail of the range (< 4 IDs
 // each) use plain loads.  Positions are attributed to trials by a segmented walk over the
 // trial offsets (prefetched 32 at a time), with the per-lane partial sums reduced at each trial
-// end; lane k of a group collects trial k's sum and the aggregate terms of 32 trials run at once.
+// end (three redux.sync limb sums); lane k of a group collects trial k's sum and the aggregate
+// terms of 32 trials run at once.
 // Every mbarrier wait is bounded: on timeout the warp records DERR_TIMEOUT, waits (bounded) for
 // its own copies still in flight, and returns.
 // ------------------------------------------------------------------------------------------
@@ -866,7 +867,7 @@ static ara_status launch_folded_one(Portfolio& pf, StreamParams& sp, cudaStream_
 
 // Compiled shapes of the bulk kernel (warps per block, ring stages, IDs per stage); the active
 // one is chosen with ara_set_stream_shape.  The default, 28 warps, measured fastest at paper
-// scale: it leaves each thread 73 registers (32 warps: 64), which costs fewer extra
+// scale: it leaves each thread up to 72 registers (32 warps: 64), which costs fewer extra
 // instructions, while keeping enough warps to hide the gathers' latency.
 static const int kBulkShapes[][3] = {{28, 2, 256}, {32, 2, 256}, {24, 4, 256}, {24, 2, 512},
                                      {16, 3, 512}, {16, 4, 256}};
