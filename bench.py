@@ -433,7 +433,8 @@ def run_ours(args, rank, ws, local):
                            "n_elts": N_ELTS, "catalogue": CATALOGUE, "flags": args.flags,
                            "layout": "folded per-event table + smem hit bitmap",
                            "accumulation": "exact 128-bit fixed-point trial sums, FP64 terms",
-                           "l2": "inputs larger than L2 (4 GB of event IDs per step), no flush",
+                           "l2": f"inputs larger than L2 ({4 * n_events / 1e9:.2g} GB of event IDs "
+                                 "per step), no flush",
                            "parallelism": f"replicas x{ws}",
                            "step": "YLT + PML/TVaR queued stream-ordered (ara_run_ylt, "
                                    "ara_risk_metrics_async), each step's results copied to pinned "
