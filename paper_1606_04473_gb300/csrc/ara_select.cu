@@ -174,7 +174,7 @@ constexpr int SEL_SMEM_VALUES = 24000;
 // contend for one shared-memory word.
 constexpr int SEL_SUBH = 32;
 
-// The whole selection of the layers [l0, l0 + gridDim.y): 8 radix passes and the tail pass.
+// The whole selection of the layers [l0, l0 + gridDim.y): up to 8 radix passes and the tail pass.
 // Block b of a layer owns the contiguous slice [b n / B, (b + 1) n / B) of the layer's row;
 // when it fits, the slice is read once into shared memory and every pass reads it there.
 //
