@@ -148,24 +148,33 @@ __global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
           prefetch_ids_l2(p.ids, p.n_events, nb, ne);
       }
       if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; continue; }
-      // sixteen independent streaming loads per lane in flight, then the filtered atomics
-      for (int64_t i0 = beg; i0 < end; i0 += 512) {
-        int ev[16];
+      // the trial's second histogram (above / equal to the threshold), uniform over the warp
+      uint32_t* const hx = c == 2 ? p.h_gt : (c == 3 ? p.h_eq : nullptr);
+      // segments of at most 2^30 IDs keep the per-ID offsets in 32 bits
+      for (int64_t sb = beg; sb < end; sb += ((int64_t)1 << 30)) {
+        const int32_t* const idp = p.ids + sb;
+        const int32_t n = (int32_t)min(end - sb, (int64_t)1 << 30);
+        // sixteen independent streaming loads per lane in flight, then the filtered atomics; the
+        // range, ID and bitmap tests are predicates, not branches
+        for (int32_t o = 0; o < n; o += 512) {
+          int ev[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int64_t i = i0 + 32 * u + lane;
-          ev[u] = i < end ? __ldcs(p.ids + i) : -1;
-        }
+          for (int u = 0; u < 16; ++u) {
+            const int32_t j = o + 32 * u + lane;
+            ev[u] = j < n ? __ldcs(idp + j) : 0;
+          }
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int64_t i = i0 + 32 * u + lane;
-          const int e = ev[u];
-          if (i >= end) continue;
-          if ((unsigned)e >= (unsigned)p.catalogue) { bad_id = true; continue; }
-          if (!((bm[(uint32_t)e >> shift5] >> (e & 31)) & 1u)) continue;
-          atomicAdd(p.h_mean + e, 1u);
-          if (c == 2) atomicAdd(p.h_gt + e, 1u);
-          else if (c == 3) atomicAdd(p.h_eq + e, 1u);
+          for (int u = 0; u < 16; ++u) {
+            const int32_t j = o + 32 * u + lane;
+            const uint32_t e = (uint32_t)ev[u];
+            const bool in = j < n, ok = e < (uint32_t)p.catalogue;
+            bad_id |= in && !ok;
+            const uint32_t w = (in && ok) ? bm[e >> shift5] : 0u;
+            if ((w >> (e & 31)) & 1u) {
+              atomicAdd(p.h_mean + e, 1u);
+              if (hx) atomicAdd(hx + e, 1u);
+            }
+          }
         }
       }
     }
