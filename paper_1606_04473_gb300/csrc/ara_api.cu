@@ -614,8 +614,9 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
     return ARA_EINVAL;
   if (flags & ARA_RUN_BATCHED) return ARA_EINVAL;
   if (h_off[0] != 0) return ARA_EINVAL;
-  for (int64_t t = 0; t < n_trials; ++t)
-    if (h_off[t + 1] < h_off[t]) return ARA_EINVAL;
+  bool decreasing = false;   // no early exit, so the scan vectorises
+  for (int64_t t = 0; t < n_trials; ++t) decreasing |= h_off[t + 1] < h_off[t];
+  if (decreasing) return ARA_EINVAL;
   const int64_t n_events = h_off[n_trials];
   if (sel.empty() || n_trials == 0) return ARA_OK;
   if (n_events > 0 && !h_ids) return ARA_EINVAL;
@@ -655,8 +656,11 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
   std::vector<int64_t> cut{0};
   int64_t max_ev = 0, max_tr = 0;
   for (int64_t t = 0; t < n_trials;) {
-    int64_t t1 = t + 1;
-    while (t1 < n_trials && t1 - t < CH_TRIALS && h_off[t1 + 1] - h_off[t] <= CH_EVENTS) ++t1;
+    // the last t1 in (t, t + CH_TRIALS] whose offset is within CH_EVENTS of h_off[t] (at least
+    // t + 1: a trial longer than CH_EVENTS is a chunk of its own), by binary search
+    const int64_t lim = std::min(n_trials, t + CH_TRIALS);
+    const int64_t* up = std::upper_bound(h_off + t + 1, h_off + lim + 1, h_off[t] + CH_EVENTS);
+    const int64_t t1 = std::max<int64_t>(t + 1, (int64_t)(up - h_off) - 1);
     max_ev = std::max(max_ev, h_off[t1] - h_off[t]);
     max_tr = std::max(max_tr, t1 - t);
     cut.push_back(t1);

@@ -315,6 +315,21 @@ def test_host_pipeline_multi_chunk():
     assert_ylt_close(y_host[:, sample], ref, agg)
 
 
+def test_host_pipeline_rejects_decreasing_offsets(tiny):
+    """Host offsets are validated before anything is queued: a decreasing pair anywhere (here
+    the last) is ARA_EINVAL in both host modes, and the portfolio stays usable."""
+    pf, yet, ref, agg = tiny
+    g = ara.Portfolio.from_tables(pf)
+    bad = np.array(yet.offsets, dtype=np.int64)
+    bad[-2] = bad[-1] + 1
+    for flags in (0, ara.ARA_RUN_HOST_DIRECT):
+        with pytest.raises(ara.AraError) as e:
+            g.run_ylt_host(bad, yet.event_ids, flags=flags)
+        assert e.value.status == ara.ARA_EINVAL
+    y = g.run_ylt_host(yet.offsets, yet.event_ids)
+    assert_ylt_close(y, ref, agg)
+
+
 def test_host_direct_reads_pinned_host_memory(mid):
     """ARA_RUN_HOST_DIRECT: the kernel reads the pinned host YET in place; same YLT as the
     device path.  Pageable memory is read in place too on platforms where the device can
