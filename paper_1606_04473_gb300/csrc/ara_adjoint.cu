@@ -83,6 +83,7 @@ struct AdjHistParams {
   uint32_t* h_gt;
   uint32_t* h_eq;
   uint32_t* err;
+  AdjCounts* acc;             // this layer's trial counts (agg) are added here
 };
 
 // Coarse regime bitmap word cw, interleaved: bit i is the OR of bit i of the exact words
@@ -111,8 +112,11 @@ __device__ __forceinline__ void prefetch_ids_l2(const int32_t* ids, int64_t n_ev
 
 __global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
   extern __shared__ uint32_t bm[];
+  // per warp: trial counts [regime 1 / 2][all, above, equal to the threshold]
+  __shared__ unsigned int tcnt[32][6];
   for (int64_t cw = threadIdx.x; cw < p.smem_words; cw += blockDim.x)
     bm[cw] = adj_coarsen(p.bits, cw, p.shift, p.bm_words);
+  if (threadIdx.x < 32 * 6) tcnt[threadIdx.x / 6][threadIdx.x % 6] = 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -129,11 +133,29 @@ __global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
     const int64_t tl = tb + (int64_t)lane * nwarps;
     int cls = 0;
     int64_t mb = 0, me = 0;
-    if (tl < p.n_trials && p.regimes[tl] == 1) {
+    const uint8_t rg = tl < p.n_trials ? p.regimes[tl] : 0;
+    bool above = false, equal = false;
+    if (rg != 0) {
       const uint64_t key = adj_key(p.ylt[tl]);
-      cls = key > thr ? 2 : (key == thr ? 3 : 1);
+      above = key > thr;
+      equal = key == thr;
+    }
+    if (rg == 1) {
+      cls = above ? 2 : (equal ? 3 : 1);
       mb = __ldg(p.offsets + tl);
       me = __ldg(p.offsets + tl + 1);
+    }
+    {   // the batch's trial counts, by regime and position against the threshold
+      const unsigned c0 = __popc(__ballot_sync(FULLM, rg == 1));
+      const unsigned c1 = __popc(__ballot_sync(FULLM, rg == 1 && above));
+      const unsigned c2 = __popc(__ballot_sync(FULLM, rg == 1 && equal));
+      const unsigned c3 = __popc(__ballot_sync(FULLM, rg == 2));
+      const unsigned c4 = __popc(__ballot_sync(FULLM, rg == 2 && above));
+      const unsigned c5 = __popc(__ballot_sync(FULLM, rg == 2 && equal));
+      if (lane == 0) {
+        unsigned int* tc = tcnt[threadIdx.x >> 5];
+        tc[0] += c0; tc[1] += c1; tc[2] += c2; tc[3] += c3; tc[4] += c4; tc[5] += c5;
+      }
     }
     unsigned todo = __ballot_sync(FULLM, cls != 0);
     while (todo) {
@@ -181,6 +203,12 @@ __global__ void __launch_bounds__(1024, 1) k_adj_hist(AdjHistParams p) {
   }
   if (bad_id) atomicOr(p.err, DERR_EVENT_RANGE);
   if (bad_off) atomicOr(p.err, DERR_OFFSETS);
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    unsigned long long sum = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += tcnt[w][threadIdx.x];
+    if (sum) atomicAdd(&p.acc->agg[0][0] + threadIdx.x, sum);
+  }
 }
 
 // Sums over catalogue events of the histograms, split by occurrence regime.
@@ -261,25 +289,6 @@ __global__ void __launch_bounds__(256) k_adj_records(AdjRecParams p) {
 }
 
 // Per trial: counts of interior / saturated aggregate regimes, overall and in TVaR's top set.
-__global__ void __launch_bounds__(256) k_adj_trials(int64_t n, const uint8_t* __restrict__ regimes,
-                                                    const double* __restrict__ ylt,
-                                                    const uint64_t* __restrict__ thr_key,
-                                                    AdjCounts* __restrict__ acc) {
-  const uint64_t thr = *thr_key;
-  unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const uint8_t r = regimes[t];
-    if (r == 0) continue;
-    const int o = (r == 1) ? 0 : 3;
-    const uint64_t k = adj_key(ylt[t]);
-    v[o + 0] += 1;
-    v[o + 1] += k > thr ? 1 : 0;
-    v[o + 2] += k == thr ? 1 : 0;
-  }
-  block_add<6>(v, &acc->agg[0][0]);
-}
-
 // Final per-layer gradients from the integer counts.
 __global__ void k_adj_finish(const AdjCounts* __restrict__ acc, const SlotCounts* __restrict__ slots,
                              int32_t n_slots, const unsigned long long* sel_gt,
@@ -465,15 +474,15 @@ extern "C" ara_status ara_adjoint(ara_portfolio* pf_, int64_t n_trials, const in
     hp.h_gt = hg;
     hp.h_eq = he;
     hp.err = pf->d_err;
+    hp.acc = acc;
     {
-      LaunchScope ls(ARA_K_ADJOINT, s, 4);
+      // the histogram pass (which also counts the trials), the event and record reductions,
+      // and the final combination
+      LaunchScope ls(ARA_K_ADJOINT, s, n_le > 0 ? 4 : 3);
       // the threshold key is read on the device from the selection result
       k_adj_hist<<<pf->n_sms, 1024, smem, s>>>(hp);
       k_adj_events<<<std::max(1, (int)std::min<int64_t>((C + 2047) / 2048, 4 * pf->n_sms)), 256, 0, s>>>(
           C, reg, hm, hg, he, acc);
-      k_adj_trials<<<std::max(1, (int)std::min<int64_t>((n_trials + 2047) / 2048, 4 * pf->n_sms)), 256, 0, s>>>(
-          n_trials, d_regimes + (int64_t)i * n_trials, d_ylt + (int64_t)i * n_trials,
-          sr.thr_key + (int64_t)i * sr.thr_stride, acc);
       AdjRecParams rp{};
       rp.rec_off = pf->d_rec_off;
       rp.rec_ids = pf->d_rec_ids;
