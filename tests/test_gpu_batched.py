@@ -84,3 +84,32 @@ def test_plan_layer_subset_and_rebound_inputs(case):
     single = g.run_ylt(off, ids, layers=[5, 0, 19])
     assert torch.equal(y2, single)
     plan.close()
+
+
+def test_plan_with_many_layers_equals_single_layer_path():
+    """130 layers of 1-4 ELTs (more than two groups of 64 layer slots in the table): the plan's
+    YLT equals the single-layer path bit for bit, and the oracle's raw trial sums (zero
+    retentions, infinite limits at the layer level) within the YLT tolerance."""
+    rng = np.random.default_rng(5)
+    C, pool, nl = 200_000, 40, 130
+    ids, losses = synth.make_elts(5, pool, 2000, C, 11.0, 2.0, f32=True)
+    r, l = synth.percentile_terms(losses)
+    layers = [sorted(rng.choice(pool, size=int(rng.integers(1, 5)), replace=False).tolist())
+              for _ in range(nl)]
+    counts = synth.poisson_counts(5, 200.0, 1500)
+    counts[:3] = [0, 1, 2]
+    yet = synth.make_yet(5, counts, C, with_timestamps=False)
+    z, inf = np.zeros(nl), np.full(nl, np.inf)
+    pf = synth.Portfolio(C, ids, losses, r, l, layers, z, inf, z, inf, losses_f32=True)
+    g = ara.Portfolio.from_tables(pf)
+    off, ev = dev(yet)
+    single = g.run_ylt(off, ev).clone()
+    plan = ara.BatchedPlan(g, off, ev, autotune=False)
+    y = plan.launch()
+    g.check()
+    assert torch.equal(y, single)
+    ref, agg = oracle.ylt(pf, yet, return_agg=True)
+    err = np.abs(y.cpu().numpy() - ref)
+    assert np.all(err <= 1e-6 * np.abs(ref) + 1e-12 * np.abs(agg))
+    plan.close()
+    g.close()
