@@ -200,3 +200,31 @@ def test_adjoint_tie_at_the_tvar_boundary():
     close(gr["layer"][1].cpu().numpy(), ref["layer"], 1.0)
     close(gr["elt"][1].cpu().numpy(), ref["elt"], 1.0)
     close(gr["loss"][1].cpu().numpy(), ref["loss"], 1.0)
+
+
+def test_adjoint_wide_layer_and_single_elt_layer():
+    """A layer of 40 ELTs (the fold stages its records in two batches of at most 32 ELTs) next
+    to a one-ELT layer: the gradients of both objectives match the FP64 chain rule."""
+    seed = 23
+    C, n_elts = 60_000, 40
+    ids, losses = synth.make_elts(seed, n_elts, 1500, C, 11.0, 2.0, f32=True)
+    r, l = synth.percentile_terms(losses)
+    counts = synth.poisson_counts(seed, 300.0, 2500)
+    counts[:2] = [0, 1]
+    yet = synth.make_yet(seed, counts, C, with_timestamps=False)
+    z = np.zeros(2)
+    pf = synth.Portfolio(C, ids, losses, r, l, [list(range(40)), [3]], z, z, z, z, losses_f32=True)
+    from oracle.derive_terms import derive
+    pf = pf.with_terms(derive(pf, synth.YET(yet.offsets[:1001], yet.event_ids[:int(yet.offsets[1000])]),
+                              20.0, 80.0))
+    assert well_posed(pf, yet, LEVEL)
+    g = ara.Portfolio.from_tables(pf)
+    off, ids_d, y, reg = forward(g, yet)
+    gr = g.adjoint(off, ids_d, y, reg, LEVEL)
+    for obj, name in ((0, "mean"), (1, "tvar")):
+        ref = oracle.adjoint(pf, yet, name, LEVEL)
+        scale = max(1.0, float(np.abs(ref["loss"]).max()))
+        close(gr["elt"][obj].cpu().numpy(), ref["elt"], 1.0)
+        close(gr["layer"][obj].cpu().numpy(), ref["layer"], 1.0)
+        close(gr["loss"][obj].cpu().numpy(), ref["loss"], scale)
+    g.close()
