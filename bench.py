@@ -440,7 +440,7 @@ def run_ours(args, rank, ws, local):
                                    "ara_risk_metrics_async), each step's results copied to pinned "
                                    "host memory; one host synchronisation after the last step"},
                 "lookups_per_step": lookups_per_step,
-                "kernel_ms": {"fold": round(fold_ms / max(fold_n, 1), 4),
+                "kernel_ms": {"fold_and_coarsen_per_step": round(fold_ms / max(args.steps, 1), 4),
                               "ylt_stream": round(per_launch_ms, 4),
                               "select": round(sel_ms / max(sel_n, 1), 4),
                               "measured": "CUDA events around every launch on its stream, over a "

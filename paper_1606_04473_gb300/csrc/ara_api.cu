@@ -147,7 +147,7 @@ static void free_portfolio(ara_portfolio* p) {
       if (q) cudaFree(q);
   } else {
     void* ptrs[] = {p->d_rec_off, p->d_rec_ids, p->d_rec_orig, p->d_rec_loss, p->d_rec_loss32,
-                    p->d_elt_ret, p->d_elt_lim, p->d_layer_elts, p->d_layers, p->d_dense, p->d_q,
+                    p->d_elt_ret, p->d_elt_lim, p->d_tile_rec, p->d_layer_elts, p->d_layers, p->d_dense, p->d_q,
                     p->d_bits, p->d_cbits, p->d_err, p->d_stage_ids[0], p->d_stage_ids[1],
                     p->d_stage_off[0], p->d_stage_off[1], p->d_ylt_full};
     for (void* q : ptrs)
@@ -357,6 +357,19 @@ ara_status ara_create_portfolio(int64_t C, int32_t n_elts, const int64_t* rec_of
   } else if ((st = upload(&p->d_rec_loss, loss_sorted.data(), (size_t)n_rec)) != ARA_OK) {
     return fail(st);
   }
+  {   // per ELT, the first record of every fold tile (records are sorted by event ID)
+    p->n_tiles = (C + FOLD_TILE - 1) / FOLD_TILE;
+    const int64_t nt1 = p->n_tiles + 1;
+    std::vector<int64_t> tile_rec((size_t)std::max<int64_t>(1, (int64_t)n_elts * nt1));
+    for (int32_t j = 0; j < n_elts; ++j) {
+      int64_t r = rec_off[j];
+      for (int64_t t = 0; t < nt1; ++t) {
+        while (r < rec_off[j + 1] && (int64_t)ids_sorted[(size_t)r] < t * FOLD_TILE) ++r;
+        tile_rec[(size_t)(j * nt1 + t)] = r;
+      }
+    }
+    if ((st = upload(&p->d_tile_rec, tile_rec.data(), tile_rec.size())) != ARA_OK) return fail(st);
+  }
   if ((st = upload(&p->d_elt_ret, elt_ret, (size_t)n_elts)) != ARA_OK) return fail(st);
   if ((st = upload(&p->d_elt_lim, elt_lim, (size_t)n_elts)) != ARA_OK) return fail(st);
   if ((st = upload(&p->d_layer_elts, p->layer_elts.data(), p->layer_elts.size())) != ARA_OK)
@@ -441,6 +454,8 @@ ara_status ara_create_layer_set(ara_portfolio* pool, int32_t n_layers, const int
   p->d_rec_loss32 = pool->d_rec_loss32;
   p->d_elt_ret = pool->d_elt_ret;
   p->d_elt_lim = pool->d_elt_lim;
+  p->n_tiles = pool->n_tiles;
+  p->d_tile_rec = pool->d_tile_rec;
   p->d_dense = pool->d_dense;
   p->layer_off.assign(layer_off, layer_off + n_layers + 1);
   p->layer_elts.assign(layer_elts, layer_elts + layer_off[n_layers]);

@@ -68,6 +68,10 @@ struct LayerConst {
   int32_t pad;
 };
 
+// Catalogue events per tile of the fold kernel; the portfolio keeps, per ELT, the first record
+// of every tile so that the fold reads each tile's record range instead of searching for it.
+constexpr int FOLD_TILE = 2048;
+
 struct Portfolio {
   bool borrowed_elts = false;       // a layer set: ELT tables belong to a resident pool
   cudaStream_t owner_stream = nullptr;  // layer sets: stream their buffers were allocated on
@@ -90,6 +94,8 @@ struct Portfolio {
   float* d_rec_loss32 = nullptr;    // [n_records] (FP32 storage) or nullptr
   double* d_elt_ret = nullptr;      // [n_elts]
   double* d_elt_lim = nullptr;      // [n_elts]
+  int64_t n_tiles = 0;              // fold tiles: ceil(catalogue / FOLD_TILE)
+  int64_t* d_tile_rec = nullptr;    // [n_elts][n_tiles + 1]: first record of each ELT per tile
   int32_t* d_layer_elts = nullptr;  // [layer_off[n_layers]]
   LayerConst* d_layers = nullptr;   // [n_layers]
   void* d_dense = nullptr;          // [n_elts][catalogue] float or double (ARA_DENSE_TABLES)

@@ -16,7 +16,6 @@
 
 namespace ara {
 
-constexpr int FOLD_TILE = 2048;
 constexpr int FOLD_THREADS = 256;
 constexpr int YLT_THREADS = 1024;
 constexpr int MAX_SEL = 256;
@@ -27,14 +26,6 @@ struct SelList {
 };
 
 
-__device__ __forceinline__ int64_t lower_bound_ids(const int32_t* __restrict__ ids, int64_t lo,
-                                                   int64_t hi, int64_t v) {
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if ((int64_t)ids[mid] < v) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
 
 // ------------------------------------------------------------------------------------------
 // Fold: o(e) = C(sum_j C(x_j(e); R_j, L_j); OccR, OccL) for every catalogue event e of one
@@ -58,7 +49,8 @@ constexpr int FOLD_REC = 2048;     // records staged in shared memory per batch
 
 template <typename LossT>
 __global__ void __launch_bounds__(FOLD_THREADS)
-k_fold(int64_t catalogue, const int64_t* __restrict__ rec_off, const int32_t* __restrict__ rec_ids,
+k_fold(int64_t catalogue, const int64_t* __restrict__ tile_rec, int64_t n_tiles,
+       const int32_t* __restrict__ rec_ids,
        const LossT* __restrict__ rec_loss, const double* __restrict__ elt_ret,
        const double* __restrict__ elt_lim, const int32_t* __restrict__ layer_elts,
        const LayerConst* __restrict__ layers, SelList sel, FoldOut out) {
@@ -79,17 +71,16 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ rec_off, const int32_t* __
   for (int i = threadIdx.x; i < FOLD_TILE; i += blockDim.x) { s[i] = 0.0; reg[i] = 0; }
   if (threadIdx.x == 0) n_list = 0;
   // The layer's ELTs in order, in batches: the record ranges of up to FOLD_GROUP ELTs within
-  // this tile are found by parallel binary searches, the records of the longest prefix of them
+  // this tile are read from the portfolio's tile index, the records of the longest prefix of them
   // that fits FOLD_REC are loaded at once with their ELT terms applied, and then added into
   // the tile one ELT after the other (IDs are unique within an ELT, so one ELT's records never
   // collide), which keeps the FP64 sum in the layer's ELT order.
   for (int k0 = lc.elt_begin; k0 < lc.elt_end;) {
     const int G = min(FOLD_GROUP, lc.elt_end - k0);
-    if (threadIdx.x < 2 * G) {
-      const int g = threadIdx.x % G;
-      const int j = layer_elts[k0 + g];
-      const int64_t v = lower_bound_ids(rec_ids, rec_off[j], rec_off[j + 1], threadIdx.x < G ? t0 : t1);
-      if (threadIdx.x < G) lo[g] = v; else hi[g] = v;
+    if (threadIdx.x < G) {
+      const int64_t* tr = tile_rec + (int64_t)layer_elts[k0 + threadIdx.x] * (n_tiles + 1) + blockIdx.x;
+      lo[threadIdx.x] = tr[0];
+      hi[threadIdx.x] = tr[1];
     }
     __syncthreads();
     if (threadIdx.x < 32) {   // counts -> offsets; the batch is the longest prefix that fits
@@ -827,11 +818,11 @@ ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
     dim3 grid((unsigned)((pf.catalogue + FOLD_TILE - 1) / FOLD_TILE), sl.n);
     LaunchScope ls(ARA_K_FOLD, s);
     if (pf.d_rec_loss32)
-      k_fold<float><<<grid, FOLD_THREADS, 0, s>>>(pf.catalogue, pf.d_rec_off, pf.d_rec_ids,
+      k_fold<float><<<grid, FOLD_THREADS, 0, s>>>(pf.catalogue, pf.d_tile_rec, pf.n_tiles, pf.d_rec_ids,
                                                   pf.d_rec_loss32, pf.d_elt_ret, pf.d_elt_lim,
                                                   pf.d_layer_elts, pf.d_layers, sl, ob);
     else
-      k_fold<double><<<grid, FOLD_THREADS, 0, s>>>(pf.catalogue, pf.d_rec_off, pf.d_rec_ids,
+      k_fold<double><<<grid, FOLD_THREADS, 0, s>>>(pf.catalogue, pf.d_tile_rec, pf.n_tiles, pf.d_rec_ids,
                                                    pf.d_rec_loss, pf.d_elt_ret, pf.d_elt_lim,
                                                    pf.d_layer_elts, pf.d_layers, sl, ob);
     ARA_TRY(cudaGetLastError());
