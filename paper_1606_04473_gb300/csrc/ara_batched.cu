@@ -2,15 +2,14 @@
 // and layer loops of Algorithm 1 folded into one launch).
 //
 // Preparation, per run (all on the stream, captured in the plan's CUDA graph):
-//   1. s_i(e) = sum over the ELTs of layer i, in layer order, of C(x_j(e); R_j, L_j): one
-//      scatter launch per ELT slot k (slot k of every layer at once; records of one ELT have
-//      distinct events, so no two threads of a launch touch the same entry), FP64, the same
-//      operation order as the single-layer fold and the FP64 reference.
-//   2. q_i(e) = round(C(s_i(e); OccR_i, OccL_i) * 2^f_i) in place of s_i(e) (the FP64 clamps
-//      run on block-compacted non-zero entries only), and the count of non-zero q per event.
-//   3. exclusive scan of the counts -> CSR row pointers.
-//   4. event-major CSR rows: for event e, its (layer slot, q) pairs in layer order, packed as
-//      slot << 56 | q (q < 2^55).
+//   1. q_i(e) = round(C(sum_j C(x_j(e); R_j, L_j); OccR_i, OccL_i) * 2^f_i) and the hit bitmap
+//      of every selected layer i, in one launch of the single-layer fold kernel (slot i of the
+//      fold workspace; only the non-zero q are stored).  The batched and the single-layer paths
+//      thus share the folded table bit for bit.
+//   2. per-event counts of non-zero q, read from the bitmaps, and their exclusive scan -> CSR
+//      row pointers.
+//   3. event-major CSR rows: for event e, its (layer slot, q) pairs in layer order, packed as
+//      slot << 56 | q (q < 2^55); q is read only where the bitmap bit is set.
 // Stream (persistent, atomic trial queue for uneven trial lengths): a warp takes trials from the
 // queue; for every occurrence it walks the event's CSR row and adds each q to the warp's
 // per-layer accumulator in shared memory (exact 128-bit: 64-bit atomic add with carry); at the
@@ -28,71 +27,13 @@ namespace ara {
 constexpr int BT_MAX_LAYERS = 255;          // slot fits in 8 bits (255 = no slot)
 constexpr int BT_SCAN_BLOCK = 1024;
 
-// ------------------------------------------------------------------------------------------
-// 1. scatter of one ELT slot of every selected layer
-// ------------------------------------------------------------------------------------------
-struct BtScatter {
-  int32_t n_sel;
-  int32_t elt[BT_MAX_LAYERS];   // ELT at this slot for each selected layer, -1 if none
-};
-
-template <typename LossT>
-__global__ void __launch_bounds__(256)
-k_bt_scatter(BtScatter sc, const int64_t* __restrict__ rec_off, const int32_t* __restrict__ rec_ids,
-             const LossT* __restrict__ rec_loss, const double* __restrict__ elt_ret,
-             const double* __restrict__ elt_lim, double* __restrict__ s_tab, int64_t catalogue) {
-  const int i = blockIdx.y;
-  const int j = sc.elt[i];
-  if (j < 0) return;
-  const double R = elt_ret[j], L = elt_lim[j];
-  double* s = s_tab + (int64_t)i * catalogue;
-  for (int64_t r = rec_off[j] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rec_off[j + 1];
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const int e = rec_ids[r];
-    double ex = __dsub_rn((double)rec_loss[r], R);
-    if (ex < 0.0) ex = 0.0;
-    if (ex > L) ex = L;
-    s[e] = __dadd_rn(s[e], ex);
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// 2. occurrence terms and fixed point in place; count of non-zero entries per event
-// ------------------------------------------------------------------------------------------
 struct BtLayers {
   int32_t n_sel;
   int32_t layer[BT_MAX_LAYERS];
 };
 
-__global__ void __launch_bounds__(256)
-k_bt_quantize(BtLayers bl, const LayerConst* __restrict__ layers, double* __restrict__ s_tab,
-              int64_t catalogue, uint32_t* __restrict__ cnt) {
-  __shared__ int32_t list[256];
-  __shared__ int32_t n_list;
-  const int i = blockIdx.y;
-  const LayerConst lc = layers[bl.layer[i]];
-  uint64_t* qt = reinterpret_cast<uint64_t*>(s_tab + (int64_t)i * catalogue);
-  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  if (threadIdx.x == 0) n_list = 0;
-  __syncthreads();
-  const double sv = e < catalogue ? s_tab[(int64_t)i * catalogue + e] : 0.0;
-  if (sv != 0.0) list[atomicAdd(&n_list, 1)] = threadIdx.x;   // compact: FP64 on full warps
-  __syncthreads();
-  if (threadIdx.x < n_list) {
-    const int64_t ee = (int64_t)blockIdx.x * 256 + list[threadIdx.x];
-    const double s = s_tab[(int64_t)i * catalogue + ee];
-    double o = __dsub_rn(s, lc.occ_ret);
-    if (o < 0.0) o = 0.0;
-    if (o > lc.occ_lim) o = lc.occ_lim;
-    const uint64_t q = __double2ull_rn(__dmul_rn(o, lc.scale));
-    qt[ee] = q;
-    if (q) atomicAdd(cnt + ee, 1u);
-  }
-  // entries that were zero stay zero (+0.0 has the bit pattern of q = 0)
-}
-
 // ------------------------------------------------------------------------------------------
-// 3. exclusive scan of the per-event counts (two levels: block sums, then their scan)
+// 2. per-event counts and their exclusive scan (two levels: block sums, then their scan)
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
   __shared__ uint32_t warp_tot[BT_SCAN_BLOCK / 32];
@@ -121,11 +62,23 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
   return before;
 }
 
+// count of event e: the number of selected layers whose bitmap has bit e set (the 32 lanes of a
+// warp read the same word of each bitmap)
+__device__ __forceinline__ uint32_t bt_count(const uint32_t* __restrict__ bits, int64_t bits_stride,
+                                             int32_t n_sel, int64_t e) {
+  const uint32_t* b = bits + (e >> 5);
+  const int sh = (int)(e & 31);
+  uint32_t c = 0;
+#pragma unroll 8
+  for (int i = 0; i < n_sel; ++i) c += (__ldg(b + (int64_t)i * bits_stride) >> sh) & 1u;
+  return c;
+}
+
 __global__ void __launch_bounds__(BT_SCAN_BLOCK)
-k_bt_scan_blocks(const uint32_t* __restrict__ cnt, int64_t n, uint32_t* __restrict__ ptr,
-                 uint32_t* __restrict__ block_sums) {
+k_bt_scan_blocks(const uint32_t* __restrict__ bits, int64_t bits_stride, int32_t n_sel, int64_t n,
+                 uint32_t* __restrict__ ptr, uint32_t* __restrict__ block_sums) {
   const int64_t e = (int64_t)blockIdx.x * BT_SCAN_BLOCK + threadIdx.x;
-  const uint32_t v = e < n ? cnt[e] : 0u;
+  const uint32_t v = e < n ? bt_count(bits, bits_stride, n_sel, e) : 0u;
   uint32_t tot;
   const uint32_t ex = block_excl_scan(v, &tot);
   if (e < n) ptr[e] = ex;
@@ -155,19 +108,33 @@ __global__ void k_bt_scan_add(uint32_t* __restrict__ ptr, int64_t n, const uint3
 }
 
 // ------------------------------------------------------------------------------------------
-// 4. CSR rows: one thread per event, layers in slot order (deterministic layout)
+// 3. CSR rows: one thread per event, layers in slot order (deterministic layout)
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-k_bt_fill(int32_t n_sel, const double* __restrict__ s_tab, int64_t catalogue,
-          const uint32_t* __restrict__ ptr, uint64_t* __restrict__ entries) {
+k_bt_fill(int32_t n_sel, const uint64_t* __restrict__ q, const uint32_t* __restrict__ bits,
+          int64_t bits_stride, int64_t catalogue, const uint32_t* __restrict__ ptr,
+          uint64_t* __restrict__ entries) {
+  constexpr int U = 8;   // slots per step: their bitmap words and table entries load together
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= catalogue) return;
   uint32_t pos = ptr[e];
   const uint32_t end = ptr[e + 1];
-  const uint64_t* qt = reinterpret_cast<const uint64_t*>(s_tab);
-  for (int i = 0; i < n_sel && pos < end; ++i) {
-    const uint64_t q = qt[(int64_t)i * catalogue + e];
-    if (q) entries[pos++] = ((uint64_t)i << 56) | q;
+  const uint32_t* b = bits + (e >> 5);
+  const int sh = (int)(e & 31);
+  for (int i0 = 0; i0 < n_sel && pos < end; i0 += U) {
+    bool hit[U];
+    uint64_t v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      hit[u] = i0 + u < n_sel && ((__ldg(b + (int64_t)(i0 + u) * bits_stride) >> sh) & 1u);
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = hit[u] ? __ldg(q + (int64_t)(i0 + u) * catalogue + e) : 0ull;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (hit[u]) {
+        if (pos < end) entries[pos] = ((uint64_t)(i0 + u) << 56) | v[u];
+        ++pos;
+      }
   }
 }
 
@@ -279,7 +246,6 @@ struct ara_plan {
   std::vector<int32_t> sel;
   double* d_ylt = nullptr;
   uint8_t* d_reg = nullptr;
-  uint32_t* d_cnt = nullptr;
   uint32_t* d_ptr = nullptr;
   uint32_t* d_bsum = nullptr;
   uint32_t* d_total = nullptr;
@@ -288,7 +254,6 @@ struct ara_plan {
   int64_t n_blocks = 0;
   int warps = 16, ctas_per_sm = 2, tpg = 2;
   double tuned_ms = 0.0;
-  int max_le = 0;
   int n_kernels = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -300,36 +265,23 @@ ara_status bt_prep(ara_plan& P, cudaStream_t s, bool fill, int* n_kernels) {
   Portfolio& pf = *P.pf;
   const int n_sel = (int)P.sel.size();
   const int64_t C = pf.catalogue;
-  double* s_tab = reinterpret_cast<double*>(pf.d_q);      // [n_sel][C] scratch
-  int k = 0;
-  ARA_TRY(cudaMemsetAsync(s_tab, 0, sizeof(double) * (size_t)n_sel * C, s));
-  ARA_TRY(cudaMemsetAsync(P.d_cnt, 0, sizeof(uint32_t) * (size_t)C, s));
-  for (int slot = 0; slot < P.max_le; ++slot) {
-    BtScatter sc;
-    sc.n_sel = n_sel;
-    for (int i = 0; i < n_sel; ++i) {
-      const LayerConst& lc = pf.layers[P.sel[i]];
-      sc.elt[i] = slot < lc.elt_end - lc.elt_begin ? pf.layer_elts[lc.elt_begin + slot] : -1;
-    }
-    dim3 grid(32, n_sel);
-    if (pf.d_rec_loss32)
-      k_bt_scatter<float><<<grid, 256, 0, s>>>(sc, pf.d_rec_off, pf.d_rec_ids, pf.d_rec_loss32,
-                                               pf.d_elt_ret, pf.d_elt_lim, s_tab, C);
-    else
-      k_bt_scatter<double><<<grid, 256, 0, s>>>(sc, pf.d_rec_off, pf.d_rec_ids, pf.d_rec_loss,
-                                                pf.d_elt_ret, pf.d_elt_lim, s_tab, C);
-    ++k;
-  }
-  BtLayers bl;
-  bl.n_sel = n_sel;
-  for (int i = 0; i < n_sel; ++i) bl.layer[i] = P.sel[i];
-  k_bt_quantize<<<dim3((unsigned)((C + 255) / 256), n_sel), 256, 0, s>>>(bl, pf.d_layers, s_tab, C, P.d_cnt);
-  k_bt_scan_blocks<<<(unsigned)P.n_blocks, BT_SCAN_BLOCK, 0, s>>>(P.d_cnt, C, P.d_ptr, P.d_bsum);
+  FoldOutHost fo;
+  fo.q = pf.d_q;                 // slot i at d_q + i * C (workspace of the single-layer runs)
+  fo.bits = pf.d_bits;
+  fo.q_stride = C;
+  fo.bits_stride = pf.bm_words;
+  fo.by_slot = 1;
+  fo.nonzero_only = 1;
+  ara_status st = launch_fold_to(pf, n_sel, P.sel.data(), fo, s, false);
+  if (st != ARA_OK) return st;
+  k_bt_scan_blocks<<<(unsigned)P.n_blocks, BT_SCAN_BLOCK, 0, s>>>(pf.d_bits, pf.bm_words, n_sel, C,
+                                                                  P.d_ptr, P.d_bsum);
   k_bt_scan_sums<<<1, BT_SCAN_BLOCK, 0, s>>>(P.d_bsum, P.n_blocks, P.d_total);
   k_bt_scan_add<<<(unsigned)((C + 1 + 255) / 256), 256, 0, s>>>(P.d_ptr, C, P.d_bsum, P.d_total);
-  k += 4;
+  int k = 4;
   if (fill) {
-    k_bt_fill<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(n_sel, s_tab, C, P.d_ptr, P.d_entries);
+    k_bt_fill<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(n_sel, pf.d_q, pf.d_bits, pf.bm_words, C,
+                                                          P.d_ptr, P.d_entries);
     ++k;
   }
   ARA_TRY(cudaGetLastError());
@@ -378,7 +330,7 @@ void bt_free(ara_plan* P) {
   if (!P) return;
   if (P->exec) cudaGraphExecDestroy(P->exec);
   if (P->graph) cudaGraphDestroy(P->graph);
-  void* ptrs[] = {P->d_cnt, P->d_ptr, P->d_bsum, P->d_total, P->d_entries, P->d_queue};
+  void* ptrs[] = {P->d_ptr, P->d_bsum, P->d_total, P->d_entries, P->d_queue};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete P;
@@ -407,7 +359,6 @@ ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   int64_t bound = 0;
   for (int32_t l : P.sel) {
     const LayerConst& lc = pf.layers[l];
-    P.max_le = std::max(P.max_le, lc.elt_end - lc.elt_begin);
     for (int k = lc.elt_begin; k < lc.elt_end; ++k) {
       const int j = pf.layer_elts[k];
       bound += pf.rec_off[j + 1] - pf.rec_off[j];
@@ -417,12 +368,11 @@ ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   P.n_blocks = (C + BT_SCAN_BLOCK - 1) / BT_SCAN_BLOCK;
   size_t off = 0;
   auto take = [&](size_t n) { size_t o = (off + 255) / 256 * 256; off = o + n; return o; };
-  const size_t o_cnt = take(4 * (size_t)C), o_ptr = take(4 * (size_t)(C + 1));
+  const size_t o_ptr = take(4 * (size_t)(C + 1));
   const size_t o_bsum = take(4 * (size_t)P.n_blocks), o_tot = take(4), o_q = take(8);
   const size_t o_ent = take(8 * (size_t)std::max<int64_t>(bound, 1));
   char* buf = nullptr;
   ARA_TRY(cudaMallocAsync((void**)&buf, off, s));
-  P.d_cnt = (uint32_t*)(buf + o_cnt);
   P.d_ptr = (uint32_t*)(buf + o_ptr);
   P.d_bsum = (uint32_t*)(buf + o_bsum);
   P.d_total = (uint32_t*)(buf + o_tot);
@@ -430,12 +380,12 @@ ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   P.d_entries = (uint64_t*)(buf + o_ent);
   ara_status st = ARA_OK;
   {
-    LaunchScope ls(ARA_K_BATCHED, s, P.max_le + 6);
+    LaunchScope ls(ARA_K_BATCHED, s, 6);
     st = bt_prep(P, s, true, nullptr);
     if (st == ARA_OK) st = bt_stream(P, s);
   }
   cudaFreeAsync(buf, s);
-  P.d_cnt = P.d_ptr = P.d_bsum = P.d_total = nullptr;
+  P.d_ptr = P.d_bsum = P.d_total = nullptr;
   P.d_entries = nullptr;
   P.d_queue = nullptr;
   return st;
@@ -480,8 +430,6 @@ ara_status ara_plan_batched(ara_portfolio* pf_, int64_t n_trials, const int64_t*
     bt_free(P);
     return ARA_ERANGE;
   }
-  for (int32_t l : P->sel)
-    P->max_le = std::max(P->max_le, pf->layers[l].elt_end - pf->layers[l].elt_begin);
   DeviceGuard g(pf->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t C = pf->catalogue;
@@ -491,8 +439,7 @@ ara_status ara_plan_batched(ara_portfolio* pf_, int64_t n_trials, const int64_t*
     bt_free(P);
     return st;
   };
-  if (cudaMalloc(&P->d_cnt, 4 * (size_t)C) != cudaSuccess ||
-      cudaMalloc(&P->d_ptr, 4 * (size_t)(C + 1)) != cudaSuccess ||
+  if (cudaMalloc(&P->d_ptr, 4 * (size_t)(C + 1)) != cudaSuccess ||
       cudaMalloc(&P->d_bsum, 4 * (size_t)P->n_blocks) != cudaSuccess ||
       cudaMalloc(&P->d_total, 4) != cudaSuccess ||
       cudaMalloc(&P->d_queue, sizeof(unsigned long long)) != cudaSuccess)

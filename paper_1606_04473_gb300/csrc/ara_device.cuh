@@ -17,6 +17,47 @@ __device__ __forceinline__ double clamp_terms(double x, double R, double L) {
   return ex;
 }
 
+// Exact binary32 -> binary64 widening with integer instructions only (FP64 conversions issue at
+// a small fraction of the integer rate on this GPU).  From the IEEE 754 formats: binary32 has an
+// 8-bit exponent biased by 127 and a 23-bit fraction, binary64 an 11-bit exponent biased by 1023
+// and a 52-bit fraction.  A normal value keeps its significand (fraction << 29) and moves its
+// exponent by 1023 - 127 = 896; a subnormal f * 2^-149 with its leading bit at position p becomes
+// the normal 2^(p-149) * (f / 2^p); zeros keep their sign; infinities and NaNs map to the
+// all-ones exponent with the fraction shifted along.
+__device__ __forceinline__ double widen_f32(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint64_t sign = (uint64_t)(b >> 31) << 63;
+  const uint32_t ex = (b >> 23) & 0xffu;
+  const uint32_t fr = b & 0x7fffffu;
+  uint64_t bits;
+  if (ex == 0xffu) {
+    bits = sign | (0x7ffull << 52) | ((uint64_t)fr << 29);
+  } else if (ex != 0u) {
+    bits = sign | ((uint64_t)(ex + 896u) << 52) | ((uint64_t)fr << 29);
+  } else if (fr == 0u) {
+    bits = sign;
+  } else {
+    const int p = 31 - __clz((int)fr);
+    bits = sign | ((uint64_t)(p + 1023 - 149) << 52) | (((uint64_t)fr << (52 - p)) & ((1ull << 52) - 1));
+  }
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double to_f64(float x) { return widen_f32(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+
+// The same terms with the two clamps done on the bit patterns (only the subtraction is FP64):
+// for ex >= +0 and L >= +0 the IEEE order is the integer order of the bit patterns, and a
+// negative ex (sign bit set) becomes +0.  The result can differ from clamp_terms only in the
+// sign of a zero (ex = -0, or L = -0), which no sum of such terms can see.  Requires finite x
+// and R (no NaN).
+__device__ __forceinline__ double clamp_terms_bits(double x, double R, double L) {
+  const long long b = __double_as_longlong(__dsub_rn(x, R));
+  const long long lb = __double_as_longlong(L);
+  long long r = b < 0 ? 0 : b;
+  r = r > lb ? lb : r;
+  return __longlong_as_double(r);
+}
+
 struct U128 {
   uint64_t lo, hi;
 };

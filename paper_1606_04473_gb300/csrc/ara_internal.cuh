@@ -135,16 +135,19 @@ struct YltArgs {
 
 ara_status launch_fold(Portfolio& pf, int32_t n_sel, const int32_t* sel_host, int32_t flags,
                        cudaStream_t s);
-// Fold into caller-chosen outputs (see k_fold): used by the adjoint for occurrence regimes.
+// Fold into caller-chosen outputs (see k_fold): used by the adjoint for occurrence regimes and
+// by the batched plan for every selected layer at once.
 struct FoldOutHost {
   uint64_t* q = nullptr;
   uint32_t* bits = nullptr;
   uint8_t* regime = nullptr;
   int64_t q_stride = 0, bits_stride = 0, regime_stride = 0;
   int by_slot = 0, f64_table = 0, bits_from_regime = 0;
+  int nonzero_only = 0;   // store only the non-zero entries of q (readers consult the bitmap)
 };
+// counted = false: the caller counts and times the launch within its own scope.
 ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
-                          const FoldOutHost& o, cudaStream_t s);
+                          const FoldOutHost& o, cudaStream_t s, bool counted = true);
 ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s);
 ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s);
 ara_status build_dense(Portfolio& pf, cudaStream_t s);

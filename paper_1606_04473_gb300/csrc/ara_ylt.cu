@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <optional>
 
 #include "ara_device.cuh"
 
@@ -29,10 +30,10 @@ struct SelList {
 
 // ------------------------------------------------------------------------------------------
 // Fold: o(e) = C(sum_j C(x_j(e); R_j, L_j); OccR, OccL) for every catalogue event e of one
-// tile, for the layer sel.idx[blockIdx.y].  The ELT sum runs in the layer's ELT order (one
-// pass per ELT, separated by barriers), the order of the FP64 reference.  Output: the fixed
-// point q(e) = round(o(e) * 2^frac_bits) (or the FP64 bits of o(e) when f64_table), and the
-// hit bitmap (bit e set iff the stored value is non-zero).
+// tile, for the layer sel.idx[blockIdx.y].  The ELT sum runs in the layer's ELT order, the
+// order of the FP64 reference.  Output: the fixed point q(e) = round(o(e) * 2^frac_bits) (or the
+// FP64 bits of o(e) when f64_table), and the hit bitmap (bit e set iff the stored value is
+// non-zero).
 // ------------------------------------------------------------------------------------------
 struct FoldOut {
   uint64_t* q;          // table, or nullptr
@@ -42,6 +43,7 @@ struct FoldOut {
   int by_slot;          // outputs indexed by blockIdx.y (else by layer index)
   int f64_table;        // store the FP64 bits of o(e) instead of fixed point
   int bits_from_regime; // bitmap bit = (regime != 0) instead of (stored value != 0)
+  int nonzero_only;     // store only the non-zero table entries (readers consult the bitmap)
 };
 
 constexpr int FOLD_GROUP = 32;     // ELTs whose record ranges are searched together
@@ -54,11 +56,14 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ tile_rec, int64_t n_tiles,
        const LossT* __restrict__ rec_loss, const double* __restrict__ elt_ret,
        const double* __restrict__ elt_lim, const int32_t* __restrict__ layer_elts,
        const LayerConst* __restrict__ layers, SelList sel, FoldOut out) {
+  static_assert(FOLD_TILE % FOLD_THREADS == 0 && FOLD_TILE <= 65536, "tile layout");
   __shared__ double s[FOLD_TILE];
-  __shared__ int32_t list[FOLD_TILE];        // staged record offsets, then the touched events
   __shared__ double rx[FOLD_REC];            // staged records after the ELT terms
+  __shared__ uint16_t rev[FOLD_REC];         // their events, relative to the tile
+  __shared__ uint16_t touched[FOLD_TILE];    // events whose sum became non-zero, in that order
   __shared__ uint8_t reg[FOLD_TILE];
-  __shared__ int64_t lo[FOLD_GROUP], hi[FOLD_GROUP];
+  __shared__ int64_t lo[FOLD_GROUP];
+  __shared__ double eR[FOLD_GROUP], eL[FOLD_GROUP];
   __shared__ int32_t cnt_off[FOLD_GROUP + 1];
   __shared__ int32_t n_batch;
   __shared__ int32_t n_list;
@@ -67,24 +72,34 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ tile_rec, int64_t n_tiles,
   const LayerConst lc = layers[layer];
   const int64_t t0 = (int64_t)blockIdx.x * FOLD_TILE;
   const int64_t t1 = min(t0 + (int64_t)FOLD_TILE, catalogue);
-  const int lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < FOLD_TILE; i += blockDim.x) { s[i] = 0.0; reg[i] = 0; }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool want_regime = out.regime != nullptr || out.bits_from_regime;
+#pragma unroll
+  for (int i = threadIdx.x; i < FOLD_TILE; i += FOLD_THREADS) s[i] = 0.0;
+  if (want_regime)
+    for (int i = threadIdx.x; i < FOLD_TILE; i += FOLD_THREADS) reg[i] = 0;
+  int n_touched = 0;   // kept by warp 0
   if (threadIdx.x == 0) n_list = 0;
-  // The layer's ELTs in order, in batches: the record ranges of up to FOLD_GROUP ELTs within
-  // this tile are read from the portfolio's tile index, the records of the longest prefix of them
-  // that fits FOLD_REC are loaded at once with their ELT terms applied, and then added into
-  // the tile one ELT after the other (IDs are unique within an ELT, so one ELT's records never
-  // collide), which keeps the FP64 sum in the layer's ELT order.
+  // The layer's ELTs in order, in batches: warp 0 reads the record ranges of up to FOLD_GROUP
+  // ELTs within this tile from the portfolio's tile index, and the batch is the longest prefix
+  // of them whose records fit FOLD_REC.  All threads stage the batch's records with their ELT
+  // terms applied (one record per thread, so that the FP64 instructions run on full warps);
+  // then warp 0 adds them into the tile one ELT after the other, which keeps the FP64 sum in
+  // the layer's ELT order (IDs are unique within an ELT, so the lanes never collide within one
+  // ELT).
   for (int k0 = lc.elt_begin; k0 < lc.elt_end;) {
     const int G = min(FOLD_GROUP, lc.elt_end - k0);
-    if (threadIdx.x < G) {
-      const int64_t* tr = tile_rec + (int64_t)layer_elts[k0 + threadIdx.x] * (n_tiles + 1) + blockIdx.x;
-      lo[threadIdx.x] = tr[0];
-      hi[threadIdx.x] = tr[1];
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {   // counts -> offsets; the batch is the longest prefix that fits
-      const int32_t c = lane < G ? (int32_t)(hi[lane] - lo[lane]) : 0;
+    if (warp == 0) {
+      int32_t c = 0;
+      if (lane < G) {
+        const int j = layer_elts[k0 + lane];
+        const int64_t* tr = tile_rec + (int64_t)j * (n_tiles + 1) + blockIdx.x;
+        const int64_t a = tr[0];
+        lo[lane] = a;
+        c = (int32_t)(tr[1] - a);
+        eR[lane] = elt_ret[j];
+        eL[lane] = elt_lim[j];
+      }
       int32_t incl = c;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -94,53 +109,75 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ tile_rec, int64_t n_tiles,
       cnt_off[lane + 1] = incl;
       if (lane == 0) cnt_off[0] = 0;
       const unsigned fit = __ballot_sync(FULL, lane < G && incl <= FOLD_REC);
-      if (lane == 0) n_batch = fit ? 32 - __clz((int)fit) : 1;  // a single ELT always fits
+      if (lane == 0) n_batch = fit ? 32 - __clz((int)fit) : 1;  // one ELT always fits a tile
     }
     __syncthreads();
     const int nb = n_batch;
     const int32_t total = cnt_off[nb];
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-      int g = 0;
-      while (cnt_off[g + 1] <= i) ++g;
-      const int j = layer_elts[k0 + g];
+    for (int i = threadIdx.x; i < total; i += FOLD_THREADS) {
+      int g = 0;   // the batch ELT of staged record i: the last g < nb with cnt_off[g] <= i
+#pragma unroll
+      for (int step = FOLD_GROUP / 2; step > 0; step >>= 1)
+        if (g + step < nb && cnt_off[g + step] <= i) g += step;
       const int64_t r = lo[g] + (i - cnt_off[g]);
-      list[i] = (int32_t)(rec_ids[r] - t0);
-      rx[i] = clamp_terms((double)rec_loss[r], elt_ret[j], elt_lim[j]);
+      rev[i] = (uint16_t)(rec_ids[r] - t0);
+      rx[i] = clamp_terms_bits(to_f64(rec_loss[r]), eR[g], eL[g]);
     }
     __syncthreads();
-    for (int g = 0; g < nb; ++g) {
-      for (int i = cnt_off[g] + threadIdx.x; i < cnt_off[g + 1]; i += blockDim.x)
-        s[list[i]] = __dadd_rn(s[list[i]], rx[i]);
-      __syncthreads();
+    if (warp == 0) {
+      for (int g = 0; g < nb; ++g) {
+        const int32_t b1 = cnt_off[g + 1];
+        for (int i = cnt_off[g] + lane; i - lane < b1; i += 32) {
+          bool first = false;
+          int e = 0;
+          if (i < b1) {
+            e = rev[i];
+            const double old = s[e], x = rx[i];
+            s[e] = __dadd_rn(old, x);
+            // Sums only grow (the ELT terms give x >= 0), so an event turns non-zero exactly
+            // once: when a zero sum meets a non-zero x (tested on the bits, off the add's path).
+            first = ((uint64_t)__double_as_longlong(old) << 1) == 0ull &&
+                    ((uint64_t)__double_as_longlong(x) << 1) != 0ull;
+          }
+          const unsigned m = __ballot_sync(FULL, first);
+          if (first) touched[n_touched + __popc(m & ((1u << lane) - 1u))] = (uint16_t)e;
+          n_touched += __popc(m);
+        }
+        __syncwarp();
+      }
+      if (lane == 0) n_list = n_touched;
     }
+    // No barrier here: the next batch's first barrier keeps the other warps' staging away from
+    // the records warp 0 is still adding.
     k0 += nb;
   }
-  // Compact the touched events so the FP64 occurrence clamp runs on full warps only.
-  for (int i = threadIdx.x; i < (int)(t1 - t0); i += blockDim.x)
-    if (s[i] != 0.0) list[atomicAdd(&n_list, 1)] = i;
   __syncthreads();
+  const int n_nz = n_list;
   uint64_t* sq = reinterpret_cast<uint64_t*>(s);  // in place: untouched entries are +0.0 == 0
-  for (int p = threadIdx.x; p < n_list; p += blockDim.x) {
-    const int i = list[p];
+  for (int p = threadIdx.x; p < n_nz; p += FOLD_THREADS) {
+    const int i = touched[p];
     const double sv = s[i];
     const double o = clamp_terms(sv, lc.occ_ret, lc.occ_lim);
-    const double ex = __dsub_rn(sv, lc.occ_ret);
-    reg[i] = (ex > 0.0 && ex < lc.occ_lim) ? 1 : (ex > lc.occ_lim ? 2 : 0);
+    if (want_regime) {
+      const double ex = __dsub_rn(sv, lc.occ_ret);
+      reg[i] = (ex > 0.0 && ex < lc.occ_lim) ? 1 : (ex > lc.occ_lim ? 2 : 0);
+    }
     sq[i] = out.f64_table ? (uint64_t)__double_as_longlong(o) : __double2ull_rn(__dmul_rn(o, lc.scale));
   }
   __syncthreads();
   uint64_t* qo = out.q ? out.q + slot * out.q_stride : nullptr;
   uint32_t* bo = out.bits + slot * out.bits_stride;
   uint8_t* ro = out.regime ? out.regime + slot * out.regime_stride : nullptr;
-  for (int i = threadIdx.x; i < FOLD_TILE; i += blockDim.x) {  // FOLD_TILE % blockDim == 0
+#pragma unroll 4
+  for (int i = threadIdx.x; i < FOLD_TILE; i += FOLD_THREADS) {
     const int64_t e = t0 + i;
     const bool in = e < t1;
     const uint64_t q = in ? sq[i] : 0ull;
-    const uint8_t r = in ? reg[i] : 0;
-    if (in && qo) qo[e] = q;
+    const uint8_t r = (in && want_regime) ? reg[i] : 0;
+    if (in && qo && (q != 0ull || !out.nonzero_only)) qo[e] = q;
     if (in && ro) ro[e] = r;
     const unsigned b = __ballot_sync(FULL, out.bits_from_regime ? r != 0 : q != 0ull);
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
       const int64_t w = (t0 + (i & ~31)) >> 5;
       if (w < out.bits_stride) bo[w] = b;
     }
@@ -794,7 +831,7 @@ ara_status build_dense(Portfolio& pf, cudaStream_t s) {
 }
 
 ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
-                          const FoldOutHost& o, cudaStream_t s) {
+                          const FoldOutHost& o, cudaStream_t s, bool counted) {
   FoldOut out;
   out.q = o.q;
   out.bits = o.bits;
@@ -805,6 +842,7 @@ ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
   out.by_slot = o.by_slot;
   out.f64_table = o.f64_table;
   out.bits_from_regime = o.bits_from_regime;
+  out.nonzero_only = o.nonzero_only;
   for (int32_t b = 0; b < n_sel; b += MAX_SEL) {
     SelList sl;
     sl.n = min(MAX_SEL, n_sel - b);
@@ -816,7 +854,8 @@ ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
       if (ob.regime) ob.regime += (int64_t)b * ob.regime_stride;
     }
     dim3 grid((unsigned)((pf.catalogue + FOLD_TILE - 1) / FOLD_TILE), sl.n);
-    LaunchScope ls(ARA_K_FOLD, s);
+    std::optional<LaunchScope> ls;
+    if (counted) ls.emplace(ARA_K_FOLD, s);
     if (pf.d_rec_loss32)
       k_fold<float><<<grid, FOLD_THREADS, 0, s>>>(pf.catalogue, pf.d_tile_rec, pf.n_tiles, pf.d_rec_ids,
                                                   pf.d_rec_loss32, pf.d_elt_ret, pf.d_elt_lim,

@@ -434,3 +434,43 @@ def test_occurrence_basis_oep(mid):
         assert np.all(err <= 1e-6 * np.abs(want[l]))
     with pytest.raises(ara.AraError):
         g.run_ylt(*dev(yet), flags=ara.ARA_RUN_OEP | ara.ARA_RUN_LDG)
+
+
+def test_fp32_storage_widens_exactly():
+    """FP32 loss storage gives the same YLT, bit for bit, as FP64 storage of the same values:
+    the fold widens binary32 losses to binary64 exactly, for zeros of both signs, subnormals
+    with every leading-bit position, normals across the whole exponent range and the largest
+    finite float.  Terms are open (zero retentions, infinite limits) so that every loss reaches
+    the sums, and each layer's fixed point resolves its own smallest losses."""
+    rng = np.random.default_rng(41)
+    C = 4096
+    sub = np.array([0x00000000, 0x80000000, 0x00000001, 0x00000003, 0x007fffff, 0x00400000,
+                    0x00000400, 0x00800000, 0x00c00000], dtype=np.uint32)
+    lead = rng.integers(0, 23, 400).astype(np.uint32)                       # subnormals
+    frac = (np.uint32(1) << lead) | (rng.integers(0, 1 << 23, 400).astype(np.uint32) &
+                                      ((np.uint32(1) << lead) - np.uint32(1)))
+    small = (rng.integers(1, 11, 200).astype(np.uint32) << 23) | rng.integers(0, 1 << 23, 200).astype(np.uint32)
+    sub = np.concatenate([sub, frac, small])
+    wide = np.concatenate([np.array([0x7f7fffff, 0x3f800000, 0x00800000], dtype=np.uint32),
+                           (rng.integers(1, 255, 700).astype(np.uint32) << 23) |
+                           rng.integers(0, 1 << 23, 700).astype(np.uint32)])
+    ordinary = rng.lognormal(11.0, 2.0, 500).astype(np.float32)
+    tabs = [sub.view(np.float32), wide.view(np.float32), ordinary]
+    ids = [np.sort(rng.choice(C, size=t.size, replace=False)).astype(np.int32) for t in tabs]
+    losses = [t.astype(np.float64)[np.argsort(rng.random(t.size))] for t in tabs]
+    layers = [[0], [1], [2, 0], [0, 1, 2]]
+    z, inf = np.zeros(len(layers)), np.full(len(layers), INF)
+    counts = synth.poisson_counts(41, 60.0, 3001)
+    yet = synth.make_yet(41, counts, C, with_timestamps=False)
+    off, ev = dev(yet)
+    out = []
+    for f32 in (True, False):
+        pf = synth.Portfolio(C, ids, losses, np.zeros(3), np.full(3, INF), layers, z, inf, z, inf,
+                             losses_f32=f32)
+        g = ara.Portfolio.from_tables(pf)
+        out.append(g.run_ylt(off, ev))
+        torch.cuda.synchronize()
+        g.check()
+        g.close()
+    assert torch.equal(out[0], out[1])
+    assert (out[0][0] > 0).any() and (out[0][1] > 0).any()
