@@ -11,10 +11,10 @@
 //   3. event-major CSR rows: for event e, its (layer slot, q) pairs in layer order, packed as
 //      slot << 56 | q (q < 2^55); q is read only where the bitmap bit is set.
 // Stream (persistent, atomic trial queue for uneven trial lengths): a warp takes trials from the
-// queue; for every occurrence it walks the event's CSR row and adds each q to the warp's
-// per-layer accumulator in shared memory (exact 128-bit: 64-bit atomic add with carry); at the
-// end of a trial its lanes apply every layer's aggregate terms to the exact sums and write the
-// YLT entries.  Integer sums make the result independent of the order of the additions and
+// queue; for every 32 occurrences it joins their events' CSR rows into one list, walks it 32
+// entries at a time and adds each q to the warp's per-layer accumulator in shared memory (exact
+// 128-bit: 64-bit atomic add with carry); at the end of a trial its lanes apply every layer's
+// aggregate terms to the exact sums and write the YLT entries.  Integer sums make the result independent of the order of the additions and
 // bitwise equal to the single-layer path.
 
 #include <algorithm>
@@ -108,17 +108,19 @@ __global__ void k_bt_scan_add(uint32_t* __restrict__ ptr, int64_t n, const uint3
 }
 
 // ------------------------------------------------------------------------------------------
-// 3. CSR rows: one thread per event, layers in slot order (deterministic layout)
+// 3. CSR rows: one thread per event, layers in slot order (deterministic layout), and the
+//    event's row descriptor (first entry | length << 32)
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_bt_fill(int32_t n_sel, const uint64_t* __restrict__ q, const uint32_t* __restrict__ bits,
           int64_t bits_stride, int64_t catalogue, const uint32_t* __restrict__ ptr,
-          uint64_t* __restrict__ entries) {
+          uint64_t* __restrict__ entries, uint64_t* __restrict__ rows) {
   constexpr int U = 8;   // slots per step: their bitmap words and table entries load together
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= catalogue) return;
   uint32_t pos = ptr[e];
   const uint32_t end = ptr[e + 1];
+  rows[e] = (uint64_t)pos | ((uint64_t)(end - pos) << 32);   // one 8-byte gather per occurrence
   const uint32_t* b = bits + (e >> 5);
   const int sh = (int)(e & 31);
   for (int i0 = 0; i0 < n_sel && pos < end; i0 += U) {
@@ -147,7 +149,7 @@ struct BtStream {
   int64_t n_events;
   const int32_t* ids;
   uint32_t catalogue;
-  const uint32_t* row_ptr;     // [catalogue + 1]
+  const uint64_t* rows;        // [catalogue]: first entry | length << 32
   const uint64_t* entries;
   int32_t n_sel;
   const LayerConst* layers;    // device, indexed by layer id
@@ -184,31 +186,44 @@ k_bt_stream(BtStream p) {
     for (int64_t t = (int64_t)t0; t < t1; ++t) {
       int64_t beg = __ldg(p.offsets + t), end = __ldg(p.offsets + t + 1);
       if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; beg = end = 0; }
-      for (int64_t i0 = beg; i0 < end; i0 += 128) {
-        int ev[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int64_t i = i0 + 32 * u + lane;
-          ev[u] = i < end ? __ldcs(p.ids + i) : -1;
+      // 32 occurrences at a time.  Their rows are laid end to end (a warp scan of the lengths)
+      // and the warp walks the joined list 32 entries per step: every lane has an entry, and
+      // the lanes of one row read consecutive words.  The lane owning item x is the first lane
+      // whose inclusive length sum exceeds x (a 5-step search over the lanes' sums).
+      for (int64_t i0 = beg; i0 < end; i0 += 32) {
+        const int64_t i = i0 + lane;
+        uint32_t rb = 0, len = 0;
+        if (i < end) {
+          const uint32_t e = (uint32_t)__ldcs(p.ids + i);
+          if (e < p.catalogue) {
+            const uint64_t ri = __ldg(p.rows + e);
+            rb = (uint32_t)ri;
+            len = (uint32_t)(ri >> 32);
+          } else {
+            bad_id = true;
+          }
         }
+        uint32_t incl = len;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int64_t i = i0 + 32 * u + lane;
-          if (i >= end) continue;
-          const uint32_t e = (uint32_t)ev[u];
-          if (e >= p.catalogue) { bad_id = true; continue; }
-          const uint32_t rb = __ldg(p.row_ptr + e), re = __ldg(p.row_ptr + e + 1);
-          // Rows list layers in slot order, so the lanes' k-th entries would crowd onto the same
-          // few slots and their shared-memory atomics onto the same words.  Each lane starts at
-          // its own place in the row (floor(lane * len / 32)) and wraps around; integer sums do
-          // not depend on the order.
-          const uint32_t len = re - rb;
-          uint32_t r = rb + (((uint32_t)lane * len) >> 5);
-          for (uint32_t k = 0; k < len; ++k) {
-            const uint64_t x = __ldg(p.entries + r);
-            const int s = (int)(x >> 56);
-            smem_add_u128(&lo[s], &hi[s], x & ((1ull << 56) - 1));
-            if (++r == re) r = rb;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t base = rb - (incl - len);   // entry of item x (in this lane's row): base + x
+        for (uint32_t w0 = 0; w0 < total; w0 += 32) {
+          const uint32_t x = w0 + (uint32_t)lane;
+          int own = 0;
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t v = __shfl_sync(0xffffffffu, incl, own + step - 1);
+            if (v <= x) own += step;
+          }
+          const uint32_t b = __shfl_sync(0xffffffffu, base, own);
+          if (x < total) {
+            const uint64_t v = __ldg(p.entries + (uint32_t)(b + x));
+            const int s = (int)(v >> 56);
+            smem_add_u128(&lo[s], &hi[s], v & ((1ull << 56) - 1));
           }
         }
       }
@@ -247,6 +262,7 @@ struct ara_plan {
   double* d_ylt = nullptr;
   uint8_t* d_reg = nullptr;
   uint32_t* d_ptr = nullptr;
+  uint64_t* d_rows = nullptr;
   uint32_t* d_bsum = nullptr;
   uint32_t* d_total = nullptr;
   uint64_t* d_entries = nullptr;
@@ -281,7 +297,7 @@ ara_status bt_prep(ara_plan& P, cudaStream_t s, bool fill, int* n_kernels) {
   int k = 4;
   if (fill) {
     k_bt_fill<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(n_sel, pf.d_q, pf.d_bits, pf.bm_words, C,
-                                                          P.d_ptr, P.d_entries);
+                                                          P.d_ptr, P.d_entries, P.d_rows);
     ++k;
   }
   ARA_TRY(cudaGetLastError());
@@ -307,7 +323,7 @@ ara_status bt_stream(ara_plan& P, cudaStream_t s) {
   bs.n_events = P.n_events;
   bs.ids = P.d_ids;
   bs.catalogue = (uint32_t)P.pf->catalogue;
-  bs.row_ptr = P.d_ptr;
+  bs.rows = P.d_rows;
   bs.entries = P.d_entries;
   bs.n_sel = (int32_t)P.sel.size();
   bs.layers = P.pf->d_layers;
@@ -330,7 +346,7 @@ void bt_free(ara_plan* P) {
   if (!P) return;
   if (P->exec) cudaGraphExecDestroy(P->exec);
   if (P->graph) cudaGraphDestroy(P->graph);
-  void* ptrs[] = {P->d_ptr, P->d_bsum, P->d_total, P->d_entries, P->d_queue};
+  void* ptrs[] = {P->d_ptr, P->d_rows, P->d_bsum, P->d_total, P->d_entries, P->d_queue};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete P;
@@ -368,12 +384,13 @@ ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   P.n_blocks = (C + BT_SCAN_BLOCK - 1) / BT_SCAN_BLOCK;
   size_t off = 0;
   auto take = [&](size_t n) { size_t o = (off + 255) / 256 * 256; off = o + n; return o; };
-  const size_t o_ptr = take(4 * (size_t)(C + 1));
+  const size_t o_ptr = take(4 * (size_t)(C + 1)), o_rows = take(8 * (size_t)C);
   const size_t o_bsum = take(4 * (size_t)P.n_blocks), o_tot = take(4), o_q = take(8);
   const size_t o_ent = take(8 * (size_t)std::max<int64_t>(bound, 1));
   char* buf = nullptr;
   ARA_TRY(cudaMallocAsync((void**)&buf, off, s));
   P.d_ptr = (uint32_t*)(buf + o_ptr);
+  P.d_rows = (uint64_t*)(buf + o_rows);
   P.d_bsum = (uint32_t*)(buf + o_bsum);
   P.d_total = (uint32_t*)(buf + o_tot);
   P.d_queue = (unsigned long long*)(buf + o_q);
@@ -386,6 +403,7 @@ ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   }
   cudaFreeAsync(buf, s);
   P.d_ptr = P.d_bsum = P.d_total = nullptr;
+  P.d_rows = nullptr;
   P.d_entries = nullptr;
   P.d_queue = nullptr;
   return st;
@@ -440,6 +458,7 @@ ara_status ara_plan_batched(ara_portfolio* pf_, int64_t n_trials, const int64_t*
     return st;
   };
   if (cudaMalloc(&P->d_ptr, 4 * (size_t)(C + 1)) != cudaSuccess ||
+      cudaMalloc(&P->d_rows, 8 * (size_t)std::max<int64_t>(C, 1)) != cudaSuccess ||
       cudaMalloc(&P->d_bsum, 4 * (size_t)P->n_blocks) != cudaSuccess ||
       cudaMalloc(&P->d_total, 4) != cudaSuccess ||
       cudaMalloc(&P->d_queue, sizeof(unsigned long long)) != cudaSuccess)
