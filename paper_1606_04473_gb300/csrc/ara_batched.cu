@@ -190,19 +190,23 @@ k_bt_stream(BtStream p) {
       // and the warp walks the joined list 32 entries per step: every lane has an entry, and
       // the lanes of one row read consecutive words.  The lane owning item x is the first lane
       // whose inclusive length sum exceeds x (a 5-step search over the lanes' sums).
+      // Software pipeline over the rounds: the row descriptors of round k + 1 and the event IDs
+      // of round k + 2 are in flight while round k's entries are walked.
+      auto load_id = [&](int64_t i) -> int64_t {   // -1 past the trial's end
+        return i < end ? (int64_t)(uint32_t)__ldcs(p.ids + i) : (int64_t)-1;
+      };
+      auto load_row = [&](int64_t e) -> uint64_t {
+        if (e < 0) return 0ull;
+        if (e >= (int64_t)p.catalogue) { bad_id = true; return 0ull; }
+        return __ldg(p.rows + e);
+      };
+      uint64_t ri_cur = load_row(load_id(beg + lane));
+      int64_t e_nxt = load_id(beg + 32 + lane);
       for (int64_t i0 = beg; i0 < end; i0 += 32) {
-        const int64_t i = i0 + lane;
-        uint32_t rb = 0, len = 0;
-        if (i < end) {
-          const uint32_t e = (uint32_t)__ldcs(p.ids + i);
-          if (e < p.catalogue) {
-            const uint64_t ri = __ldg(p.rows + e);
-            rb = (uint32_t)ri;
-            len = (uint32_t)(ri >> 32);
-          } else {
-            bad_id = true;
-          }
-        }
+        const uint64_t ri_nxt = load_row(e_nxt);
+        e_nxt = load_id(i0 + 64 + lane);
+        const uint32_t rb = (uint32_t)ri_cur, len = (uint32_t)(ri_cur >> 32);
+        ri_cur = ri_nxt;
         uint32_t incl = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {

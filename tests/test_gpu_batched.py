@@ -113,3 +113,30 @@ def test_plan_with_many_layers_equals_single_layer_path():
     assert np.all(err <= 1e-6 * np.abs(ref) + 1e-12 * np.abs(agg))
     plan.close()
     g.close()
+
+
+def test_plan_skips_and_reports_out_of_range_ids(case):
+    """Event IDs outside the catalogue (the catalogue size, -1, 2^31 - 1) at the first, the
+    33rd and the 65th occurrence of a trial and at its last: the plan reports ARA_EDATA, and
+    every other trial's YLT equals the single-layer path's bit for bit."""
+    pf, yet, _, _ = case
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    counts = np.diff(yet.offsets)
+    t = int(np.nonzero(counts >= 100)[0][0])
+    b = int(yet.offsets[t])
+    bad = ids.clone()
+    for k, v in ((0, pf.catalogue), (32, -1), (64, 2**31 - 1), (int(counts[t]) - 1, pf.catalogue + 7)):
+        bad[b + k] = v
+    single = g.run_ylt(off, ids).clone()
+    g.check()
+    plan = ara.BatchedPlan(g, off, bad, autotune=False)
+    y = plan.launch()
+    with pytest.raises(ara.AraError) as e:
+        g.check()
+    assert e.value.status == ara.ARA_EDATA
+    keep = torch.ones(yet.n_trials, dtype=torch.bool, device="cuda")
+    keep[t] = False
+    assert torch.equal(y[:, keep], single[:, keep])
+    plan.close()
+    g.close()
