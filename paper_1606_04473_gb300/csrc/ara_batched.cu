@@ -158,6 +158,7 @@ struct BtStream {
   uint8_t* regimes;            // or nullptr
   unsigned long long* queue;   // trial counter (zeroed before the launch)
   int32_t trials_per_grab;
+  int32_t copies;              // accumulator copies per warp: 1, 2 or 4
   uint32_t* err;
 };
 
@@ -169,12 +170,17 @@ __device__ __forceinline__ void smem_add_u128(unsigned long long* lo, unsigned l
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_bt_stream(BtStream p) {
-  extern __shared__ __align__(16) unsigned long long bt_acc[];   // [WARPS][2][n_sel]
+  extern __shared__ __align__(16) unsigned long long bt_acc[];   // [WARPS][copies][2][n_sel]
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = p.n_sel;
-  unsigned long long* lo = bt_acc + (int64_t)wid * 2 * ns;
-  unsigned long long* hi = lo + ns;
-  for (int i = lane; i < 2 * ns; i += 32) lo[i] = 0ull;
+  // Each group of 32 / copies lanes has its own copy of the warp's accumulators, so that lanes
+  // of different groups never add to the same word; the copies are summed exactly at the end of
+  // a trial.
+  const int nc = p.copies;
+  unsigned long long* const acc0 = bt_acc + (int64_t)wid * 2 * nc * ns;
+  unsigned long long* const lo = acc0 + (int64_t)(lane / (32 / nc)) * 2 * ns;
+  unsigned long long* const hi = lo + ns;
+  for (int i = lane; i < 2 * nc * ns; i += 32) acc0[i] = 0ull;
   __syncwarp();
   bool bad_id = false, bad_off = false;
   while (true) {
@@ -234,9 +240,13 @@ k_bt_stream(BtStream p) {
       __syncwarp();
       // aggregate terms of every layer on the exact sums; reset the accumulators
       for (int i = lane; i < ns; i += 32) {
-        U128 S{lo[i], hi[i]};
-        lo[i] = 0ull;
-        hi[i] = 0ull;
+        U128 S{0ull, 0ull};
+        for (int c = 0; c < nc; ++c) {
+          unsigned long long* const a = acc0 + (int64_t)c * 2 * ns;
+          add_u128(S, a[i], a[ns + i]);
+          a[i] = 0ull;
+          a[ns + i] = 0ull;
+        }
         const LayerConst lc = p.layers[p.sel.layer[i]];
         uint8_t reg;
         const double y = AccOps<U128>::finish(S, lc, reg);
@@ -272,7 +282,7 @@ struct ara_plan {
   uint64_t* d_entries = nullptr;
   unsigned long long* d_queue = nullptr;
   int64_t n_blocks = 0;
-  int warps = 16, ctas_per_sm = 2, tpg = 2;
+  int warps = 16, ctas_per_sm = 2, tpg = 2, copies = 2;
   double tuned_ms = 0.0;
   int n_kernels = 0;
   cudaGraph_t graph = nullptr;
@@ -311,7 +321,7 @@ ara_status bt_prep(ara_plan& P, cudaStream_t s, bool fill, int* n_kernels) {
 
 template <int W>
 ara_status bt_launch_w(ara_plan& P, const BtStream& bs, cudaStream_t s) {
-  const int smem = W * 2 * (int)P.sel.size() * 8;
+  const int smem = W * 2 * P.copies * (int)P.sel.size() * 8;
   const auto fn = k_bt_stream<W>;
   if (smem > 48 * 1024)
     ARA_TRY(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -337,6 +347,7 @@ ara_status bt_stream(ara_plan& P, cudaStream_t s) {
   bs.regimes = P.d_reg;
   bs.queue = P.d_queue;
   bs.trials_per_grab = P.tpg;
+  bs.copies = P.copies;
   bs.err = P.pf->d_err;
   ARA_TRY(cudaMemsetAsync(P.d_queue, 0, sizeof(unsigned long long), s));
   switch (P.warps) {
@@ -484,16 +495,19 @@ ara_status ara_plan_batched(ara_portfolio* pf_, int64_t n_trials, const int64_t*
     const int cand_w[] = {8, 16, 32};
     const int cand_c[] = {1, 2, 4};
     const int cand_t[] = {1, 4};
+    const int cand_k[] = {1, 2, 4};
     float best = 1e30f;
-    int bw = P->warps, bc = P->ctas_per_sm, bt = P->tpg;
+    int bw = P->warps, bc = P->ctas_per_sm, bt = P->tpg, bk = P->copies;
     for (int w : cand_w)
       for (int c : cand_c)
-        for (int t : cand_t) {
-          const int64_t smem = (int64_t)w * 2 * (int64_t)P->sel.size() * 8;
+        for (int t : cand_t)
+          for (int k : cand_k) {
+          const int64_t smem = (int64_t)w * 2 * k * (int64_t)P->sel.size() * 8;
           if (smem * c > (int64_t)pf->max_smem_block || w * 32 * c > 2048) continue;
           P->warps = w;
           P->ctas_per_sm = c;
           P->tpg = t;
+          P->copies = k;
           float ms = 0.f, tot = 0.f;
           for (int rep = 0; rep < 3; ++rep) {
             cudaEventRecord(a, s);
@@ -507,13 +521,14 @@ ara_status ara_plan_batched(ara_portfolio* pf_, int64_t n_trials, const int64_t*
             cudaEventElapsedTime(&ms, a, b);
             if (rep > 0) tot += ms;
           }
-          if (tot / 2 < best) { best = tot / 2; bw = w; bc = c; bt = t; }
+          if (tot / 2 < best) { best = tot / 2; bw = w; bc = c; bt = t; bk = k; }
         }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     P->warps = bw;
     P->ctas_per_sm = bc;
     P->tpg = bt;
+    P->copies = bk;
     P->tuned_ms = best;
   }
   // capture the whole run into a graph on a private stream
