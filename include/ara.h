@@ -406,8 +406,11 @@ ARA_API ara_status ara_risk_metrics_async(const double* d_ylt, int64_t n_trials,
  * the process exits).  Arguments, results and errors are those of ara_risk_metrics, plus:
  *   - a request whose scratch (about 8 KiB per layer per requested PML/TVaR level) does not
  *     fit in the array returns ARA_ERANGE and launches nothing;
- *   - the first call on each device looks up the array's device address on that device
- *     (with it current); make that first call before any stream capture begins there;
+ *   - every call looks up the array's device address on the current device (a cheap host
+ *     query), so the address stays right after the device's context is torn down and
+ *     recreated (cudaDeviceReset reloads the library's module, possibly elsewhere);
+ *   - the call waits for `stream` before it returns, also when a result copy fails, so no
+ *     copy queued by it lands in the caller's buffers afterwards;
  *   - every call reuses the same array and clears the part it needs first; calls whose
  *     work overlaps on a device (other streams, other host threads) race on it and must be
  *     serialised by the caller.

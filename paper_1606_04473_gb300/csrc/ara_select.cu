@@ -636,30 +636,21 @@ extern "C" ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, in
 
 // ------------------------------------------------------------------------------------------
 // Allocation-free variant: the selection scratch lives in a fixed device array of this
-// library.  Host code cannot use the array's name as a device address, so its address is
-// looked up once per device (with that device current) and cached.
+// library.  Host code cannot use the array's name as a device address, so every call looks the
+// address up on the current device (with that device current).  The lookup is a cheap host
+// query; not caching it keeps the address right after anything that tears down and recreates
+// the device's primary context (cudaDeviceReset), which reloads the module elsewhere.
 // ------------------------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_select_scratch[ARA_STATIC_SELECT_BYTES];
 
-namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
-void* g_static_scratch[kMaxDevices];
-}  // namespace
-
-static ara_status static_scratch(int dev, void** out) {
-  if (dev < 0 || dev >= kMaxDevices) return ARA_ECUDA;
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_scratch[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_select_scratch);
-    if (e != cudaSuccess || !p) {
-      note_cuda_error(e, "cudaGetSymbolAddress(g_select_scratch)", __FILE__, __LINE__);
-      return ARA_ECUDA;
-    }
-    g_static_scratch[dev] = p;
+static ara_status static_scratch(void** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_select_scratch);
+  if (e != cudaSuccess || !p) {
+    note_cuda_error(e, "cudaGetSymbolAddress(g_select_scratch)", __FILE__, __LINE__);
+    return ARA_ECUDA;
   }
-  *out = g_static_scratch[dev];
+  *out = p;
   return ARA_OK;
 }
 
@@ -684,24 +675,34 @@ extern "C" ara_status ara_risk_metrics_static(const double* d_ylt, int64_t n_tri
   const size_t bytes = select_scratch_bytes(n_layers, tg.n_t, blocks);
   if (bytes > ARA_STATIC_SELECT_BYTES) return ARA_ERANGE;
   void* scratch = nullptr;
-  if ((st = static_scratch(dev, &scratch)) != ARA_OK) return st;
+  if ((st = static_scratch(&scratch)) != ARA_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   SelScratch sc;
   // launch_select clears the used part of the scratch before its first kernel
   if ((st = launch_select(d_ylt, n_trials, n_layers, tg, scratch, bytes, blocks, h_mean != nullptr,
                           s, &sc)) != ARA_OK)
     return st;
+  // Keep the first failing copy's status, but always wait for the stream before returning, so
+  // that no copy queued here can land in the caller's buffers after the call has returned.
+  cudaError_t e = cudaSuccess;
   const size_t row = sizeof(double) * (size_t)tg.n_t;
-  if (n_rp > 0)
-    ARA_TRY(cudaMemcpy2DAsync(h_pml, sizeof(double) * n_rp, sc.out, row, sizeof(double) * n_rp,
-                              (size_t)n_layers, cudaMemcpyDeviceToHost, s));
-  if (n_tvar > 0)
-    ARA_TRY(cudaMemcpy2DAsync(h_tvar, sizeof(double) * n_tvar, sc.out + n_rp, row,
-                              sizeof(double) * n_tvar, (size_t)n_layers, cudaMemcpyDeviceToHost, s));
-  if (h_mean)
-    ARA_TRY(cudaMemcpyAsync(h_mean, sc.mean, sizeof(double) * n_layers, cudaMemcpyDeviceToHost, s));
+  if (e == cudaSuccess && n_rp > 0)
+    e = cudaMemcpy2DAsync(h_pml, sizeof(double) * n_rp, sc.out, row, sizeof(double) * n_rp,
+                          (size_t)n_layers, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && n_tvar > 0)
+    e = cudaMemcpy2DAsync(h_tvar, sizeof(double) * n_tvar, sc.out + n_rp, row,
+                          sizeof(double) * n_tvar, (size_t)n_layers, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && h_mean)
+    e = cudaMemcpyAsync(h_mean, sc.mean, sizeof(double) * n_layers, cudaMemcpyDeviceToHost, s);
   uint32_t timed_out = 0;
-  ARA_TRY(cudaMemcpyAsync(&timed_out, sc.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  ARA_TRY(cudaStreamSynchronize(s));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&timed_out, sc.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) note_cuda_error(e, "static risk metrics: result copy", __FILE__, __LINE__);
+  const cudaError_t es = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && es != cudaSuccess) {
+    note_cuda_error(es, "cudaStreamSynchronize", __FILE__, __LINE__);
+    e = es;
+  }
+  if (e != cudaSuccess) return ARA_ECUDA;
   return timed_out ? ARA_ETIMEOUT : ARA_OK;
 }

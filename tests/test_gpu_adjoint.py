@@ -228,3 +228,60 @@ def test_adjoint_wide_layer_and_single_elt_layer():
         close(gr["layer"][obj].cpu().numpy(), ref["layer"], 1.0)
         close(gr["loss"][obj].cpu().numpy(), ref["loss"], scale)
     g.close()
+
+
+def _occurrence_regimes(pf, layer):
+    """Per catalogue event, the occurrence clamp's regime of one layer (0: s(e) <= OccR, 1:
+    interior, 2: above OccR + OccL), restated with numpy from the notation of Section IV-B.
+    Used only to show that a test case reaches the condition it is meant to exercise."""
+    s = np.zeros(pf.catalogue)
+    for j in pf.layer_elts[layer]:
+        a = np.minimum(np.maximum(pf.elt_losses[j] - pf.elt_ret[j], 0.0), pf.elt_lim[j])
+        s[pf.elt_ids[j]] += a
+    ex = s - pf.occ_ret[layer]
+    return np.where(ex <= 0, 0, np.where(ex < pf.occ_lim[layer], 1, 2)).astype(np.int8)
+
+
+def test_adjoint_coarse_regime_bitmap_at_the_adjoint_workload_catalogue():
+    """The adjoint workload's shape: a 2,000,000-event catalogue with ELTs of 20,000 events.
+    Its exact regime bitmap (250 KB) exceeds the histogram pass's shared-memory budget, so the
+    pass filters occurrences with the coarse bitmap (one bit per two events, 32 apart) and
+    counts events of regime 0 that share a coarse bit with an event of non-zero regime; those
+    counts must be dropped afterwards.  The case shows such events occur in interior trials,
+    then compares every gradient of both objectives with the FP64 chain rule."""
+    full = synth.adjoint_portfolio(0)
+    sel = [0, 5]
+    yet = synth.adjoint_yet(0, n_trials=4000)       # the first 4,000 trials of the workload's YET
+    sub = full.with_terms(full.terms_dict())
+    sub.layer_elts = [full.layer_elts[i] for i in sel]
+    for name in ["occ_ret", "occ_lim", "agg_ret", "agg_lim"]:
+        setattr(sub, name, np.asarray(getattr(full, name))[sel])
+    assert full.catalogue == 2_000_000 and (full.catalogue + 31) // 32 * 4 > 200 * 1024
+    assert well_posed(sub, yet, LEVEL)
+    # false positives of the coarse bitmap in interior trials, for every selected layer
+    _, agg = oracle.ylt(sub, yet, return_agg=True)
+    for l in range(len(sel)):
+        r = _occurrence_regimes(sub, l)
+        partner = np.arange(sub.catalogue) ^ 32
+        partner = np.minimum(partner, sub.catalogue - 1)
+        false_pos = (r == 0) & (r[partner] != 0)
+        interior = (agg[l] > sub.agg_ret[l]) & (agg[l] - sub.agg_ret[l] < sub.agg_lim[l])
+        counts = np.diff(yet.offsets)
+        occ_interior = np.repeat(interior, counts)
+        assert np.count_nonzero(false_pos[yet.event_ids[occ_interior]]) > 1000
+    g = ara.Portfolio.from_tables(full)
+    off, ids = dev(yet)
+    reg = torch.empty((len(sel), yet.n_trials), dtype=torch.uint8, device="cuda")
+    y = g.run_ylt(off, ids, layers=sel, regimes=reg)
+    g.check()
+    gr = g.adjoint(off, ids, y, reg, LEVEL, layers=sel)
+    g.check()
+    for obj, name in ((0, "mean"), (1, "tvar")):
+        ref = oracle.adjoint(sub, yet, name, LEVEL)
+        scale = max(1.0, float(np.abs(ref["loss"]).max()))
+        close(gr["elt"][obj].cpu().numpy(), ref["elt"], 1.0)
+        close(gr["layer"][obj].cpu().numpy(), ref["layer"], 1.0)
+        close(gr["loss"][obj].cpu().numpy(), ref["loss"], scale)
+        assert np.count_nonzero(ref["loss"]) > 1000 and np.all(ref["layer"][:, 0] != 0)
+    assert gr["ties"].tolist() == [0, 0]
+    g.close()
