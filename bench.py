@@ -579,18 +579,21 @@ def measure_batched(rank: int, reps: int = 5):
     return out
 
 
-def measure_serving(rank: int, n_requests: int = 200, workers: int = 2):
+def measure_serving(rank: int, n_requests: int = 200, workers: int = 2, low_rate: float = 50.0):
     """Serving: a seeded Poisson stream (200 requests/s, 32 tenants) of risk queries over a
     resident pool of 500 ELTs and a resident YET of 1e6 trials x Poisson(1000) events (1-32
     layers of 5-20 ELTs each, slices of 1e4-1e6 trials, 20 % with the adjoint), served by the
-    native server (continuous admission by device memory, requests overlapping on separate
-    streams), against the same queries run one at a time."""
+    native server: continuous admission by device memory, queued requests with overlapping slices
+    merged into one YET pass (up to 4), groups overlapping on separate streams.  Compared with
+    the same queries run one at a time (one worker, no merging; the batched path for requests of
+    4 or more layers, as in the served mode) and with sequential plain runs (one at a time, every
+    layer by the single-layer path).  The same queries arrive again at low_rate requests/s, below
+    capacity, for latencies without queueing.  Results must be identical in every mode."""
     import threading
     import torch
     import paper_1606_04473_gb300 as ara
     import synth
     pool_t = synth.serving_pool(0)
-    ids_h = None
     yet = synth.serving_yet(rank)
     pool = ara.Portfolio.from_tables(pool_t)
     off = torch.from_numpy(yet.offsets).cuda()
@@ -601,60 +604,65 @@ def measure_serving(rank: int, n_requests: int = 200, workers: int = 2):
     lookups = [sum(len(l) for l in q["layer_elts"]) * int(offs[q["trials"][1]] - offs[q["trials"][0]])
                for q in trace]
 
-    def query_args(q):
+    def query_args(q, plain):
+        batched = len(q["layer_elts"]) >= 4 and not plain
         return dict(layer_elts=q["layer_elts"], occ_ret=q["occ_ret"], occ_lim=q["occ_lim"],
                     agg_ret=q["agg_ret"], agg_lim=q["agg_lim"], trials=q["trials"],
                     return_periods=[100.0, 250.0], tvar_levels=[0.99], want_mean=True,
                     want_adjoint=q["want_adjoint"], adjoint_level=0.99,
-                    flags=ara.ARA_RUN_BATCHED if len(q["layer_elts"]) >= 4 else 0, tenant=q["tenant"])
+                    flags=ara.ARA_RUN_BATCHED if batched else 0, tenant=q["tenant"])
 
-    def serve(max_concurrent, paced):
-        srv = ara.Server(pool, off, ev, max_concurrent=max_concurrent)
-        # warm-up: one small request
-        srv.wait(srv.submit(**dict(query_args(trace[0]), trials=(0, 1000))))
+    def serve(max_concurrent, merge, plain=False, stretch=1.0):
+        srv = ara.Server(pool, off, ev, max_concurrent=max_concurrent, max_merge=merge)
+        srv.wait(srv.submit(**dict(query_args(trace[0], plain), trials=(0, 1000))))
+        c0 = srv.counters()
         tickets = [None] * len(trace)
         t_start = time.perf_counter()
 
         def feeder():
             for k, q in enumerate(trace):
-                if paced:
-                    d = q["arrival"] - (time.perf_counter() - t_start)
-                    if d > 0:
-                        time.sleep(d)
-                tickets[k] = srv.submit(**query_args(q))
+                d = q["arrival"] * stretch - (time.perf_counter() - t_start)
+                if d > 0:
+                    time.sleep(d)
+                tickets[k] = srv.submit(**query_args(q, plain))
 
         th = threading.Thread(target=feeder)
         th.start()
         th.join()
         res = [srv.wait(t) for t in tickets]
         makespan = time.perf_counter() - t_start
-        stats = srv.stats()
+        stats, cnt = srv.stats(), srv.counters()
         srv.close()
         lat = np.array([r["latency_s"] for r in res]) * 1e3
-        return res, makespan, lat, stats
+        arm = {"workers": max_concurrent, "max_merge": merge,
+               "p50_ms": round(float(np.percentile(lat, 50)), 2),
+               "p99_ms": round(float(np.percentile(lat, 99)), 2), "makespan_s": round(makespan, 3),
+               "lookups_per_s": float(sum(lookups)) / makespan,
+               "requests_per_s": len(trace) / makespan, "peak_running": stats["peak_running"],
+               "passes": cnt["passes"] - c0["passes"],
+               "merged_requests": cnt["merged_requests"] - c0["merged_requests"],
+               "head_passed": cnt["head_passed"] - c0["head_passed"]}
+        return res, arm
 
-    res_s, mk_s, lat_s, st_s = serve(workers, paced=True)
-    res_2, mk_2, lat_2, st_2 = serve(4, paced=True)
-    res_1, mk_1, lat_1, st_1 = serve(1, paced=True)
-    same = all(np.array_equal(a["pml"], b["pml"]) and np.array_equal(a["tvar"], b["tvar"]) and
-               np.array_equal(a["mean"], b["mean"]) and np.array_equal(c["pml"], b["pml"]) and
-               np.array_equal(c["tvar"], b["tvar"]) and np.array_equal(c["mean"], b["mean"])
-               for a, c, b in zip(res_s, res_2, res_1))
-    tot = float(sum(lookups))
+    res_s, served = serve(workers, 4)
+    res_1, one = serve(1, 1)
+    res_p, plain = serve(1, 1, plain=True)
+    stretch = 200.0 / low_rate
+    res_sl, served_low = serve(workers, 4, stretch=stretch)
+    res_1l, one_low = serve(1, 1, stretch=stretch)
+    keys = ("pml", "tvar", "mean", "grad_layer")
+    same = all(all((a[k] is None and b[k] is None) or np.array_equal(a[k], b[k]) for k in keys)
+               for other in (res_s, res_p, res_sl, res_1l) for a, b in zip(other, res_1))
     out = {"workload": f"{n_requests} requests, Poisson 200/s, 32 tenants; 1-32 layers x 5-20 ELTs of a "
                        "500-ELT pool; slices of 1e4-1e6 trials of a 1e6 x Poisson(1000) YET; 20% adjoint",
-           "served": {"workers": workers, "p50_ms": round(float(np.percentile(lat_s, 50)), 2),
-                      "p99_ms": round(float(np.percentile(lat_s, 99)), 2),
-                      "makespan_s": round(mk_s, 3), "lookups_per_s": tot / mk_s,
-                      "peak_running": st_s["peak_running"]},
-           "served_4_workers": {"p50_ms": round(float(np.percentile(lat_2, 50)), 2),
-                                "p99_ms": round(float(np.percentile(lat_2, 99)), 2),
-                                "makespan_s": round(mk_2, 3), "lookups_per_s": tot / mk_2},
-           "one_at_a_time": {"p50_ms": round(float(np.percentile(lat_1, 50)), 2),
-                             "p99_ms": round(float(np.percentile(lat_1, 99)), 2),
-                             "makespan_s": round(mk_1, 3), "lookups_per_s": tot / mk_1},
-           "throughput_gain": round(mk_1 / mk_s, 3), "results_identical": bool(same),
-           "total_lookups": tot}
+           "offered_load_high": "200 requests/s (above capacity: latencies include queueing)",
+           "served": served, "one_at_a_time": one, "sequential_plain": plain,
+           "offered_load_low": f"{low_rate:g} requests/s (the same queries, arrivals stretched "
+                               f"x{stretch:g})",
+           "served_low_load": served_low, "one_at_a_time_low_load": one_low,
+           "throughput_gain": round(one["makespan_s"] / served["makespan_s"], 3),
+           "throughput_gain_vs_sequential_plain": round(plain["makespan_s"] / served["makespan_s"], 3),
+           "results_identical": bool(same), "total_lookups": float(sum(lookups))}
     pool.close()
     return out
 

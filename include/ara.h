@@ -231,6 +231,29 @@ ARA_API ara_status ara_plan_info(ara_plan* plan, int32_t* warps, int32_t* blocks
                                  int32_t* trials_per_grab, double* tuned_ms);
 ARA_API void ara_plan_destroy(ara_plan* plan);
 
+/*
+ * Several requests' YLTs in one pass over a shared YET (the batched path serving several
+ * requests at once; the paper has no counterpart, it is the single-GPU way for its many tenants
+ * to share one reading of the YET).  Request r owns the portfolio's layers
+ * [req_layer_first[r], req_layer_first[r + 1]) (every layer of the portfolio belongs to exactly
+ * one request, in order) and the trials [req_trial_begin[r], req_trial_end[r]) of the n_trials
+ * trials given.  Every trial is read once and walks only the table entries of the requests that
+ * cover it.  Request r's YLT goes to d_ylt[r], a device [its layers][its trials] double array
+ * (row-major), and its aggregate regimes (as ara_run_ylt) to d_regimes[r] (device, same shape,
+ * or NULL; d_regimes itself may be NULL).  Results equal those of ara_run_ylt of each request
+ * alone, bit for bit.  Asynchronous on `stream`; scratch from the stream-ordered allocator.
+ *   n_req      1..4; the portfolio has at most 255 layers
+ *   d_ylt, d_regimes   host arrays [n_req] of device pointers
+ * Errors: ARA_EINVAL, ARA_ERANGE, ARA_ENOMEM, ARA_ECUDA; data errors via ara_check().
+ */
+ARA_API ara_status ara_run_ylt_requests(ara_portfolio* pf, int64_t n_trials,
+                                        const int64_t* d_trial_offsets, int64_t n_events,
+                                        const int32_t* d_event_ids, int32_t n_req,
+                                        const int32_t* req_layer_first,
+                                        const int64_t* req_trial_begin,
+                                        const int64_t* req_trial_end, double* const* d_ylt,
+                                        uint8_t* const* d_regimes, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * Serving: many risk queries over resident ELTs and a resident YET, on one GPU (the single-GPU
  * form of the paper's multi-tenant GPUs, Section V-D).
@@ -262,11 +285,19 @@ typedef struct ara_query {
 
 /*
  * Start a server over a resident pool portfolio (its ELTs) and a resident device YET.  Up to
- * max_concurrent (1..64) requests run at once, each on its own stream; a request is admitted,
- * first come first served, when a worker is free and its estimated device memory fits
- * memory_budget bytes together with the requests already running (<= 0: 80 % of the device's
- * free memory now).  A request larger than the budget runs alone.  The pool and the YET must
- * outlive the server.  Results of a request do not depend on what else runs.
+ * max_concurrent (1..64) workers run requests at once, each on its own stream.  A free worker
+ * admits the oldest queued request when its estimated device memory fits both memory_budget
+ * bytes together with the requests already running (<= 0: 80 % of the device's free memory at
+ * creation) and the device memory free at that moment; when it does not fit, the first of the
+ * next 31 queued requests that fits runs ahead of it (at most 4 times per blocked request).  A
+ * request larger than the budget runs alone.  Into the admitted request the worker merges up to
+ * three more queued requests (of the next 32) whose trial slices overlap the group's (by at
+ * least 30 % of their union, see ara_server_set_merging), best overlap first, while their
+ * memory fits: the group's layers run in one batched pass over the union of the slices, each
+ * trial walking only the table entries of the requests that cover it, so the requests share the
+ * reading of the YET.  Creation runs a few small warm-up requests (synchronous), so the first
+ * real requests pay no one-time costs.  The pool and the YET must outlive the server.  Results
+ * of a request do not depend on what else runs or on the group it ran in (bitwise).
  */
 ARA_API ara_status ara_server_create(ara_portfolio* pool, int64_t n_trials,
                                      const int64_t* d_trial_offsets, int64_t n_events,
@@ -288,6 +319,16 @@ ARA_API ara_status ara_server_wait(ara_server* server, int64_t ticket, double* h
  * estimated memory ever admitted at once, and the budget. */
 ARA_API ara_status ara_server_stats(ara_server* server, int32_t* queued_or_running,
                                     int32_t* peak_running, int64_t* peak_bytes, int64_t* budget);
+/* Merging of queued requests into one pass: at most max_requests_per_pass (1..4; 1 = every
+ * request runs its own pass) requests per pass, a request joining a group when its slice
+ * overlaps the group's by at least min_overlap (0 < min_overlap <= 1) of their union.  Applies
+ * to groups formed after the call.  Default 4 and 0.3.  Errors: ARA_EINVAL. */
+ARA_API ara_status ara_server_set_merging(ara_server* server, int32_t max_requests_per_pass,
+                                          double min_overlap);
+/* Passes run so far (a pass serves one request or a merged group), requests that ran in a merged
+ * group of two or more, and the times a blocked oldest request was passed by a later one. */
+ARA_API ara_status ara_server_counters(ara_server* server, int64_t* passes,
+                                       int64_t* merged_requests, int64_t* head_passed);
 /* Finish every queued request, then stop the workers and release the server. */
 ARA_API void ara_server_destroy(ara_server* server);
 

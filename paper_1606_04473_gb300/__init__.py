@@ -102,6 +102,12 @@ def lib() -> ctypes.CDLL:
     L.ara_server_stats.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64),
                                    ctypes.POINTER(i64)]
     L.ara_server_stats.restype = i32
+    L.ara_run_ylt_requests.argtypes = [P, i64, P, i64, P, i32, P, P, P, P, P, P]
+    L.ara_run_ylt_requests.restype = i32
+    L.ara_server_set_merging.argtypes = [P, i32, d]
+    L.ara_server_set_merging.restype = i32
+    L.ara_server_counters.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.ara_server_counters.restype = i32
     L.ara_server_destroy.argtypes = [P]
     L.ara_server_destroy.restype = None
     L.ara_adjoint.argtypes = [P, i64, P, i64, P, i32, P, P, P, d, P, P, P, P, P]
@@ -230,6 +236,32 @@ class Portfolio:
                                int(flags), _stream_handle(stream))
         _check(st, "ara_run_ylt")
         return out
+
+    def run_ylt_requests(self, offsets, event_ids, requests, regimes: bool = False, stream=None):
+        """Several requests in one pass (ara_run_ylt_requests): requests is a list of
+        (layer_begin, layer_end, trial_begin, trial_end) covering the portfolio's layers in
+        order.  Returns one YLT tensor [its layers, its trials] per request (and the regime
+        tensors when regimes=True)."""
+        import torch
+        n_trials = offsets.numel() - 1
+        n = len(requests)
+        first = np.ascontiguousarray([r[0] for r in requests] + [requests[-1][1]], dtype=np.int32)
+        tb = np.ascontiguousarray([r[2] for r in requests], dtype=np.int64)
+        te = np.ascontiguousarray([r[3] for r in requests], dtype=np.int64)
+        ys = [torch.empty((r[1] - r[0], r[3] - r[2]), dtype=torch.float64, device=offsets.device)
+              for r in requests]
+        rs = [torch.empty((r[1] - r[0], r[3] - r[2]), dtype=torch.uint8, device=offsets.device)
+              for r in requests] if regimes else None
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+        rp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in rs]) if regimes else None
+        st = lib().ara_run_ylt_requests(self._h, n_trials, _dev_ptr(offsets, torch.int64, "offsets"),
+                                        event_ids.numel(), _dev_ptr(event_ids, torch.int32, "event_ids"),
+                                        n, _np_ptr(first), _np_ptr(tb), _np_ptr(te),
+                                        ctypes.cast(yp, ctypes.c_void_p),
+                                        ctypes.cast(rp, ctypes.c_void_p) if regimes else None,
+                                        _stream_handle(stream))
+        _check(st, "ara_run_ylt_requests")
+        return (ys, rs) if regimes else ys
 
     def run_ylt_host(self, offsets: np.ndarray, event_ids: np.ndarray, layers=None, out=None,
                      return_periods: Sequence[float] = (), tvar_levels: Sequence[float] = (),
@@ -386,7 +418,7 @@ class Server:
     (ara_server_*).  submit() queues a query and returns a ticket; wait() returns its results."""
 
     def __init__(self, pool: Portfolio, offsets, event_ids, max_concurrent: int = 4,
-                 memory_budget: int = 0):
+                 memory_budget: int = 0, max_merge: int = 4, min_overlap: float = 0.3):
         import torch
         self._keep = (pool, offsets, event_ids)
         self.n_trials = offsets.numel() - 1
@@ -397,6 +429,19 @@ class Server:
         _check(st, "ara_server_create")
         self._h = h
         self._shapes = {}
+        self.set_merging(max_merge, min_overlap)
+
+    def set_merging(self, max_merge: int, min_overlap: float = 0.3):
+        """Merge up to max_merge queued requests with overlapping slices into one pass
+        (ara_server_set_merging; 1 = no merging)."""
+        _check(lib().ara_server_set_merging(self._h, int(max_merge), float(min_overlap)),
+               "ara_server_set_merging")
+
+    def counters(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ara_server_counters(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "ara_server_counters")
+        return {"passes": a.value, "merged_requests": b.value, "head_passed": c.value}
 
     def submit(self, layer_elts, occ_ret, occ_lim, agg_ret, agg_lim, trials, return_periods=(),
                tvar_levels=(), want_mean=False, want_adjoint=False, adjoint_level=0.99, flags=0,

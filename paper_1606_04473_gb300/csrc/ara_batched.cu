@@ -9,7 +9,11 @@
 //   2. per-event counts of non-zero q, read from the bitmaps, and their exclusive scan -> CSR
 //      row pointers.
 //   3. event-major CSR rows: for event e, its (layer slot, q) pairs in layer order, packed as
-//      slot << 56 | q (q < 2^55); q is read only where the bitmap bit is set.
+//      slot << 56 | q (q < 2^55); q is read only where the bitmap bit is set.  The event's row
+//      descriptor holds its first entry and, per request of a merged serving pass (slots are
+//      grouped by request), the number of its entries in one byte each (a row has at most 255
+//      entries, one per slot), so that a trial covered by some of the requests walks only
+//      their part of the row.
 // Stream (persistent, atomic trial queue for uneven trial lengths): a warp takes trials from the
 // queue; for every 32 occurrences it joins their events' CSR rows into one list, walks it 32
 // entries at a time and adds each q to the warp's per-layer accumulator in shared memory (exact
@@ -111,16 +115,27 @@ __global__ void k_bt_scan_add(uint32_t* __restrict__ ptr, int64_t n, const uint3
 // 3. CSR rows: one thread per event, layers in slot order (deterministic layout), and the
 //    event's row descriptor (first entry | length << 32)
 // ------------------------------------------------------------------------------------------
+// Request boundaries of a merged pass, in slots: request r owns [first[r], first[r + 1]); unused
+// requests start at BT_MAX_LAYERS + 1 (past every slot).
+struct BtReqSlots {
+  int32_t first[BT_MAX_REQ + 1];
+};
+
+__device__ __forceinline__ uint32_t bt_req_of_slot(const BtReqSlots& rs, int i) {
+  return (uint32_t)(i >= rs.first[1]) + (uint32_t)(i >= rs.first[2]) + (uint32_t)(i >= rs.first[3]);
+}
+
 __global__ void __launch_bounds__(256)
 k_bt_fill(int32_t n_sel, const uint64_t* __restrict__ q, const uint32_t* __restrict__ bits,
           int64_t bits_stride, int64_t catalogue, const uint32_t* __restrict__ ptr,
-          uint64_t* __restrict__ entries, uint64_t* __restrict__ rows) {
+          uint64_t* __restrict__ entries, uint64_t* __restrict__ rows, BtReqSlots rs) {
   constexpr int U = 8;   // slots per step: their bitmap words and table entries load together
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= catalogue) return;
-  uint32_t pos = ptr[e];
+  const uint32_t pos0 = ptr[e];
+  uint32_t pos = pos0;
   const uint32_t end = ptr[e + 1];
-  rows[e] = (uint64_t)pos | ((uint64_t)(end - pos) << 32);   // one 8-byte gather per occurrence
+  uint32_t lens = 0;   // entries of request r in byte r (one 8-byte descriptor per occurrence)
   const uint32_t* b = bits + (e >> 5);
   const int sh = (int)(e & 31);
   for (int i0 = 0; i0 < n_sel && pos < end; i0 += U) {
@@ -134,10 +149,14 @@ k_bt_fill(int32_t n_sel, const uint64_t* __restrict__ q, const uint32_t* __restr
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (hit[u]) {
-        if (pos < end) entries[pos] = ((uint64_t)(i0 + u) << 56) | v[u];
+        if (pos < end) {
+          entries[pos] = ((uint64_t)(i0 + u) << 56) | v[u];
+          lens += 1u << (8 * bt_req_of_slot(rs, i0 + u));
+        }
         ++pos;
       }
   }
+  rows[e] = (uint64_t)pos0 | ((uint64_t)lens << 32);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -154,8 +173,14 @@ struct BtStream {
   int32_t n_sel;
   const LayerConst* layers;    // device, indexed by layer id
   BtLayers sel;                // slot -> layer id
-  double* ylt;                 // [n_sel][n_trials]
-  uint8_t* regimes;            // or nullptr
+  // Requests of the pass (one outside serving): request r owns the slots [rs.first[r],
+  // rs.first[r + 1]) and the trials [t0[r], t1[r]); row i of its YLT (its slot first + i) is
+  // ylt[r] + i * (t1[r] - t0[r]), indexed by t - t0[r]; regimes likewise (or nullptr).
+  int32_t n_req;
+  BtReqSlots rs;
+  int64_t t0[BT_MAX_REQ], t1[BT_MAX_REQ];
+  double* ylt[BT_MAX_REQ];
+  uint8_t* regimes[BT_MAX_REQ];
   unsigned long long* queue;   // trial counter (zeroed before the launch)
   int32_t trials_per_grab;
   int32_t copies;              // accumulator copies per warp: 1, 2 or 4
@@ -190,6 +215,20 @@ k_bt_stream(BtStream p) {
     if (t0 >= (unsigned long long)p.n_trials) break;
     const int64_t t1 = min((int64_t)t0 + p.trials_per_grab, p.n_trials);
     for (int64_t t = (int64_t)t0; t < t1; ++t) {
+      // The requests covering trial t (warp-uniform): each occurrence walks the part of its row
+      // from the first to the last of them, [fa, la]; a request inside that range that does not
+      // cover t (at most the two middle ones of four, always adjacent) owns the slots
+      // [skip_lo, skip_hi), whose entries are skipped.
+      uint32_t amask = 0;
+      for (int r = 0; r < p.n_req; ++r)
+        if (t >= p.t0[r] && t < p.t1[r]) amask |= 1u << r;
+      if (amask == 0) continue;
+      const int fa = __ffs(amask) - 1, la = 31 - __clz(amask);
+      const uint32_t sh_lo = 8u * (uint32_t)fa, sh_hi = 8u * (uint32_t)la;
+      const uint32_t inner = ((2u << la) - (1u << fa)) & ~amask;   // uncovered, between fa and la
+      const uint32_t skip_lo = inner ? (uint32_t)p.rs.first[__ffs(inner) - 1] : 0u;
+      const uint32_t skip_n =
+          inner ? (uint32_t)p.rs.first[32 - __clz(inner)] - skip_lo : 0u;
       int64_t beg = __ldg(p.offsets + t), end = __ldg(p.offsets + t + 1);
       if (!(0 <= beg && beg <= end && end <= p.n_events)) { bad_off = true; beg = end = 0; }
       // 32 occurrences at a time.  Their rows are laid end to end (a warp scan of the lengths)
@@ -211,7 +250,11 @@ k_bt_stream(BtStream p) {
       for (int64_t i0 = beg; i0 < end; i0 += 32) {
         const uint64_t ri_nxt = load_row(e_nxt);
         e_nxt = load_id(i0 + 64 + lane);
-        const uint32_t rb = (uint32_t)ri_cur, len = (uint32_t)(ri_cur >> 32);
+        // byte r of lens * 0x01010101 is the number of entries of requests 0..r (< 256)
+        const uint32_t incl_b = (uint32_t)(ri_cur >> 32) * 0x01010101u;
+        const uint32_t skip_b = ((incl_b << 8) >> sh_lo) & 0xffu;   // entries before request fa
+        const uint32_t rb = (uint32_t)ri_cur + skip_b;
+        const uint32_t len = ((incl_b >> sh_hi) & 0xffu) - skip_b;
         ri_cur = ri_nxt;
         uint32_t incl = len;
 #pragma unroll
@@ -233,7 +276,8 @@ k_bt_stream(BtStream p) {
           if (x < total) {
             const uint64_t v = __ldg(p.entries + (uint32_t)(b + x));
             const int s = (int)(v >> 56);
-            smem_add_u128(&lo[s], &hi[s], v & ((1ull << 56) - 1));
+            if ((uint32_t)s - skip_lo >= skip_n)
+              smem_add_u128(&lo[s], &hi[s], v & ((1ull << 56) - 1));
           }
         }
       }
@@ -247,11 +291,14 @@ k_bt_stream(BtStream p) {
           a[i] = 0ull;
           a[ns + i] = 0ull;
         }
+        const uint32_t r = bt_req_of_slot(p.rs, i);
+        if (!((amask >> r) & 1u)) continue;
         const LayerConst lc = p.layers[p.sel.layer[i]];
         uint8_t reg;
         const double y = AccOps<U128>::finish(S, lc, reg);
-        p.ylt[(int64_t)i * p.n_trials + t] = y;
-        if (p.regimes) p.regimes[(int64_t)i * p.n_trials + t] = reg;
+        const int64_t at = (int64_t)(i - p.rs.first[r]) * (p.t1[r] - p.t0[r]) + (t - p.t0[r]);
+        p.ylt[r][at] = y;
+        if (p.regimes[r]) p.regimes[r][at] = reg;
       }
       __syncwarp();
     }
@@ -275,6 +322,12 @@ struct ara_plan {
   std::vector<int32_t> sel;
   double* d_ylt = nullptr;
   uint8_t* d_reg = nullptr;
+  // requests of a merged serving pass (one request otherwise: all trials, d_ylt / d_reg)
+  int32_t n_req = 1;
+  BtReqSlots rs{{0, BT_MAX_LAYERS + 1, BT_MAX_LAYERS + 1, BT_MAX_LAYERS + 1, BT_MAX_LAYERS + 1}};
+  int64_t req_t0[BT_MAX_REQ] = {0, 0, 0, 0}, req_t1[BT_MAX_REQ] = {0, 0, 0, 0};
+  double* req_ylt[BT_MAX_REQ] = {nullptr, nullptr, nullptr, nullptr};
+  uint8_t* req_reg[BT_MAX_REQ] = {nullptr, nullptr, nullptr, nullptr};
   uint32_t* d_ptr = nullptr;
   uint64_t* d_rows = nullptr;
   uint32_t* d_bsum = nullptr;
@@ -290,6 +343,15 @@ struct ara_plan {
 };
 
 namespace {
+
+// The plan as one request: every selected layer over every trial, into d_ylt / d_reg.
+void single_request(ara_plan& P) {
+  P.n_req = 1;
+  P.req_t0[0] = 0;
+  P.req_t1[0] = P.n_trials;
+  P.req_ylt[0] = P.d_ylt;
+  P.req_reg[0] = P.d_reg;
+}
 
 ara_status bt_prep(ara_plan& P, cudaStream_t s, bool fill, int* n_kernels) {
   Portfolio& pf = *P.pf;
@@ -311,7 +373,7 @@ ara_status bt_prep(ara_plan& P, cudaStream_t s, bool fill, int* n_kernels) {
   int k = 4;
   if (fill) {
     k_bt_fill<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(n_sel, pf.d_q, pf.d_bits, pf.bm_words, C,
-                                                          P.d_ptr, P.d_entries, P.d_rows);
+                                                          P.d_ptr, P.d_entries, P.d_rows, P.rs);
     ++k;
   }
   ARA_TRY(cudaGetLastError());
@@ -343,8 +405,15 @@ ara_status bt_stream(ara_plan& P, cudaStream_t s) {
   bs.layers = P.pf->d_layers;
   bs.sel.n_sel = bs.n_sel;
   for (int i = 0; i < bs.n_sel; ++i) bs.sel.layer[i] = P.sel[i];
-  bs.ylt = P.d_ylt;
-  bs.regimes = P.d_reg;
+  bs.n_req = P.n_req;
+  bs.rs = P.rs;
+  for (int r = 0; r < BT_MAX_REQ; ++r) {
+    bs.t0[r] = P.req_t0[r];
+    bs.t1[r] = P.req_t1[r];
+    bs.ylt[r] = P.req_ylt[r];
+    bs.regimes[r] = P.req_reg[r];
+  }
+  if (!bs.ylt[0]) return ARA_EINVAL;
   bs.queue = P.d_queue;
   bs.trials_per_grab = P.tpg;
   bs.copies = P.copies;
@@ -370,6 +439,10 @@ void bt_free(ara_plan* P) {
 }  // namespace
 
 namespace ara {
+namespace {
+ara_status run_plan_async(ara_plan& P, cudaStream_t s);
+}  // namespace
+
 // The batched path as one asynchronous call (no graph, default schedule): scratch comes from the
 // stream-ordered allocator, the table is sized by a host-known bound (every non-zero entry of
 // layer i is an event of one of its ELTs), and nothing waits on the host.
@@ -384,6 +457,41 @@ ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   P.d_ylt = a.ylt;
   P.d_reg = a.regimes;
   if (a.id_base != 0 || a.row_stride != a.n_trials) return ARA_EINVAL;
+  single_request(P);
+  return run_plan_async(P, s);
+}
+
+// Several requests in one pass (serving): every layer of the portfolio, request r owning the
+// slots [slot_first[r], slot_first[r + 1]) and the trials [t0[r], t1[r]) of the union range.
+ara_status run_batched_group_async(Portfolio& pf, const GroupArgs& g, cudaStream_t s) {
+  if (g.n_req < 1 || g.n_req > BT_MAX_REQ || g.n_trials < 1 || !g.offsets) return ARA_EINVAL;
+  if (g.slot_first[0] != 0 || g.slot_first[g.n_req] != pf.n_layers) return ARA_EINVAL;
+  ara_plan P;
+  P.pf = &pf;
+  P.n_trials = g.n_trials;
+  P.n_events = g.n_events;
+  P.d_off = g.offsets;
+  P.d_ids = g.ids;
+  for (int32_t l = 0; l < pf.n_layers; ++l) P.sel.push_back(l);
+  P.n_req = g.n_req;
+  for (int r = 0; r < BT_MAX_REQ; ++r) {
+    P.rs.first[r + 1] = r < g.n_req ? g.slot_first[r + 1] : BT_MAX_LAYERS + 1;
+    if (r >= g.n_req) continue;
+    if (g.slot_first[r + 1] <= g.slot_first[r] || g.t0[r] < 0 || g.t1[r] <= g.t0[r] ||
+        g.t1[r] > g.n_trials || !g.ylt[r])
+      return ARA_EINVAL;
+    P.req_t0[r] = g.t0[r];
+    P.req_t1[r] = g.t1[r];
+    P.req_ylt[r] = g.ylt[r];
+    P.req_reg[r] = g.reg[r];
+  }
+  P.rs.first[0] = 0;
+  return run_plan_async(P, s);
+}
+
+namespace {
+ara_status run_plan_async(ara_plan& P, cudaStream_t s) {
+  Portfolio& pf = *P.pf;
   if ((int)P.sel.size() > BT_MAX_LAYERS || (int)P.sel.size() > pf.n_layers ||
       (int64_t)P.sel.size() * pf.catalogue >= ((int64_t)1 << 32))
     return ARA_ERANGE;
@@ -423,6 +531,7 @@ ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   P.d_queue = nullptr;
   return st;
 }
+}  // namespace
 }  // namespace ara
 
 extern "C" {
@@ -448,6 +557,7 @@ ara_status ara_plan_batched(ara_portfolio* pf_, int64_t n_trials, const int64_t*
   P->d_ids = d_ids ? d_ids : reinterpret_cast<const int32_t*>(d_off);
   P->d_ylt = d_ylt;
   P->d_reg = d_reg;
+  single_request(*P);
   if (n_sel_in == 0 && layer_sel == nullptr) {
     for (int32_t l = 0; l < pf->n_layers; ++l) P->sel.push_back(l);
   } else {
@@ -554,6 +664,40 @@ ara_status ara_plan_batched(ara_portfolio* pf_, int64_t n_trials, const int64_t*
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(ARA_ECUDA);
   *out = P;
   return ARA_OK;
+}
+
+ara_status ara_run_ylt_requests(ara_portfolio* pf_, int64_t n_trials, const int64_t* d_off,
+                                int64_t n_events, const int32_t* d_ids, int32_t n_req,
+                                const int32_t* req_layer_first, const int64_t* req_trial_begin,
+                                const int64_t* req_trial_end, double* const* d_ylt,
+                                uint8_t* const* d_regimes, void* stream) {
+  Portfolio* pf = static_cast<Portfolio*>(pf_);
+  if (!pf || n_trials < 1 || n_events < 0 || !d_off || (n_events > 0 && !d_ids)) return ARA_EINVAL;
+  if (n_req < 1 || !req_layer_first || !req_trial_begin || !req_trial_end || !d_ylt) return ARA_EINVAL;
+  if (n_req > BT_MAX_REQ || pf->n_layers > BT_MAX_LAYERS) return ARA_ERANGE;
+  if (((uintptr_t)d_ids & 3) || ((uintptr_t)d_off & 7)) return ARA_EINVAL;
+  if (pf->catalogue > 0xffffffffll) return ARA_ERANGE;
+  GroupArgs g;
+  g.n_trials = n_trials;
+  g.offsets = d_off;
+  g.n_events = n_events;
+  g.ids = d_ids ? d_ids : reinterpret_cast<const int32_t*>(d_off);
+  g.n_req = n_req;
+  if (req_layer_first[0] != 0 || req_layer_first[n_req] != pf->n_layers) return ARA_EINVAL;
+  for (int32_t r = 0; r < n_req; ++r) {
+    if (req_layer_first[r + 1] <= req_layer_first[r]) return ARA_EINVAL;
+    if (req_trial_begin[r] < 0 || req_trial_end[r] <= req_trial_begin[r] || req_trial_end[r] > n_trials)
+      return ARA_EINVAL;
+    if (!d_ylt[r] || ((uintptr_t)d_ylt[r] & 7)) return ARA_EINVAL;
+    g.slot_first[r] = req_layer_first[r];
+    g.t0[r] = req_trial_begin[r];
+    g.t1[r] = req_trial_end[r];
+    g.ylt[r] = d_ylt[r];
+    g.reg[r] = d_regimes ? d_regimes[r] : nullptr;
+  }
+  g.slot_first[n_req] = req_layer_first[n_req];
+  DeviceGuard dg(pf->device);
+  return run_batched_group_async(*pf, g, (cudaStream_t)stream);
 }
 
 ara_status ara_plan_launch(ara_plan* P, void* stream) {

@@ -150,6 +150,24 @@ ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
                           const FoldOutHost& o, cudaStream_t s, bool counted = true);
 ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s);
 ara_status run_batched_async(Portfolio& pf, const YltArgs& a, cudaStream_t s);
+// One pass of the batched stream for several requests at once (serving): request r owns the
+// portfolio's layers (= slots) [slot_first[r], slot_first[r + 1]) and the trials [t0[r], t1[r])
+// of a union range of trials; every trial of the union is read once and walks only the table
+// entries of the requests that cover it.  Each request's YLT rows go to its own buffer
+// ylt[r] ([layers of r][t1[r] - t0[r]], row-major), bitwise equal to a run of that request alone.
+constexpr int BT_MAX_REQ = 4;
+struct GroupArgs {
+  int64_t n_trials = 0;                 // trials of the union range
+  const int64_t* offsets = nullptr;     // [n_trials + 1], first trial of the union range
+  int64_t n_events = 0;
+  const int32_t* ids = nullptr;
+  int32_t n_req = 0;                    // 1 .. BT_MAX_REQ
+  int32_t slot_first[BT_MAX_REQ + 1] = {0, 0, 0, 0, 0};
+  int64_t t0[BT_MAX_REQ] = {0, 0, 0, 0}, t1[BT_MAX_REQ] = {0, 0, 0, 0};   // relative to the union
+  double* ylt[BT_MAX_REQ] = {nullptr, nullptr, nullptr, nullptr};
+  uint8_t* reg[BT_MAX_REQ] = {nullptr, nullptr, nullptr, nullptr};
+};
+ara_status run_batched_group_async(Portfolio& pf, const GroupArgs& g, cudaStream_t s);
 ara_status build_dense(Portfolio& pf, cudaStream_t s);
 // Compiled shapes (warps per block, ring stages) of the bulk-staged YET stream kernel.
 int32_t n_bulk_shapes();

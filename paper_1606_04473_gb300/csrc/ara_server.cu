@@ -1,11 +1,17 @@
 // Request server: many risk queries (portfolios of layers over a resident pool of ELTs, each on
 // a slice of a resident YET) served concurrently on one GPU.  This is the single-GPU form of the
-// paper's many tenants sharing GPUs (Section V-D): the ELTs stay resident across requests,
-// requests are admitted first-come first-served whenever a worker is free and their estimated
-// device memory fits the budget (continuous admission as earlier requests finish and release
-// memory), and admitted requests run on separate streams so their transfers and kernels
-// overlap on the device.  Every request's computation is the deterministic single-request path,
-// so its results do not depend on what else is running.
+// paper's many tenants sharing GPUs (Section V-D): the ELTs stay resident across requests, and
+// requests are admitted whenever a worker is free and their estimated device memory fits, both
+// under the server's budget and within the device memory free at that moment (continuous
+// admission as earlier requests finish and release memory).  A free worker takes the oldest
+// queued request (or, when that one does not fit, a later one that does, a bounded number of
+// times) and merges into it up to three more queued requests whose trial slices overlap the
+// group's: their layers run in one batched pass over the union of the slices, each trial
+// walking only the table entries of the requests that cover it, so overlapping requests share
+// the reading of the YET.  Admitted groups run on separate streams, so their transfers and
+// kernels overlap on the device.  Every request's arithmetic is exact or deterministic (integer
+// trial sums, an exact selection, integer adjoint counts), so its results do not depend on what
+// else is running or on the group it ran in.
 
 #include <chrono>
 #include <condition_variable>
@@ -28,6 +34,7 @@ struct Request {
   int32_t want_mean = 0, want_adjoint = 0, flags = 0, tenant = 0;
   double adjoint_level = 0.99;
   int64_t mem = 0;
+  int32_t passed = 0;     // times a later request was admitted ahead of this one
   // results
   ara_status status = ARA_OK;
   std::vector<double> pml, tvar, mean, grad_layer;
@@ -50,6 +57,13 @@ struct ara_server {
   int64_t n_trials = 0, n_events = 0;
   int64_t budget = 0, in_use = 0, peak_in_use = 0;
   int32_t max_concurrent = 0, running = 0, peak_running = 0;
+  // merging: at most max_merge requests per pass; a queued request joins a group when its
+  // slice's overlap with the group's slice is at least min_overlap of their union
+  int32_t max_merge = 4;
+  double min_overlap = 0.3;
+  int32_t window = 32;        // queued requests examined for a group or to pass a blocked head
+  int32_t max_passed = 4;     // a blocked head is passed at most this many times
+  int64_t n_passes = 0, n_merged = 0, n_head_passed = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<Request>> pending;
@@ -67,7 +81,7 @@ int64_t estimate_bytes(const Portfolio& pool, const Request& r) {
   int64_t b = nl * (8 * C + 4 * (pool.bm_words + pool.cbits_stride)) + 4096 * nl;   // layer set
   b += nl * n * 9;                                                                  // YLT + regimes
   b += 8192 * (int64_t)(r.rps.size() + r.levels.size() + 2) * nl + (1 << 20);       // selection
-  if (r.flags & ARA_RUN_BATCHED) {
+  {   // batched table (every request may run in a merged batched pass)
     int64_t bound = 0;
     for (int32_t j : r.layer_elts) bound += pool.rec_off[j + 1] - pool.rec_off[j];
     b += 12 * C + 8 * bound;
@@ -80,6 +94,63 @@ int64_t estimate_bytes(const Portfolio& pool, const Request& r) {
   return b;
 }
 
+// The metrics and the adjoint of one request whose YLT (and regimes) are computed: its layers are
+// the layer set's layers [slot0, slot0 + nl), its trials [r.t0, r.t1) of the resident YET.
+ara_status finish_request(ara_server& S, Request& r, ara_portfolio* ls, int32_t slot0, double* ylt,
+                          uint8_t* reg, cudaStream_t s) {
+  const int32_t nl = (int32_t)r.layer_off.size() - 1;
+  const int64_t n = r.t1 - r.t0;
+  ara_status st = ARA_OK;
+  if (!r.rps.empty() || !r.levels.empty() || r.want_mean) {
+    r.pml.assign((size_t)nl * r.rps.size(), 0.0);
+    r.tvar.assign((size_t)nl * r.levels.size(), 0.0);
+    r.mean.assign(r.want_mean ? (size_t)nl : 0, 0.0);
+    st = risk_metrics_device(ylt, n, nl, (int32_t)r.rps.size(), r.rps.data(), (int32_t)r.levels.size(),
+                             r.levels.data(), r.pml.data(), r.tvar.data(),
+                             r.want_mean ? r.mean.data() : nullptr, s);
+  }
+  if (st == ARA_OK && r.want_adjoint) {
+    int64_t K = 0, M = 0;
+    for (int32_t j : r.layer_elts) {
+      ++K;
+      M += S.pool->rec_off[j + 1] - S.pool->rec_off[j];
+    }
+    std::vector<int32_t> sel(nl);
+    for (int32_t i = 0; i < nl; ++i) sel[i] = slot0 + i;
+    double *ge = nullptr, *gl = nullptr, *gx = nullptr;
+    if (cudaMallocAsync((void**)&ge, 8 * (size_t)std::max<int64_t>(4 * K, 1), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&gl, 8 * (size_t)(8 * nl), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&gx, 8 * (size_t)std::max<int64_t>(2 * M, 1), s) != cudaSuccess) {
+      st = ARA_ENOMEM;
+    } else {
+      st = ara_adjoint(ls, n, S.d_off + r.t0, S.n_events, S.d_ids, nl, sel.data(), ylt, reg,
+                       r.adjoint_level, ge, gl, gx, nullptr, s);
+      if (st == ARA_OK) {
+        r.grad_layer.assign((size_t)8 * nl, 0.0);
+        if (cudaMemcpyAsync(r.grad_layer.data(), gl, 8 * (size_t)(8 * nl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+          st = ARA_ECUDA;
+      }
+    }
+    if (ge) cudaFreeAsync(ge, s);
+    if (gl) cudaFreeAsync(gl, s);
+    if (gx) cudaFreeAsync(gx, s);
+  }
+  return st;
+}
+
+void mark_done(ara_server& S, Request& r, ara_status st) {
+  r.status = st;
+  r.t_done = now_s();
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    r.done = true;
+  }
+  S.cv_done.notify_all();
+}
+
+// One request on its own: its own layer set and the ordinary path (ARA_RUN_BATCHED or the
+// single-layer stream, as the query asks).
 void run_request(ara_server& S, Request& r, cudaStream_t s) {
   const int32_t nl = (int32_t)r.layer_off.size() - 1;
   const int64_t n = r.t1 - r.t0;
@@ -96,85 +167,214 @@ void run_request(ara_server& S, Request& r, cudaStream_t s) {
   if (st == ARA_OK)
     st = ara_run_ylt(ls, n, S.d_off + r.t0, S.n_events, S.d_ids, nullptr, 0, nullptr, ylt, reg,
                      r.flags, s);
-  if (st == ARA_OK && (!r.rps.empty() || !r.levels.empty() || r.want_mean)) {
-    r.pml.assign((size_t)nl * r.rps.size(), 0.0);
-    r.tvar.assign((size_t)nl * r.levels.size(), 0.0);
-    r.mean.assign(r.want_mean ? (size_t)nl : 0, 0.0);
-    st = risk_metrics_device(ylt, n, nl, (int32_t)r.rps.size(), r.rps.data(), (int32_t)r.levels.size(),
-                             r.levels.data(), r.pml.data(), r.tvar.data(),
-                             r.want_mean ? r.mean.data() : nullptr, s);
-  }
-  if (st == ARA_OK && r.want_adjoint) {
-    int64_t K = 0, M = 0;
-    for (int32_t j : r.layer_elts) {
-      ++K;
-      M += S.pool->rec_off[j + 1] - S.pool->rec_off[j];
-    }
-    double *ge = nullptr, *gl = nullptr, *gx = nullptr;
-    if (cudaMallocAsync((void**)&ge, 8 * (size_t)std::max<int64_t>(4 * K, 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&gl, 8 * (size_t)(8 * nl), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&gx, 8 * (size_t)std::max<int64_t>(2 * M, 1), s) != cudaSuccess) {
-      st = ARA_ENOMEM;
-    } else {
-      st = ara_adjoint(ls, n, S.d_off + r.t0, S.n_events, S.d_ids, 0, nullptr, ylt, reg,
-                       r.adjoint_level, ge, gl, gx, nullptr, s);
-      if (st == ARA_OK) {
-        r.grad_layer.assign((size_t)8 * nl, 0.0);
-        if (cudaMemcpyAsync(r.grad_layer.data(), gl, 8 * (size_t)(8 * nl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-          st = ARA_ECUDA;
-      }
-    }
-    if (ge) cudaFreeAsync(ge, s);
-    if (gl) cudaFreeAsync(gl, s);
-    if (gx) cudaFreeAsync(gx, s);
-  }
+  if (st == ARA_OK) st = finish_request(S, r, ls, 0, ylt, reg, s);
   if (st == ARA_OK) st = ara_check(ls, s);
   if (ylt) cudaFreeAsync(ylt, s);
   if (reg) cudaFreeAsync(reg, s);
   if (ls) ara_destroy_portfolio(ls);
   if (cudaStreamSynchronize(s) != cudaSuccess && st == ARA_OK) st = ARA_ECUDA;
-  r.status = st;
+  mark_done(S, r, st);
+}
+
+// Several requests in one pass: one layer set holding every request's layers (request k's at the
+// slots [first[k], first[k + 1])), one batched pass over the union of their trial slices, then
+// each request's metrics and adjoint from its own YLT.  Each request is marked done as soon as
+// its own results are in.
+void run_group(ara_server& S, std::vector<std::shared_ptr<Request>>& g, cudaStream_t s) {
+  const int nr = (int)g.size();
+  GroupArgs ga;
+  ga.n_req = nr;
+  std::vector<int32_t> loff{0}, lel;
+  std::vector<double> oR, oL, aR, aL;
+  int64_t u0 = g[0]->t0, u1 = g[0]->t1;
+  for (int k = 0; k < nr; ++k) {
+    const Request& r = *g[k];
+    const int32_t nl = (int32_t)r.layer_off.size() - 1;
+    for (int32_t l = 0; l < nl; ++l) loff.push_back(loff.back() + r.layer_off[l + 1] - r.layer_off[l]);
+    lel.insert(lel.end(), r.layer_elts.begin(), r.layer_elts.end());
+    oR.insert(oR.end(), r.occ_ret.begin(), r.occ_ret.end());
+    oL.insert(oL.end(), r.occ_lim.begin(), r.occ_lim.end());
+    aR.insert(aR.end(), r.agg_ret.begin(), r.agg_ret.end());
+    aL.insert(aL.end(), r.agg_lim.begin(), r.agg_lim.end());
+    ga.slot_first[k + 1] = ga.slot_first[k] + nl;
+    u0 = std::min(u0, r.t0);
+    u1 = std::max(u1, r.t1);
+  }
+  ara_portfolio* ls = nullptr;
+  ara_status st = ara_create_layer_set(static_cast<ara_portfolio*>(S.pool), ga.slot_first[nr],
+                                       loff.data(), lel.data(), oR.data(), oL.data(), aR.data(),
+                                       aL.data(), s, &ls);
+  ga.n_trials = u1 - u0;
+  ga.offsets = S.d_off + u0;
+  ga.n_events = S.n_events;
+  ga.ids = S.d_ids;
+  for (int k = 0; k < nr && st == ARA_OK; ++k) {
+    const Request& r = *g[k];
+    const int64_t nl = (int64_t)r.layer_off.size() - 1, n = r.t1 - r.t0;
+    ga.t0[k] = r.t0 - u0;
+    ga.t1[k] = r.t1 - u0;
+    if (cudaMallocAsync((void**)&ga.ylt[k], 8 * (size_t)(nl * n), s) != cudaSuccess ||
+        (r.want_adjoint && cudaMallocAsync((void**)&ga.reg[k], (size_t)(nl * n), s) != cudaSuccess))
+      st = ARA_ENOMEM;
+  }
+  if (st == ARA_OK) st = run_batched_group_async(*static_cast<Portfolio*>(ls), ga, s);
+  if (st == ARA_OK) st = ara_check(ls, s);
+  for (int k = 0; k < nr; ++k) {
+    ara_status sk = st;
+    if (sk == ARA_OK) sk = finish_request(S, *g[k], ls, ga.slot_first[k], ga.ylt[k], ga.reg[k], s);
+    if (sk == ARA_OK && cudaStreamSynchronize(s) != cudaSuccess) sk = ARA_ECUDA;
+    mark_done(S, *g[k], sk);
+  }
+  for (int k = 0; k < nr; ++k) {
+    if (ga.ylt[k]) cudaFreeAsync(ga.ylt[k], s);
+    if (ga.reg[k]) cudaFreeAsync(ga.reg[k], s);
+  }
+  if (ls) ara_destroy_portfolio(ls);
+  cudaStreamSynchronize(s);
+}
+
+// Device memory that admission may still hand out: the budget left, and no more than the device
+// has free now (less what admitted requests may still allocate).
+int64_t admissible_bytes(ara_server& S) {
+  int64_t avail = S.budget - S.in_use;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+    avail = std::min(avail, (int64_t)(0.95 * (double)free_b) - S.in_use);
+  return avail;
+}
+
+int64_t overlap(int64_t a0, int64_t a1, int64_t b0, int64_t b1) {
+  return std::max<int64_t>(0, std::min(a1, b1) - std::max(a0, b0));
+}
+
+// Choose the next group under the lock: the oldest request if it fits (or if nothing runs), else
+// the first of the next `window` requests that fits, unless the oldest has already been passed
+// max_passed times; then up to max_merge - 1 more requests of the window whose slices overlap the
+// group's by at least min_overlap of the union, best overlap first, while the memory fits.
+// Returns an empty group when nothing can be admitted now.
+std::vector<std::shared_ptr<Request>> pick_group(ara_server& S) {
+  std::vector<std::shared_ptr<Request>> g;
+  if (S.pending.empty()) return g;
+  // the oldest request runs even when it does not fit if nothing else runs (alone); every other
+  // request, and every request merged into a group, must fit
+  const int64_t avail = admissible_bytes(S);
+  size_t lead = 0;
+  if (S.pending[0]->mem > avail && S.running > 0) {
+    if (S.pending[0]->passed >= S.max_passed) return g;
+    lead = SIZE_MAX;
+    for (size_t i = 1; i < S.pending.size() && i < (size_t)S.window; ++i)
+      if (S.pending[i]->mem <= avail) { lead = i; break; }
+    if (lead == SIZE_MAX) return g;
+    S.pending[0]->passed += 1;
+    S.n_head_passed += 1;
+  }
+  g.push_back(S.pending[lead]);
+  S.pending.erase(S.pending.begin() + (long)lead);
+  int64_t mem = g[0]->mem;
+  int32_t slots = (int32_t)g[0]->layer_off.size() - 1;
+  int64_t u0 = g[0]->t0, u1 = g[0]->t1;
+  while ((int)g.size() < std::min(S.max_merge, (int)BT_MAX_REQ)) {
+    size_t best = SIZE_MAX;
+    double best_ov = 0.0;
+    for (size_t i = 0; i < S.pending.size() && i < (size_t)S.window; ++i) {
+      const Request& c = *S.pending[i];
+      const int32_t nl = (int32_t)c.layer_off.size() - 1;
+      if (slots + nl > 255 || mem + c.mem > avail) continue;
+      const int64_t ov = overlap(u0, u1, c.t0, c.t1);
+      const double frac = (double)ov / (double)(std::max(u1, c.t1) - std::min(u0, c.t0));
+      if (ov > 0 && frac >= S.min_overlap && frac > best_ov) { best = i; best_ov = frac; }
+    }
+    if (best == SIZE_MAX) break;
+    std::shared_ptr<Request> c = S.pending[best];
+    S.pending.erase(S.pending.begin() + (long)best);
+    mem += c->mem;
+    slots += (int32_t)c->layer_off.size() - 1;
+    u0 = std::min(u0, c->t0);
+    u1 = std::max(u1, c->t1);
+    g.push_back(c);
+  }
+  return g;
 }
 
 void worker_main(ara_server* S) {
-  DeviceGuard g(S->pool->device);
+  DeviceGuard dg(S->pool->device);
   cudaStream_t s = nullptr;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) s = nullptr;
   while (true) {
-    std::shared_ptr<Request> r;
+    std::vector<std::shared_ptr<Request>> g;
+    int64_t mem = 0;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv_work.wait(lk, [&] {
         if (S->stop && S->pending.empty()) return true;
-        if (S->pending.empty()) return false;
-        // first come, first served: the head of the queue is admitted when it fits, or when
-        // nothing else is running (a request larger than the budget still runs, alone)
-        const int64_t need = S->pending.front()->mem;
-        return S->running == 0 || S->in_use + need <= S->budget;
+        g = pick_group(*S);
+        return !g.empty();
       });
-      if (S->pending.empty()) break;
-      r = S->pending.front();
-      S->pending.pop_front();
-      S->in_use += r->mem;
-      S->running += 1;
+      if (g.empty()) break;
+      for (auto& r : g) mem += r->mem;
+      S->in_use += mem;
+      S->running += (int32_t)g.size();
+      S->n_passes += 1;
+      if (g.size() > 1) S->n_merged += (int64_t)g.size();
       S->peak_in_use = std::max(S->peak_in_use, S->in_use);
       S->peak_running = std::max(S->peak_running, S->running);
     }
-    r->t_start = now_s();
-    if (s) run_request(*S, *r, s);
-    else r->status = ARA_ECUDA;
-    r->t_done = now_s();
+    const double t = now_s();
+    for (auto& r : g) r->t_start = t;
+    if (!s) {
+      for (auto& r : g) mark_done(*S, *r, ARA_ECUDA);
+    } else if (g.size() == 1) {
+      run_request(*S, *g[0], s);
+    } else {
+      run_group(*S, g, s);
+    }
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      S->in_use -= r->mem;
-      S->running -= 1;
-      r->done = true;
+      S->in_use -= mem;
+      S->running -= (int32_t)g.size();
     }
     S->cv_done.notify_all();
     S->cv_work.notify_all();
   }
   if (s) cudaStreamDestroy(s);
+}
+
+// Warm-up at creation: two small requests with every output (metrics and adjoint) run alone,
+// batched, and merged, so that the first real requests pay no one-time costs (kernel loading,
+// the stream-ordered allocator's first reservations).
+ara_status warm_up(ara_server& S) {
+  if (S.pool->n_elts < 1) return ARA_OK;
+  cudaStream_t s = nullptr;
+  ARA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  std::vector<std::shared_ptr<Request>> rs;
+  ara_status st = ARA_OK;
+  const int64_t n = std::min<int64_t>(S.n_trials, 256);
+  for (int k = 0; k < 3; ++k) {
+    auto r = std::make_shared<Request>();
+    r->layer_off = {0, 1};
+    r->layer_elts = {std::min(k, S.pool->n_elts - 1)};
+    r->occ_ret = {0.0};
+    r->occ_lim = {1e300};
+    r->agg_ret = {0.0};
+    r->agg_lim = {1e300};
+    r->rps = {1.0};
+    r->levels = {0.5};
+    r->want_mean = 1;
+    r->want_adjoint = tail_count_snap(n, 0.5) >= 1 ? 1 : 0;
+    r->adjoint_level = 0.5;
+    r->t0 = 0;
+    r->t1 = n;
+    r->flags = k == 0 ? 0 : ARA_RUN_BATCHED;
+    rs.push_back(r);
+  }
+  run_request(S, *rs[0], s);
+  run_request(S, *rs[1], s);
+  std::vector<std::shared_ptr<Request>> g{rs[1], rs[2]};
+  run_group(S, g, s);
+  for (auto& r : rs)
+    if (r->status != ARA_OK && st == ARA_OK) st = r->status;
+  cudaStreamDestroy(s);
+  return st;
 }
 
 }  // namespace
@@ -207,6 +407,14 @@ ara_status ara_server_create(ara_portfolio* pool, int64_t n_trials, const int64_
     memory_budget = (int64_t)(0.8 * (double)free_b);
   }
   S->budget = memory_budget;
+  {
+    DeviceGuard g(pool->device);
+    const ara_status st = warm_up(*S);
+    if (st != ARA_OK) {
+      delete S;
+      return st;
+    }
+  }
   for (int i = 0; i < max_concurrent; ++i) S->workers.emplace_back(worker_main, S);
   *out = S;
   return ARA_OK;
@@ -298,6 +506,26 @@ ara_status ara_server_stats(ara_server* S, int32_t* queued_or_running, int32_t* 
   if (peak_running) *peak_running = S->peak_running;
   if (peak_bytes) *peak_bytes = S->peak_in_use;
   if (budget) *budget = S->budget;
+  return ARA_OK;
+}
+
+ara_status ara_server_set_merging(ara_server* S, int32_t max_requests_per_pass, double min_overlap) {
+  if (!S || max_requests_per_pass < 1 || max_requests_per_pass > BT_MAX_REQ || !(min_overlap > 0.0) ||
+      min_overlap > 1.0)
+    return ARA_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->max_merge = max_requests_per_pass;
+  S->min_overlap = min_overlap;
+  return ARA_OK;
+}
+
+ara_status ara_server_counters(ara_server* S, int64_t* passes, int64_t* merged_requests,
+                               int64_t* head_passed) {
+  if (!S) return ARA_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (passes) *passes = S->n_passes;
+  if (merged_requests) *merged_requests = S->n_merged;
+  if (head_passed) *head_passed = S->n_head_passed;
   return ARA_OK;
 }
 

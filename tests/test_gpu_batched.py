@@ -140,3 +140,49 @@ def test_plan_skips_and_reports_out_of_range_ids(case):
     assert torch.equal(y[:, keep], single[:, keep])
     plan.close()
     g.close()
+
+
+@pytest.mark.parametrize("requests", [
+    # (layer_begin, layer_end, trial_begin, trial_end): trials [1500, 2400) are covered by the
+    # first and the third request but not the middle one, whose entries those trials skip
+    [(0, 7, 0, 2400), (7, 9, 1000, 1500), (9, 20, 1200, 3000)],
+    # four requests: a middle pair uncovered together, single-request stretches, a one-trial
+    # request and a request covering everything
+    [(0, 3, 0, 900), (3, 5, 100, 101), (5, 12, 400, 700), (12, 20, 0, 3000)],
+    # one request over every layer and trial: the plain batched pass
+    [(0, 20, 0, 3000)],
+])
+def test_requests_in_one_pass_equal_each_request_alone(case, requests):
+    """ara_run_ylt_requests: several requests' layers over different trial slices in one pass.
+    Each request's YLT and regimes equal the single-layer path on its own layers and slice, bit
+    for bit, and the oracle within the YLT tolerance."""
+    pf, yet, ref, agg = case
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    ys, regs = g.run_ylt_requests(off, ids, requests, regimes=True)
+    g.check()
+    for (l0, l1, t0, t1), y, rg in zip(requests, ys, regs):
+        sub_off = off[t0:t1 + 1]
+        reg = torch.empty((l1 - l0, t1 - t0), dtype=torch.uint8, device="cuda")
+        alone = g.run_ylt(sub_off, ids, layers=list(range(l0, l1)), regimes=reg)
+        g.check()
+        assert torch.equal(y, alone)
+        assert torch.equal(rg, reg)
+        err = np.abs(y.cpu().numpy() - ref[l0:l1, t0:t1])
+        assert np.all(err <= 1e-6 * np.abs(ref[l0:l1, t0:t1]) + 1e-12 * np.abs(agg[l0:l1, t0:t1]))
+    g.close()
+
+
+def test_requests_in_one_pass_reject_bad_arguments(case):
+    pf, yet, _, _ = case
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    bad = [[(0, 10, 0, 100)],                                   # layers not all covered
+           [(0, 10, 0, 100), (10, 20, 50, 3001)],               # trials past the end
+           [(0, 10, 5, 5), (10, 20, 0, 10)],                    # empty trial range
+           [(0, 4, 0, 9), (4, 8, 0, 9), (8, 12, 0, 9), (12, 16, 0, 9), (16, 20, 0, 9)]]  # 5 requests
+    for rq in bad:
+        with pytest.raises(ara.AraError) as e:
+            g.run_ylt_requests(off, ids, rq)
+        assert e.value.status in (ara.ARA_EINVAL, ara.ARA_ERANGE)
+    g.close()

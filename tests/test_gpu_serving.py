@@ -129,3 +129,53 @@ def test_server_rejects_invalid_queries(world):
         assert e.value.status == ara.ARA_EINVAL
     srv.wait(srv.submit(**good))
     srv.close()
+
+
+def test_server_merges_overlapping_requests_with_identical_results(world):
+    """Queued requests whose slices overlap run merged, several per pass over the union of their
+    slices; every result (PML, TVaR, mean, layer-term gradients) equals the same request served
+    with merging off, bit for bit, and the oracle within the YLT tolerance."""
+    pool_tables, yet, pool, off, ev = world
+    rng = np.random.default_rng(17)
+    qs = random_queries(16, 13, yet.n_trials)
+    for q in qs:                                      # heavily overlapping slices
+        t0 = int(rng.integers(0, 1500))
+        q["trials"] = (t0, int(rng.integers(4000, yet.n_trials + 1)))
+    srv = ara.Server(pool, off, ev, max_concurrent=1, max_merge=4, min_overlap=0.1)
+    merged = [srv.wait(t) for t in [srv.submit(**q) for q in qs]]
+    cnt = srv.counters()
+    srv.close()
+    assert cnt["merged_requests"] >= 2 and cnt["passes"] < len(qs)
+    alone_srv = ara.Server(pool, off, ev, max_concurrent=1, max_merge=1)
+    for q, m in zip(qs, merged):
+        a = alone_srv.wait(alone_srv.submit(**q))
+        for k in ("pml", "tvar", "mean", "grad_layer"):
+            if a[k] is None:
+                assert m[k] is None
+            else:
+                assert np.array_equal(a[k], m[k]), k
+    assert alone_srv.counters()["merged_requests"] == 0
+    alone_srv.close()
+    for q, m in list(zip(qs, merged))[:3]:
+        t0, t1 = q["trials"]
+        sub = synth.YET(yet.offsets[t0:t1 + 1] - yet.offsets[t0],
+                        yet.event_ids[yet.offsets[t0]:yet.offsets[t1]])
+        tab = synth.Portfolio(C, pool_tables.elt_ids, pool_tables.elt_losses, pool_tables.elt_ret,
+                              pool_tables.elt_lim, q["layer_elts"], np.asarray(q["occ_ret"]),
+                              np.asarray(q["occ_lim"]), np.asarray(q["agg_ret"]),
+                              np.asarray(q["agg_lim"]))
+        y = oracle.ylt(tab, sub)
+        p, t = oracle.risk_metrics(y, q["return_periods"], q["tvar_levels"])
+        np.testing.assert_allclose(m["pml"], p, rtol=1e-6)
+        np.testing.assert_allclose(m["tvar"], t, rtol=1e-6)
+        np.testing.assert_allclose(m["mean"], y.mean(1), rtol=1e-6)
+
+
+def test_server_merging_arguments(world):
+    pool_tables, yet, pool, off, ev = world
+    srv = ara.Server(pool, off, ev, max_concurrent=1)
+    for bad in [(0, 0.3), (5, 0.3), (2, 0.0), (2, 1.5)]:
+        with pytest.raises(ara.AraError):
+            srv.set_merging(*bad)
+    srv.set_merging(1)
+    srv.close()
