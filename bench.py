@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-oep", action="store_true", help="skip the occurrence-basis measurement")
     ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--no-layouts", action="store_true", help="skip the layout-variant timings")
     return ap.parse_args()
 
 
@@ -115,10 +116,15 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a while to start: the region begins once it has sampled
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.005)
+            self.lines.clear()
         except Exception:
             self.proc = None
         return self
@@ -189,11 +195,13 @@ def stream_kernel_name(flags):
     return "k_ylt_bulk"
 
 
-def ncu_traffic_per_launch():
-    """DRAM bytes per event of the YET-stream kernel from the committed ncu summary
-    (profiles/k_ylt_bulk_paper_scale.md: lines 'dram_bytes_per_event: X' and
-    'kernel_source_sha: Y'); None when absent or when the kernel source changed since."""
+def ncu_profile_figures():
+    """Per-occurrence figures of the YET-stream kernel from the committed ncu summary
+    (profiles/k_ylt_bulk_paper_scale.md, lines 'key: value'): dram_bytes_per_event,
+    l2_hit_rate_pct, gather_sectors_per_event.  Empty when the summary is absent or was taken of
+    another kernel source (its 'kernel_source_sha' line differs)."""
     path = os.path.join(ROOT, "profiles", "k_ylt_bulk_paper_scale.md")
+    out = {}
     try:
         kv = {}
         with open(path) as f:
@@ -203,10 +211,13 @@ def ncu_traffic_per_launch():
                     k, v = line.split(":", 1)
                     kv[k.strip().strip("`")] = v.strip().strip("`")
         if kv.get("kernel_source_sha") != kernel_source_sha():
-            return None
-        return float(kv["dram_bytes_per_event"])
+            return out
+        for k in ("dram_bytes_per_event", "l2_hit_rate_pct", "gather_sectors_per_event"):
+            if k in kv:
+                out[k] = float(kv[k].split()[0])
     except Exception:
-        return None
+        pass
+    return out
 
 
 def kernel_source_sha():
@@ -338,14 +349,15 @@ def run_ours(args, rank, ws, local):
     n0 = ara.launch_count()
     barrier(ws)
     torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for k in range(args.steps):
-            step(k)
-        e1.record(stream)
-        torch.cuda.synchronize()
+    # clocks sampled from here through the end-to-end runs below
+    clk = ClockSampler(torch.cuda.current_device()).__enter__()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
     barrier(ws)
     launches = (ara.launch_count() - n0)
     ms = e0.elapsed_time(e1) / args.steps
@@ -387,11 +399,40 @@ def run_ours(args, rank, ws, local):
         barrier(ws)
         return t
 
+    def e2e_breakdown(flags, reps=3):
+        """Where one end-to-end call's time goes: per-class times from CUDA events on the
+        streams they run on (fold, stream kernel, selection, the library's own copies) and the
+        host-timed offset check; the rest (launch, synchronisation and small result copies) is
+        the difference to the call's wall time."""
+        torch.cuda.synchronize()
+        ara.timing_reset()
+        ara.timing_enable(True)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            g.run_ylt_host(off_np, ids_np, out=ylt_np, return_periods=RPS, tvar_levels=LEVELS, flags=flags)
+        wall = (time.perf_counter() - t0) / reps * 1e3
+        ara.timing_enable(False)
+        out = {"wall_ms": round(wall, 3)}
+        for name, k in (("fold_ms", ara.ARA_K_FOLD), ("stream_ms", ara.ARA_K_YLT),
+                        ("select_ms", ara.ARA_K_SELECT), ("copies_ms", ara.ARA_K_TRANSFER),
+                        ("host_offset_check_ms", ara.ARA_K_HOST_CHECK)):
+            ms, n = ara.timing_read(k)
+            out[name] = round(ms / reps, 3)
+        serial = out["fold_ms"] + out["stream_ms"] + out["select_ms"]
+        if flags & ara.ARA_RUN_HOST_DIRECT:
+            serial += out["copies_ms"]          # only the YLT copy, after the kernels
+        out["rest_ms"] = round(wall - serial, 3)
+        return out
+
     e2e_staged = e2e_time(args.flags)
+    staged_parts = e2e_breakdown(args.flags)
     try:
         e2e_direct = e2e_time(args.flags | ara.ARA_RUN_HOST_DIRECT)
+        direct_parts = e2e_breakdown(args.flags | ara.ARA_RUN_HOST_DIRECT)
     except ara.AraError:
         e2e_direct = float("inf")
+        direct_parts = None
+    clk.__exit__(None, None, None)
     e2e_s = min(e2e_staged, e2e_direct)
     e2e_api = ("ara_run_ylt_host, ARA_RUN_HOST_DIRECT (kernel reads the pinned host YET over the CPU-GPU link)"
                if e2e_direct <= e2e_staged else "ara_run_ylt_host (chunked H2D copies overlapped with kernels)")
@@ -403,14 +444,28 @@ def run_ours(args, rank, ws, local):
     alg_bytes = 4 * n_events + 8 * (n_trials + 1) + 8 * n_trials + 8 * CATALOGUE
     per_launch_ms = ylt_ms / max(ylt_n, 1)
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    tpe = ncu_traffic_per_launch()
+    prof = ncu_profile_figures()
+    tpe = prof.get("dram_bytes_per_event")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": (tpe * n_events if tpe else None),
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture of "
+                               "this kernel source at 1e8 occurrences "
+                               "(profiles/k_ylt_bulk_paper_scale.md), scaled per occurrence to "
+                               "this launch" if tpe else "no capture of the current kernel source"),
+            "l2_hit_rate_pct": prof.get("l2_hit_rate_pct"),
+            "gather_sectors_per_occurrence": prof.get("gather_sectors_per_event"),
+            "l2_source": "same ncu capture" if prof.get("l2_hit_rate_pct") is not None else None,
             "peak_source": peak_kind, "kernel": stream_kernel_name(args.flags),
             "alg_bytes_per_launch": alg_bytes, "ms_per_launch": round(per_launch_ms, 4),
-            "frac_8byte_events": round((alg_bytes + 4 * n_events) / (per_launch_ms / 1e3) / 1e9 / peak, 4)}
+            "frac_8byte_events": round((alg_bytes + 4 * n_events) / (per_launch_ms / 1e3) / 1e9 / peak, 4),
+            "frac_of_nominal_8tbs": round(achieved / 8000.0, 4),
+            "frac_basis": "frac: 4 B of event ID per occurrence (timestamps are never read) + "
+                          "offsets + YLT + the q table once, over the measured copy bandwidth; "
+                          "frac_8byte_events adds 4 B of timestamp per occurrence; "
+                          "frac_of_nominal_8tbs divides by 8 TB/s instead"}
 
     oep_line = None if args.no_oep else measure_oep(g, off, ids, ylt, lookups_per_step)
+    layout_line = None if args.no_layouts else measure_layouts(pf, g, off, ids, ylt, n_events)
     g.close()
     del ids, off, ylt
     torch.cuda.empty_cache()
@@ -451,13 +506,23 @@ def run_ours(args, rank, ws, local):
                         "ms_per_step": e2e_s * 1e3, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "api": e2e_api,
                         "ms_per_step_staged": e2e_staged * 1e3,
-                        "ms_per_step_direct": (e2e_direct * 1e3 if e2e_direct != float("inf") else None)},
+                        "ms_per_step_direct": (e2e_direct * 1e3 if e2e_direct != float("inf") else None),
+                        "link_floor_ms": round(h2d / 211e9 * 1e3, 3),
+                        "link_floor_basis": "h2d bytes / 211 GB/s, the host-to-device rate measured "
+                                            "on this box for copies and for SM loads of host memory",
+                        "breakdown_direct": direct_parts, "breakdown_staged": staged_parts},
+                "layout_variants": layout_line,
+                "occurrences_per_s": n_events * ws / (ms_max / 1e3),
+                "metric_note": "logical (occurrence, ELT) pairs, 15 per occurrence; the folded "
+                               "path makes at most one table gather per occurrence (the "
+                               "occurrences that pass the shared-memory hit filter)",
                 "oep": oep_line,
                 "adjoint": adjoint_line,
                 "batched": batched_line,
                 "serving": serving_line,
                 "gpu_launches": launches,
-                "clocks": clk.summary(),
+                "clocks": dict(clk.summary(), covers="the timed steps, their event-timed repeat "
+                               "and the end-to-end runs (nvidia-smi every 20 ms)"),
                 "results": {"pml100": float(pml[0, 0]), "pml250": float(pml[0, 1]),
                             "tvar99": float(tvar[0, 0])}}
         print(json.dumps(line), flush=True)
@@ -481,6 +546,43 @@ def measure_oep(g, off, ids, ylt, lookups: int, reps: int = 20):
     ms = e0.elapsed_time(e1) / reps
     return {"workload": "paper scale, occurrence basis (largest net occurrence loss per trial)",
             "ms_per_run": round(ms, 4), "lookups_per_s": lookups / (ms / 1e3)}
+
+
+def measure_layouts(pf, g, off, ids, ylt, n_events: int, reps: int = 5):
+    """The YET-stream kernel at paper scale under the layouts the ELT lookup can take: the folded
+    per-event table behind the shared-memory hit filter (the default), the same table without the
+    filter (a gather for every occurrence), and the literal direct-access tables of every ELT
+    (dense FP32 [15][catalogue], 15 lookups per occurrence).  Kernel time only (CUDA events
+    around each stream launch), results compared with the default's."""
+    import torch
+    import paper_1606_04473_gb300 as ara
+
+    def kernel_ms(port, flags):
+        y = torch.empty_like(ylt)
+        port.run_ylt(off, ids, out=y, flags=flags)
+        torch.cuda.synchronize()
+        ara.timing_reset()
+        ara.timing_enable(True)
+        for _ in range(reps):
+            port.run_ylt(off, ids, out=y, flags=flags)
+        torch.cuda.synchronize()
+        ara.timing_enable(False)
+        port.check()
+        ms, n = ara.timing_read(ara.ARA_K_YLT)
+        return ms / max(n, 1), y
+
+    base_ms, y0 = kernel_ms(g, 0)
+    nf_ms, y1 = kernel_ms(g, ara.ARA_RUN_NO_FILTER)
+    dense = ara.Portfolio.from_tables(pf, dense_tables=True)
+    pe_ms, y2 = kernel_ms(dense, ara.ARA_RUN_PER_ELT)
+    dense.close()
+    same = bool(torch.equal(y0, y1) and torch.equal(y0, y2))
+    return {"folded_filtered_ms": round(base_ms, 4), "folded_no_filter_ms": round(nf_ms, 4),
+            "per_elt_dense_fp32_ms": round(pe_ms, 4),
+            "per_elt_lookups_per_s": n_events * N_ELTS / (pe_ms / 1e3),
+            "results_identical": same,
+            "note": "kernel time of the YET stream only; the folded layouts add a fold of "
+                    "the 2M-event catalogue per run (see kernel_ms)"}
 
 
 def measure_adjoint(rank: int, reps: int = 5):
@@ -521,9 +623,55 @@ def measure_adjoint(rank: int, reps: int = 5):
     out = {"workload": "16 layers x 15 ELTs (2M catalogue, 20k events each), 2e5 trials x 1000 events",
            "forward_ms": round(f_ms, 3), "adjoint_ms": round(a_ms, 3), "ratio": round(a_ms / f_ms, 3),
            "objectives": "mean year loss and TVaR99 per layer; gradients w.r.t. every retention, "
-                         "limit and ELT loss"}
+                         "limit and ELT loss",
+           "check": check_adjoint(pf, yet, g, off, ids, y, reg)}
     g.close()
     return out
+
+
+def check_adjoint(pf, yet, g, off, ids, y, reg, sel=(0, 1), slice_trials: int = 4000):
+    """The timed adjoint against the FP64 oracle's chain rule (rtol 1e-4): the TVaR99 gradients
+    of two layers over the whole YET, read from the timed computation's own output (the oracle
+    follows only the top trials back), and both objectives of the same layers on the first
+    slice_trials trials of the same device YET (the mean objective needs every trial)."""
+    import oracle
+    import synth
+    sel = list(sel)
+    sub = pf.with_terms(pf.terms_dict())
+    sub.layer_elts = [pf.layer_elts[i] for i in sel]
+    for name in ["occ_ret", "occ_lim", "agg_ret", "agg_lim"]:
+        setattr(sub, name, np.asarray(getattr(pf, name))[sel])
+    k_slots = sum(len(pf.layer_elts[i]) for i in sel)
+    m_recs = sum(pf.elt_ids[j].size for i in sel for j in pf.layer_elts[i])
+    worst = 0.0
+
+    def rel(got, want):
+        got, want = np.asarray(got), np.asarray(want)
+        scale = max(1.0, float(np.abs(want).max())) if want.size else 1.0
+        return float(np.max(np.abs(got - want) / (1e-4 * np.abs(want) + 1e-12 * scale))) if want.size else 0.0
+
+    t0 = time.perf_counter()
+    full = g.adjoint(off, ids, y, reg, 0.99)
+    ref = oracle.adjoint(sub, yet, "tvar", 0.99)
+    worst = max(worst, rel(full["elt"][1][:k_slots].cpu().numpy(), ref["elt"]),
+                rel(full["layer"][1][:len(sel)].cpu().numpy(), ref["layer"]),
+                rel(full["loss"][1][:m_recs].cpu().numpy(), ref["loss"]))
+    import torch
+    n = slice_trials
+    ys = synth.YET(yet.offsets[:n + 1], yet.event_ids[:int(yet.offsets[n])])
+    reg_s = torch.empty((len(sel), n), dtype=torch.uint8, device="cuda")
+    y_s = g.run_ylt(off[:n + 1], ids, layers=sel, regimes=reg_s)
+    part = g.adjoint(off[:n + 1], ids, y_s, reg_s, 0.99, layers=sel)
+    g.check()
+    for obj, name in ((0, "mean"), (1, "tvar")):
+        r = oracle.adjoint(sub, ys, name, 0.99)
+        worst = max(worst, rel(part["elt"][obj].cpu().numpy(), r["elt"]),
+                    rel(part["layer"][obj].cpu().numpy(), r["layer"]),
+                    rel(part["loss"][obj].cpu().numpy(), r["loss"]))
+    return {"ok": bool(worst <= 1.0), "worst_error_over_tolerance": round(worst, 6),
+            "what": f"TVaR99 gradients of layers {sel} over all trials; mean and TVaR99 "
+                    f"gradients of the same layers on the first {n} trials; rtol 1e-4 against "
+                    "the FP64 chain-rule oracle", "seconds": round(time.perf_counter() - t0, 1)}
 
 
 def measure_batched(rank: int, reps: int = 5):
@@ -566,25 +714,55 @@ def measure_batched(rank: int, reps: int = 5):
     plan_ms = timed(plan.launch)
     g.check()
     identical = bool(torch.equal(plan.out, y_seq))
+    info = plan.info()
+    # Roofline of the stream kernel (its autotuned time, CUDA events around the launch): the bytes
+    # it gathers per pass are every occurrence's ID and row descriptor and every table entry of
+    # its row, plus the trial offsets and the YLT writes.
+    rows, n_entries = plan.table()
+    lens = (rows >> 32) & 0xFF
+    freq = torch.bincount(ids.long(), minlength=pf.catalogue)
+    walked = int((lens * freq).sum().item())
+    n_occ = int(yet.n_events)
+    alg = 4 * n_occ + 8 * n_occ + 8 * walked + 8 * (yet.n_trials + 1) + 8 * pf.n_layers * yet.n_trials
+    peak, peak_kind = measured_peaks()
+    stream_ms = info["tuned_ms"]
+    roof = {"bound": "l1 / l2 gathers and shared-memory atomics (not hbm)",
+            "alg_bytes_per_launch": alg, "entries_walked": walked, "table_entries": n_entries,
+            "table_mb": round(8 * n_entries / 1e6, 1), "stream_ms": round(stream_ms, 4),
+            "achieved_gbs": round(alg / (stream_ms / 1e3) / 1e9, 1), "peak_gbs": peak,
+            "frac": round(alg / (stream_ms / 1e3) / 1e9 / peak, 4), "peak_source": peak_kind,
+            "bytes": "4 B ID + 8 B row descriptor per occurrence, 8 B per table entry walked, "
+                     "offsets, 8 B YLT per (layer, trial); gathered bytes, not DRAM traffic"}
+    plan.close()
+    # The same 64 layers as two plans of 32, each table about half the size, run back to back.
+    plans = [ara.BatchedPlan(g, off, ids, layers=list(range(h * 32, h * 32 + 32)), autotune=True)
+             for h in range(2)]
+    split_ms = timed(lambda: [p.launch() for p in plans])
+    split_tables = [round(8 * p.table()[1] / 1e6, 1) for p in plans]
+    for p in plans:
+        p.close()
     out = {"workload": "64 layers x U{3..30} ELTs from a pool of 200 (2M catalogue), 2e5 trials x "
                        "Poisson(U[200,2000]) events",
-           "events": int(yet.n_events), "lookups_per_pass": lookups,
+           "events": n_occ, "lookups_per_pass": lookups,
            "sequential_ms": round(seq_ms, 3), "batched_ms": round(plan_ms, 3),
            "speedup": round(seq_ms / plan_ms, 3),
            "batched_lookups_per_s": lookups / (plan_ms / 1e3),
-           "identical_to_sequential": identical, "schedule": plan.info(),
-           "plan_build_s": round(t_plan, 3)}
-    plan.close()
+           "identical_to_sequential": identical, "schedule": info,
+           "plan_build_s": round(t_plan, 3), "roofline": roof,
+           "split_two_plans_of_32_layers_ms": round(split_ms, 3),
+           "split_table_mb": split_tables}
     g.close()
     return out
 
 
-def measure_serving(rank: int, n_requests: int = 200, workers: int = 2, low_rate: float = 50.0):
+def measure_serving(rank: int, n_requests: int = 200, workers: int = 1, low_rate: float = 50.0):
     """Serving: a seeded Poisson stream (200 requests/s, 32 tenants) of risk queries over a
     resident pool of 500 ELTs and a resident YET of 1e6 trials x Poisson(1000) events (1-32
     layers of 5-20 ELTs each, slices of 1e4-1e6 trials, 20 % with the adjoint), served by the
     native server: continuous admission by device memory, queued requests with overlapping slices
-    merged into one YET pass (up to 4), groups overlapping on separate streams.  Compared with
+    merged into one YET pass (up to 4); by default one worker (a second worker, whose host work
+    and small kernels overlap the first's passes, measured no faster; reported beside it).
+    Compared with
     the same queries run one at a time (one worker, no merging; the batched path for requests of
     4 or more layers, as in the served mode) and with sequential plain runs (one at a time, every
     layer by the single-layer path).  The same queries arrive again at low_rate requests/s, below
@@ -645,6 +823,7 @@ def measure_serving(rank: int, n_requests: int = 200, workers: int = 2, low_rate
         return res, arm
 
     res_s, served = serve(workers, 4)
+    res_2, served_2 = serve(2, 4)
     res_1, one = serve(1, 1)
     res_p, plain = serve(1, 1, plain=True)
     stretch = 200.0 / low_rate
@@ -652,11 +831,12 @@ def measure_serving(rank: int, n_requests: int = 200, workers: int = 2, low_rate
     res_1l, one_low = serve(1, 1, stretch=stretch)
     keys = ("pml", "tvar", "mean", "grad_layer")
     same = all(all((a[k] is None and b[k] is None) or np.array_equal(a[k], b[k]) for k in keys)
-               for other in (res_s, res_p, res_sl, res_1l) for a, b in zip(other, res_1))
+               for other in (res_s, res_2, res_p, res_sl, res_1l) for a, b in zip(other, res_1))
     out = {"workload": f"{n_requests} requests, Poisson 200/s, 32 tenants; 1-32 layers x 5-20 ELTs of a "
                        "500-ELT pool; slices of 1e4-1e6 trials of a 1e6 x Poisson(1000) YET; 20% adjoint",
            "offered_load_high": "200 requests/s (above capacity: latencies include queueing)",
-           "served": served, "one_at_a_time": one, "sequential_plain": plain,
+           "served": served, "served_2_workers": served_2, "one_at_a_time": one,
+           "sequential_plain": plain,
            "offered_load_low": f"{low_rate:g} requests/s (the same queries, arrivals stretched "
                                f"x{stretch:g})",
            "served_low_load": served_low, "one_at_a_time_low_load": one_low,

@@ -177,7 +177,10 @@ ARA_API ara_status ara_run_ylt(ara_portfolio* pf, int64_t n_trials, const int64_
  * on `stream`, so host-to-device traffic overlaps the kernels (pinned host memory gives full
  * link bandwidth); the YLT stays on the device for the risk metrics and is copied back.
  * Synchronous: returns when every output is written.
- *   h_trial_offsets host [n_trials + 1], [0] = 0, non-decreasing (validated: ARA_EINVAL)
+ *   h_trial_offsets host [n_trials + 1], [0] = 0, non-decreasing (validated: ARA_EINVAL; with
+ *                   ARA_RUN_HOST_DIRECT the check runs on the host while the kernels already read
+ *                   the YET, whose own bounds checks keep bad offsets harmless; a rejected call
+ *                   still waits for them and clears the device error word, as ara_check does)
  *   h_event_ids     host [h_trial_offsets[n_trials]]
  *   h_ylt           host [n_layer_sel][n_trials] or NULL (then only the metrics are returned)
  *   n_rp, return_periods, n_tvar, tvar_levels, h_pml, h_tvar, h_mean: as in
@@ -229,6 +232,12 @@ ARA_API ara_status ara_plan_launch(ara_plan* plan, void* stream);
  * time of one stream kernel in ms (0 without ARA_PLAN_AUTOTUNE). */
 ARA_API ara_status ara_plan_info(ara_plan* plan, int32_t* warps, int32_t* blocks_per_sm,
                                  int32_t* trials_per_grab, double* tuned_ms);
+/* The plan's event-major table, for measurement: d_rows receives its device array of row
+ * descriptors [catalogue] (bits 0..31: the event's first table entry; byte 4: the number of its
+ * entries, one per selected layer whose occurrence loss for the event is non-zero), valid until
+ * the plan is destroyed and rewritten by every launch; n_entries the table's entry count.
+ * Synchronises the device.  Errors: ARA_EINVAL, ARA_ECUDA. */
+ARA_API ara_status ara_plan_table(ara_plan* plan, const uint64_t** d_rows, int64_t* n_entries);
 ARA_API void ara_plan_destroy(ara_plan* plan);
 
 /*
@@ -295,9 +304,15 @@ typedef struct ara_query {
  * least 30 % of their union, see ara_server_set_merging), best overlap first, while their
  * memory fits: the group's layers run in one batched pass over the union of the slices, each
  * trial walking only the table entries of the requests that cover it, so the requests share the
- * reading of the YET.  Creation runs a few small warm-up requests (synchronous), so the first
- * real requests pay no one-time costs.  The pool and the YET must outlive the server.  Results
- * of a request do not depend on what else runs or on the group it ran in (bitwise).
+ * reading of the YET (a group's table is kept near L2 size).  The workers' YET passes (batched
+ * or single-layer streams, adjoint histograms) run one after the other on the device, each
+ * queued behind the previous one; their folds, selections and host work overlap.  While a
+ * server exists, the device's default memory pool keeps up to memory_budget bytes of freed
+ * memory cached (its release threshold is raised; the previous value is restored when the last
+ * server on the device is destroyed).  Creation runs a few small warm-up requests
+ * (synchronous), so the first real requests pay no one-time costs.  The pool and the YET must
+ * outlive the server.  Results of a request do not depend on what else runs or on the group it
+ * ran in (bitwise).
  */
 ARA_API ara_status ara_server_create(ara_portfolio* pool, int64_t n_trials,
                                      const int64_t* d_trial_offsets, int64_t n_events,
@@ -501,11 +516,16 @@ ARA_API ara_status ara_debug_set(int32_t key, int64_t value);
 #define ARA_K_SELECT  2   /* PML / TVaR selection (all of its launches) */
 #define ARA_K_ADJOINT 3   /* adjoint kernels */
 #define ARA_K_BATCHED 4   /* one replay of a batched-portfolio plan (its whole CUDA graph) */
-#define ARA_K_COUNT   5
+#define ARA_K_TRANSFER 5  /* ara_run_ylt_host's own copies: host-to-device YET chunks (staged
+                             mode) and the device-to-host YLT */
+#define ARA_K_HOST_CHECK 6 /* ara_run_ylt_host's host-side check of the trial offsets: host wall
+                             time, not device time */
+#define ARA_K_COUNT   7
 
 /* When enabled, CUDA events are recorded on the launching stream around every launch of
- * each kernel class.  ara_timing_read synchronises those events and returns the summed
- * device time (ms) and the number of launches since the last reset. */
+ * each kernel class (and every copy of ARA_K_TRANSFER; ARA_K_HOST_CHECK is timed on the host).
+ * ara_timing_read synchronises those events and returns the summed time (ms) and the number of
+ * launches (copies, checks) since the last reset. */
 ARA_API void ara_timing_enable(int32_t on);
 ARA_API void ara_timing_reset(void);
 ARA_API ara_status ara_timing_read(int32_t kernel_class, double* total_ms, int64_t* launches);

@@ -44,6 +44,7 @@ class Query(ctypes.Structure):
                 ("want_adjoint", ctypes.c_int32), ("adjoint_level", ctypes.c_double),
                 ("flags", ctypes.c_int32), ("tenant", ctypes.c_int32)]
 ARA_K_FOLD, ARA_K_YLT, ARA_K_SELECT, ARA_K_ADJOINT, ARA_K_BATCHED = 0, 1, 2, 3, 4
+ARA_K_TRANSFER, ARA_K_HOST_CHECK = 5, 6
 ARA_PLAN_AUTOTUNE = 1
 
 _lib = None
@@ -89,6 +90,8 @@ def lib() -> ctypes.CDLL:
     L.ara_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                 ctypes.POINTER(d)]
     L.ara_plan_info.restype = i32
+    L.ara_plan_table.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(i64)]
+    L.ara_plan_table.restype = i32
     L.ara_plan_destroy.argtypes = [P]
     L.ara_plan_destroy.restype = None
     L.ara_create_layer_set.argtypes = [P, i32, P, P, P, P, P, P, P, ctypes.POINTER(P)]
@@ -400,6 +403,22 @@ class BatchedPlan:
                                    ctypes.byref(ms)), "ara_plan_info")
         return {"warps": w.value, "blocks_per_sm": c.value, "trials_per_grab": t.value,
                 "tuned_ms": ms.value}
+
+    def table(self):
+        """(row descriptors, entries): the plan's event-major table for measurement
+        (ara_plan_table) as an int64 device tensor [catalogue] viewing the plan's own array (valid
+        while the plan lives; bits 32..39 of a descriptor: the event's number of entries), and
+        the table's entry count."""
+        import torch
+        p, n = ctypes.c_void_p(), ctypes.c_int64()
+        _check(lib().ara_plan_table(self._h, ctypes.byref(p), ctypes.byref(n)), "ara_plan_table")
+
+        class _View:
+            pass
+        v = _View()
+        v.__cuda_array_interface__ = {"shape": (self._keep[0].catalogue,), "typestr": "<i8",
+                                      "data": (p.value, False), "version": 3}
+        return torch.as_tensor(v, device=self._keep[1].device), n.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -3,6 +3,7 @@
 // overlapped with Algorithm 3's kernels), data-error reporting and timing.
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -76,6 +77,13 @@ void timing_end(int k, cudaStream_t s) {
   if (e && cudaEventRecord(e, s) == cudaSuccess) g_pending[k].push_back({t_open[k], e});
   t_open[k] = nullptr;
   if (g_pending[k].size() > 4096) drain(k);
+}
+
+void timing_add_host(int k, double ms) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  if (!g_timing) return;
+  g_total_ms[k] += ms;
+  g_count[k] += 1;
 }
 
 bool timing_suspend() {
@@ -629,16 +637,26 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
     return ARA_EINVAL;
   if (flags & ARA_RUN_BATCHED) return ARA_EINVAL;
   if (h_off[0] != 0) return ARA_EINVAL;
-  bool decreasing = false;   // no early exit, so the scan vectorises
-  for (int64_t t = 0; t < n_trials; ++t) decreasing |= h_off[t + 1] < h_off[t];
-  if (decreasing) return ARA_EINVAL;
+  // Host check that the offsets never decrease (no early exit, so the scan vectorises), timed
+  // under ARA_K_HOST_CHECK.
+  auto offsets_decrease = [&]() {
+    const auto c0 = std::chrono::steady_clock::now();
+    bool decreasing = false;
+    for (int64_t t = 0; t < n_trials; ++t) decreasing |= h_off[t + 1] < h_off[t];
+    timing_add_host(ARA_K_HOST_CHECK,
+                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c0).count());
+    return decreasing;
+  };
+  const bool direct = (flags & ARA_RUN_HOST_DIRECT) != 0;
+  if (!direct && offsets_decrease()) return ARA_EINVAL;   // the chunk cuts rely on the order
   const int64_t n_events = h_off[n_trials];
-  if (sel.empty() || n_trials == 0) return ARA_OK;
+  if (n_events < 0) return ARA_EINVAL;
+  if (sel.empty() || n_trials == 0) return direct && offsets_decrease() ? ARA_EINVAL : ARA_OK;
   if (n_events > 0 && !h_ids) return ARA_EINVAL;
   if (!h_ylt && !metrics) return ARA_EINVAL;
   DeviceGuard g(pf->device);
   cudaStream_t s = (cudaStream_t)stream;
-  if (flags & ARA_RUN_HOST_DIRECT) {
+  if (direct) {
     // The device reads the host arrays in place: they must be mapped into its address space.
     void* d_off_v = nullptr;
     void* d_ids_v = nullptr;
@@ -665,6 +683,12 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
     a.row_stride = n_trials;
     a.flags = f;
     if ((st = launch_ylt(*pf, a, s)) != ARA_OK) return st;
+    // The offsets are checked while the kernels run: they bound every offset they read, so
+    // decreasing offsets only make them record a data error, which ara_check clears.
+    if (offsets_decrease()) {
+      ara_check(pf, stream);
+      return ARA_EINVAL;
+    }
   } else {
   // chunk boundaries: at most CH_EVENTS events and CH_TRIALS trials per chunk
   const int64_t CH_EVENTS = (int64_t)1 << 24, CH_TRIALS = (int64_t)1 << 20;
@@ -693,11 +717,13 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
     const int64_t t0 = cut[c], t1 = cut[c + 1], nt = t1 - t0;
     const int64_t e0 = h_off[t0], ne = h_off[t1] - e0;
     ARA_TRY(cudaStreamWaitEvent(pf->copy_stream, pf->ev_done[b], 0));
+    timing_begin(ARA_K_TRANSFER, pf->copy_stream);
     if (ne > 0)
       ARA_TRY(cudaMemcpyAsync(pf->d_stage_ids[b], h_ids + e0, sizeof(int32_t) * (size_t)ne,
                               cudaMemcpyHostToDevice, pf->copy_stream));
     ARA_TRY(cudaMemcpyAsync(pf->d_stage_off[b], h_off + t0, sizeof(int64_t) * (size_t)(nt + 1),
                             cudaMemcpyHostToDevice, pf->copy_stream));
+    timing_end(ARA_K_TRANSFER, pf->copy_stream);
     ARA_TRY(cudaEventRecord(pf->ev_copied[b], pf->copy_stream));
     ARA_TRY(cudaStreamWaitEvent(s, pf->ev_copied[b], 0));
     YltArgs a{};
@@ -716,9 +742,12 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
     ARA_TRY(cudaEventRecord(pf->ev_done[b], s));
   }
   }  // staged copies
-  if (h_ylt)
+  if (h_ylt) {
+    timing_begin(ARA_K_TRANSFER, s);
     ARA_TRY(cudaMemcpyAsync(h_ylt, pf->d_ylt_full, sizeof(double) * sel.size() * (size_t)n_trials,
                             cudaMemcpyDeviceToHost, s));
+    timing_end(ARA_K_TRANSFER, s);
+  }
   if (metrics) {
     if ((st = risk_metrics_device(pf->d_ylt_full, n_trials, (int32_t)sel.size(), n_rp, rps, n_tvar,
                                   levels, h_pml, h_tvar, h_mean, s)) != ARA_OK)

@@ -718,6 +718,19 @@ ara_status ara_plan_info(ara_plan* P, int32_t* warps, int32_t* bpsm, int32_t* tp
   return ARA_OK;
 }
 
+ara_status ara_plan_table(ara_plan* P, const uint64_t** d_rows, int64_t* n_entries) {
+  if (!P || !P->d_rows || !P->d_total) return ARA_EINVAL;
+  DeviceGuard g(P->pf->device);
+  if (d_rows) *d_rows = P->d_rows;
+  if (n_entries) {
+    uint32_t total = 0;
+    ARA_TRY(cudaDeviceSynchronize());
+    ARA_TRY(cudaMemcpy(&total, P->d_total, 4, cudaMemcpyDeviceToHost));
+    *n_entries = total;
+  }
+  return ARA_OK;
+}
+
 void ara_plan_destroy(ara_plan* P) {
   if (!P) return;
   DeviceGuard g(P->pf->device);

@@ -37,6 +37,8 @@ void timing_end(int kclass, cudaStream_t s);
 // switch event timing off (e.g. while a stream is captured into a graph); returns the old state
 bool timing_suspend();
 void timing_resume(bool was_on);
+// add a host-timed interval (ms) to a timing class (when timing is enabled)
+void timing_add_host(int kclass, double ms);
 
 // RAII helper: events around every launch of a kernel class (when timing is enabled) and
 // one count per launch.

@@ -34,6 +34,7 @@ struct Request {
   int32_t want_mean = 0, want_adjoint = 0, flags = 0, tenant = 0;
   double adjoint_level = 0.99;
   int64_t mem = 0;
+  int64_t table_bound = 0;   // upper bound of its batched table: 8 B per record of its layers' ELTs
   int32_t passed = 0;     // times a later request was admitted ahead of this one
   // results
   ara_status status = ARA_OK;
@@ -63,7 +64,17 @@ struct ara_server {
   double min_overlap = 0.3;
   int32_t window = 32;        // queued requests examined for a group or to pass a blocked head
   int32_t max_passed = 4;     // a blocked head is passed at most this many times
+  // A group's event-major table is kept near L2 size: merged passes whose table far exceeds it
+  // were measured slower than their requests run one after the other.  Bounded by 8 bytes per
+  // record of every layer's ELTs (an upper bound of the table's entries).
+  int64_t max_table_bytes = 192ll << 20;
   int64_t n_passes = 0, n_merged = 0, n_head_passed = 0;
+  // The YET passes (batched or single-layer streams, adjoint histograms) of different workers
+  // run one after the other on the device: each waits for the previous one's completion event.
+  // Concurrent passes each hold a large table in L2 and slow each other down; everything else
+  // (folds, selections, host work) still overlaps.
+  std::mutex pass_mu;
+  cudaEvent_t pass_done = nullptr;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<Request>> pending;
@@ -92,6 +103,16 @@ int64_t estimate_bytes(const Portfolio& pool, const Request& r) {
     b += 14 * C + 4 * pool.bm_words + 16 * recs + 64 * (int64_t)r.layer_elts.size() + 64 * nl;
   }
   return b;
+}
+
+// Queue one YET pass on `s` behind the previous pass of any worker.
+template <typename F>
+ara_status chained_pass(ara_server& S, cudaStream_t s, F&& launch) {
+  std::lock_guard<std::mutex> lk(S.pass_mu);
+  if (S.pass_done && cudaStreamWaitEvent(s, S.pass_done, 0) != cudaSuccess) return ARA_ECUDA;
+  const ara_status st = launch();
+  if (S.pass_done && cudaEventRecord(S.pass_done, s) != cudaSuccess && st == ARA_OK) return ARA_ECUDA;
+  return st;
 }
 
 // The metrics and the adjoint of one request whose YLT (and regimes) are computed: its layers are
@@ -123,8 +144,10 @@ ara_status finish_request(ara_server& S, Request& r, ara_portfolio* ls, int32_t 
         cudaMallocAsync((void**)&gx, 8 * (size_t)std::max<int64_t>(2 * M, 1), s) != cudaSuccess) {
       st = ARA_ENOMEM;
     } else {
-      st = ara_adjoint(ls, n, S.d_off + r.t0, S.n_events, S.d_ids, nl, sel.data(), ylt, reg,
-                       r.adjoint_level, ge, gl, gx, nullptr, s);
+      st = chained_pass(S, s, [&] {
+        return ara_adjoint(ls, n, S.d_off + r.t0, S.n_events, S.d_ids, nl, sel.data(), ylt, reg,
+                           r.adjoint_level, ge, gl, gx, nullptr, s);
+      });
       if (st == ARA_OK) {
         r.grad_layer.assign((size_t)8 * nl, 0.0);
         if (cudaMemcpyAsync(r.grad_layer.data(), gl, 8 * (size_t)(8 * nl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -165,8 +188,10 @@ void run_request(ara_server& S, Request& r, cudaStream_t s) {
       cudaMallocAsync((void**)&reg, (size_t)nl * n, s) != cudaSuccess)
     st = ARA_ENOMEM;
   if (st == ARA_OK)
-    st = ara_run_ylt(ls, n, S.d_off + r.t0, S.n_events, S.d_ids, nullptr, 0, nullptr, ylt, reg,
-                     r.flags, s);
+    st = chained_pass(S, s, [&] {
+      return ara_run_ylt(ls, n, S.d_off + r.t0, S.n_events, S.d_ids, nullptr, 0, nullptr, ylt, reg,
+                         r.flags, s);
+    });
   if (st == ARA_OK) st = finish_request(S, r, ls, 0, ylt, reg, s);
   if (st == ARA_OK) st = ara_check(ls, s);
   if (ylt) cudaFreeAsync(ylt, s);
@@ -217,7 +242,8 @@ void run_group(ara_server& S, std::vector<std::shared_ptr<Request>>& g, cudaStre
         (r.want_adjoint && cudaMallocAsync((void**)&ga.reg[k], (size_t)(nl * n), s) != cudaSuccess))
       st = ARA_ENOMEM;
   }
-  if (st == ARA_OK) st = run_batched_group_async(*static_cast<Portfolio*>(ls), ga, s);
+  if (st == ARA_OK)
+    st = chained_pass(S, s, [&] { return run_batched_group_async(*static_cast<Portfolio*>(ls), ga, s); });
   if (st == ARA_OK) st = ara_check(ls, s);
   for (int k = 0; k < nr; ++k) {
     ara_status sk = st;
@@ -271,6 +297,7 @@ std::vector<std::shared_ptr<Request>> pick_group(ara_server& S) {
   g.push_back(S.pending[lead]);
   S.pending.erase(S.pending.begin() + (long)lead);
   int64_t mem = g[0]->mem;
+  int64_t table = g[0]->table_bound;
   int32_t slots = (int32_t)g[0]->layer_off.size() - 1;
   int64_t u0 = g[0]->t0, u1 = g[0]->t1;
   while ((int)g.size() < std::min(S.max_merge, (int)BT_MAX_REQ)) {
@@ -279,7 +306,8 @@ std::vector<std::shared_ptr<Request>> pick_group(ara_server& S) {
     for (size_t i = 0; i < S.pending.size() && i < (size_t)S.window; ++i) {
       const Request& c = *S.pending[i];
       const int32_t nl = (int32_t)c.layer_off.size() - 1;
-      if (slots + nl > 255 || mem + c.mem > avail) continue;
+      if (slots + nl > 255 || mem + c.mem > avail || table + c.table_bound > S.max_table_bytes)
+        continue;
       const int64_t ov = overlap(u0, u1, c.t0, c.t1);
       const double frac = (double)ov / (double)(std::max(u1, c.t1) - std::min(u0, c.t0));
       if (ov > 0 && frac >= S.min_overlap && frac > best_ov) { best = i; best_ov = frac; }
@@ -288,6 +316,7 @@ std::vector<std::shared_ptr<Request>> pick_group(ara_server& S) {
     std::shared_ptr<Request> c = S.pending[best];
     S.pending.erase(S.pending.begin() + (long)best);
     mem += c->mem;
+    table += c->table_bound;
     slots += (int32_t)c->layer_off.size() - 1;
     u0 = std::min(u0, c->t0);
     u1 = std::max(u1, c->t1);
@@ -337,6 +366,50 @@ void worker_main(ara_server* S) {
     S->cv_work.notify_all();
   }
   if (s) cudaStreamDestroy(s);
+}
+
+// While a server runs on a device, the device's default memory pool (which the request path
+// allocates from, stream-ordered) keeps up to the server's budget of freed memory instead of
+// returning it to the system at every synchronisation: requests allocate their layer sets,
+// tables and YLTs anew, and re-mapping that memory for every request was measured at about an
+// eighth of a one-at-a-time run's time.  The pool's previous threshold is restored when the
+// last server on the device is destroyed.
+std::mutex g_pool_mu;
+struct PoolKeep {
+  int servers = 0;
+  uint64_t saved = 0;
+};
+PoolKeep g_pool_keep[64];
+
+void keep_pool_memory(int dev, int64_t budget) {
+  if (dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  cudaMemPool_t mp;
+  if (cudaDeviceGetDefaultMemPool(&mp, dev) != cudaSuccess) return;
+  PoolKeep& k = g_pool_keep[dev];
+  uint64_t cur = 0;
+  if (k.servers == 0) {
+    if (cudaMemPoolGetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &cur) != cudaSuccess) return;
+    k.saved = cur;
+  }
+  k.servers += 1;
+  cudaMemPoolGetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &cur);
+  uint64_t want = (uint64_t)std::max<int64_t>(budget, 0);
+  if (want > cur) cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &want);
+}
+
+void release_pool_memory(int dev) {
+  if (dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  PoolKeep& k = g_pool_keep[dev];
+  if (k.servers <= 0) return;
+  if (--k.servers == 0) {
+    cudaMemPool_t mp;
+    if (cudaDeviceGetDefaultMemPool(&mp, dev) == cudaSuccess) {
+      cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &k.saved);
+      cudaMemPoolTrimTo(mp, (size_t)k.saved);
+    }
+  }
 }
 
 // Warm-up at creation: two small requests with every output (metrics and adjoint) run alone,
@@ -409,8 +482,15 @@ ara_status ara_server_create(ara_portfolio* pool, int64_t n_trials, const int64_
   S->budget = memory_budget;
   {
     DeviceGuard g(pool->device);
+    if (cudaEventCreateWithFlags(&S->pass_done, cudaEventDisableTiming) != cudaSuccess) {
+      delete S;
+      return ARA_ECUDA;
+    }
+    keep_pool_memory(pool->device, memory_budget);
     const ara_status st = warm_up(*S);
     if (st != ARA_OK) {
+      release_pool_memory(pool->device);
+      cudaEventDestroy(S->pass_done);
       delete S;
       return st;
     }
@@ -459,6 +539,7 @@ ara_status ara_server_submit(ara_server* S, const ara_query* q, int64_t* ticket)
   if (r->want_adjoint && tail_count_snap(r->t1 - r->t0, r->adjoint_level) < 1) return ARA_EINVAL;
   if (r->flags & ~(ARA_RUN_BATCHED | ARA_RUN_LDG | ARA_RUN_NO_FILTER)) return ARA_EINVAL;
   r->mem = estimate_bytes(pool, *r);
+  for (int32_t j : r->layer_elts) r->table_bound += 8 * (pool.rec_off[j + 1] - pool.rec_off[j]);
   r->t_submit = now_s();
   {
     std::lock_guard<std::mutex> lk(S->mu);
@@ -537,6 +618,11 @@ void ara_server_destroy(ara_server* S) {
   }
   S->cv_work.notify_all();
   for (auto& t : S->workers) t.join();
+  {
+    DeviceGuard g(S->pool->device);
+    if (S->pass_done) cudaEventDestroy(S->pass_done);
+    release_pool_memory(S->pool->device);
+  }
   delete S;
 }
 

@@ -32,9 +32,12 @@ def test_hash_ignores_comments_and_blank_lines(tree):
     assert bench.kernel_source_sha() != h0
 
 
-def test_traffic_is_read_only_for_the_matching_source(tree):
+def test_profile_figures_are_read_only_for_the_matching_source(tree):
     prof = tree / "profiles" / "k_ylt_bulk_paper_scale.md"
-    prof.write_text(f"- kernel_source_sha: {bench.kernel_source_sha()}\n- dram_bytes_per_event: 4.25\n")
-    assert bench.ncu_traffic_per_launch() == pytest.approx(4.25)
+    prof.write_text(f"- kernel_source_sha: {bench.kernel_source_sha()}\n- dram_bytes_per_event: 4.25\n"
+                    "- l2_hit_rate_pct: 61.5 (lts__t_sector_hit_rate.pct)\n")
+    fig = bench.ncu_profile_figures()
+    assert fig["dram_bytes_per_event"] == pytest.approx(4.25)
+    assert fig["l2_hit_rate_pct"] == pytest.approx(61.5)
     prof.write_text("- kernel_source_sha: 0000000000000000\n- dram_bytes_per_event: 4.25\n")
-    assert bench.ncu_traffic_per_launch() is None
+    assert bench.ncu_profile_figures() == {}
