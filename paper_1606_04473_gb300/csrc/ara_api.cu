@@ -161,6 +161,9 @@ static void free_portfolio(ara_portfolio* p) {
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
+  if (p->d_res) cudaFree(p->d_res);
+  if (p->h_res) cudaFreeHost(p->h_res);
+  if (p->d_sel_scratch) cudaFree(p->d_sel_scratch);
   for (int i = 0; i < 2; ++i) {
     if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
     if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
@@ -742,18 +745,75 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
     ARA_TRY(cudaEventRecord(pf->ev_done[b], s));
   }
   }  // staged copies
+  // Results.  The YLT goes back on the copy stream while the selection runs on `s`; the metrics,
+  // the selection's status and the device error word come back in one small copy into pinned
+  // memory; then one wait for both streams.
+  const int32_t nsel = (int32_t)sel.size();
   if (h_ylt) {
-    timing_begin(ARA_K_TRANSFER, s);
-    ARA_TRY(cudaMemcpyAsync(h_ylt, pf->d_ylt_full, sizeof(double) * sel.size() * (size_t)n_trials,
-                            cudaMemcpyDeviceToHost, s));
-    timing_end(ARA_K_TRANSFER, s);
+    ARA_TRY(cudaEventRecord(pf->ev_done[0], s));
+    ARA_TRY(cudaStreamWaitEvent(pf->copy_stream, pf->ev_done[0], 0));
+    timing_begin(ARA_K_TRANSFER, pf->copy_stream);
+    ARA_TRY(cudaMemcpyAsync(h_ylt, pf->d_ylt_full, sizeof(double) * (size_t)nsel * (size_t)n_trials,
+                            cudaMemcpyDeviceToHost, pf->copy_stream));
+    timing_end(ARA_K_TRANSFER, pf->copy_stream);
   }
+  const int64_t n_pml = (int64_t)nsel * n_rp, n_tv = (int64_t)nsel * n_tvar;
+  const int64_t n_mean = h_mean ? nsel : 0;
+  const int64_t res_elems = n_pml + n_tv + n_mean + 1;   // + one slot: status and error words
+  if (res_elems > pf->res_elems) {
+    if (pf->d_res) cudaFree(pf->d_res);
+    if (pf->h_res) cudaFreeHost(pf->h_res);
+    pf->d_res = nullptr;
+    pf->h_res = nullptr;
+    pf->res_elems = 0;
+    ARA_TRY(cudaMalloc((void**)&pf->d_res, sizeof(double) * (size_t)res_elems));
+    ARA_TRY(cudaMallocHost((void**)&pf->h_res, sizeof(double) * (size_t)res_elems));
+    pf->res_elems = res_elems;
+  }
+  uint32_t* d_words = reinterpret_cast<uint32_t*>(pf->d_res + n_pml + n_tv + n_mean);
+  ARA_TRY(cudaMemsetAsync(d_words, 0, 2 * sizeof(uint32_t), s));
   if (metrics) {
-    if ((st = risk_metrics_device(pf->d_ylt_full, n_trials, (int32_t)sel.size(), n_rp, rps, n_tvar,
-                                  levels, h_pml, h_tvar, h_mean, s)) != ARA_OK)
+    // the selection's scratch is kept with the portfolio, so repeated calls allocate nothing
+    auto queue = [&](size_t* need) {
+      return risk_metrics_queue(pf->d_ylt_full, n_trials, nsel, n_rp, rps, n_tvar, levels,
+                                n_rp > 0 ? pf->d_res : nullptr, n_tvar > 0 ? pf->d_res + n_pml : nullptr,
+                                h_mean ? pf->d_res + n_pml + n_tv : nullptr, d_words,
+                                pf->d_sel_scratch, pf->sel_scratch_bytes, need, s);
+    };
+    size_t need = 0;
+    st = queue(&need);
+    if (st == ARA_ERANGE && need > pf->sel_scratch_bytes) {
+      ARA_TRY(cudaStreamSynchronize(s));
+      if (pf->d_sel_scratch) cudaFree(pf->d_sel_scratch);
+      pf->d_sel_scratch = nullptr;
+      pf->sel_scratch_bytes = 0;
+      ARA_TRY(cudaMalloc(&pf->d_sel_scratch, need));
+      pf->sel_scratch_bytes = need;
+      st = queue(&need);
+    }
+    if (st != ARA_OK) {
+      cudaStreamSynchronize(pf->copy_stream);
+      cudaStreamSynchronize(s);
       return st;
+    }
   }
-  return ara_check(pf, stream);
+  ARA_TRY(cudaMemcpyAsync(d_words + 1, pf->d_err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  ARA_TRY(cudaMemcpyAsync(pf->h_res, pf->d_res, sizeof(double) * (size_t)res_elems,
+                          cudaMemcpyDeviceToHost, s));
+  ARA_TRY(cudaStreamSynchronize(s));
+  ARA_TRY(cudaStreamSynchronize(pf->copy_stream));
+  const uint32_t* h_words = reinterpret_cast<const uint32_t*>(pf->h_res + n_pml + n_tv + n_mean);
+  const uint32_t sel_status = h_words[0], err = h_words[1];
+  if (err) {   // as ara_check: report and clear the device error word
+    ARA_TRY(cudaMemsetAsync(pf->d_err, 0, sizeof(uint32_t), s));
+    ARA_TRY(cudaStreamSynchronize(s));
+    return (err & DERR_TIMEOUT) ? ARA_ETIMEOUT : ARA_EDATA;
+  }
+  if (sel_status & ARA_DEVICE_TIMEOUT) return ARA_ETIMEOUT;
+  if (n_pml) std::copy(pf->h_res, pf->h_res + n_pml, h_pml);
+  if (n_tv) std::copy(pf->h_res + n_pml, pf->h_res + n_pml + n_tv, h_tvar);
+  if (n_mean) std::copy(pf->h_res + n_pml + n_tv, pf->h_res + n_pml + n_tv + n_mean, h_mean);
+  return ARA_OK;
 }
 
 }  // extern "C"

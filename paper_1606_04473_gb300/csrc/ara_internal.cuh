@@ -116,6 +116,13 @@ struct Portfolio {
   int64_t stage_events = 0, stage_trials = 0;
   double* d_ylt_full = nullptr;     // [n_sel][n_trials] YLT of the host pipeline
   int64_t ylt_full_elems = 0;
+  // results of the host pipeline: metrics, selection status and the device error word, in one
+  // device block and its pinned host copy (one copy and one synchronisation per call)
+  double* d_res = nullptr;
+  double* h_res = nullptr;
+  int64_t res_elems = 0;
+  void* d_sel_scratch = nullptr;    // the host pipeline's selection scratch (grown on demand)
+  size_t sel_scratch_bytes = 0;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -200,6 +207,12 @@ struct SelectResult {
 ara_status select_one_rank(const double* d_ylt, int64_t n, int32_t n_layers, int64_t m, int n_sms,
                            cudaStream_t s, SelectResult* out, uint32_t* err);
 void free_select_result(SelectResult& r, cudaStream_t s);
+// The stream-ordered risk metrics with caller-owned scratch: ARA_ERANGE (and *need) when the
+// scratch is too small.
+ara_status risk_metrics_queue(const double* d_ylt, int64_t n_trials, int32_t n_layers, int32_t n_rp,
+                              const double* rps, int32_t n_tvar, const double* levels,
+                              double* d_pml, double* d_tvar, double* d_mean, uint32_t* d_status,
+                              void* scratch, size_t scratch_bytes, size_t* need, cudaStream_t s);
 // PML / TVaR of n_layers device YLT rows into host arrays (synchronises s); scratch from the
 // stream-ordered allocator.
 ara_status risk_metrics_device(const double* d_ylt, int64_t n, int32_t n_layers, int32_t n_rp,

@@ -594,6 +594,34 @@ ara_status risk_metrics_device(const double* d_ylt, int64_t n_trials, int32_t n_
 
 }  // namespace ara
 
+namespace ara {
+// ara_risk_metrics_async with caller-owned scratch (the host pipeline keeps one per portfolio):
+// ARA_ERANGE with *need set when scratch_bytes is too small, nothing queued.
+ara_status risk_metrics_queue(const double* d_ylt, int64_t n_trials, int32_t n_layers, int32_t n_rp,
+                              const double* rps, int32_t n_tvar, const double* levels,
+                              double* d_pml, double* d_tvar, double* d_mean, uint32_t* d_status,
+                              void* scratch, size_t scratch_bytes, size_t* need, cudaStream_t s) {
+  SelTargets tg;
+  if (!d_ylt || n_layers < 1 || !d_status || !need) return ARA_EINVAL;
+  if ((n_rp > 0 && !d_pml) || (n_tvar > 0 && !d_tvar)) return ARA_EINVAL;
+  if ((uintptr_t)d_ylt & 7) return ARA_EINVAL;
+  ara_status st = select_targets(n_trials, n_rp, rps, n_tvar, levels, tg);
+  if (st != ARA_OK) return st;
+  if (tg.n_t == 0 && !d_mean) return ARA_EINVAL;
+  int dev = 0, sms = 0;
+  ARA_TRY(cudaGetDevice(&dev));
+  ARA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int32_t blocks = select_blocks(n_trials, sms, n_layers);
+  *need = select_scratch_bytes(n_layers, tg.n_t, blocks);
+  if (!scratch || scratch_bytes < *need) return ARA_ERANGE;
+  SelScratch sc;
+  ARA_TRY(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+  return launch_select(d_ylt, n_trials, n_layers, tg, scratch, *need, blocks, d_mean != nullptr, s,
+                       &sc, d_status, n_rp > 0 ? d_pml : nullptr, n_tvar > 0 ? d_tvar : nullptr,
+                       d_mean);
+}
+}  // namespace ara
+
 extern "C" ara_status ara_risk_metrics_async(const double* d_ylt, int64_t n_trials,
                                              int32_t n_layers, int32_t n_rp, const double* rps,
                                              int32_t n_tvar, const double* levels, double* d_pml,
