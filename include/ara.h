@@ -27,6 +27,10 @@
  *     trial counts as empty, and the next ara_check() on the portfolio returns ARA_EDATA.
  *   - The library is thread-compatible: one portfolio must not run on two streams at once
  *     (its fold workspace is shared); distinct portfolios are independent.
+ *   - Scratch that calls allocate in stream order (selections, adjoint, batched runs, layer
+ *     sets, serving) comes from the library's own memory pool on each device, which keeps freed
+ *     memory for the next call instead of returning it at every synchronisation;
+ *     ara_release_memory() returns the idle part to the system.
  */
 #ifndef ARA_H
 #define ARA_H
@@ -306,10 +310,9 @@ typedef struct ara_query {
  * trial walking only the table entries of the requests that cover it, so the requests share the
  * reading of the YET (a group's table is kept near L2 size).  The workers' YET passes (batched
  * or single-layer streams, adjoint histograms) run one after the other on the device, each
- * queued behind the previous one; their folds, selections and host work overlap.  While a
- * server exists, the device's default memory pool keeps up to memory_budget bytes of freed
- * memory cached (its release threshold is raised; the previous value is restored when the last
- * server on the device is destroyed).  Creation runs a few small warm-up requests
+ * queued behind the previous one; their folds, selections and host work overlap.  Admission
+ * counts the library's idle pooled memory (see ara_release_memory) as free.  Creation runs a
+ * few small warm-up requests
  * (synchronous), so the first real requests pay no one-time costs.  The pool and the YET must
  * outlive the server.  Results of a request do not depend on what else runs or on the group it
  * ran in (bitwise).
@@ -420,7 +423,7 @@ ARA_API ara_status ara_adjoint_accumulate(ara_portfolio* pf, int64_t n_trials,
  *   h_pml         host [n_layers][n_rp];  h_tvar host [n_layers][n_tvar]
  *   h_mean        host [n_layers] or NULL: the mean year loss (1/N) sum_t y_t of each row
  * n_rp + n_tvar <= 16 (at least one metric requested), n_trials >= 1.  Allocates its scratch
- * with the stream-ordered allocator (cudaMallocAsync) on `stream`.  The selection is one
+ * in stream order on `stream`, from the library's memory pool.  The selection is one
  * cooperative launch whose blocks meet at device-side barriers, each wait bounded like the
  * bulk copies' (ara_debug_set ARA_DBG_WAIT_LIMIT_NS).
  * Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA, ARA_ETIMEOUT (a barrier wait ran out).
@@ -440,7 +443,7 @@ ARA_API ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, int32
  *   d_mean       device [n_layers] double or NULL
  *   d_status     device uint32: set to 0 when the work starts; ARA_DEVICE_TIMEOUT is OR-ed
  *                in when a device-side wait runs out (the other outputs are then undefined)
- * Scratch comes from the stream-ordered allocator and is released in stream order.  Argument
+ * Scratch comes from the library's memory pool in stream order and is released in stream order.  Argument
  * errors are returned at once (ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA) and nothing is queued.
  */
 #define ARA_DEVICE_TIMEOUT 4u
@@ -481,6 +484,10 @@ ARA_API ara_status ara_risk_metrics_static(const double* d_ylt, int64_t n_trials
 /* ---------------------------------------------------------------------------------------
  * Introspection for measurement.
  * --------------------------------------------------------------------------------------- */
+
+/* Return the memory that the library's pools hold idle (freed scratch kept for reuse) to the
+ * system, on every device.  Memory in use is not touched.  Errors: ARA_ECUDA. */
+ARA_API ara_status ara_release_memory(void);
 
 /* Kernels launched by this library in this process so far. */
 ARA_API int64_t ara_launch_count(void);

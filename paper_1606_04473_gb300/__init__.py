@@ -107,6 +107,8 @@ def lib() -> ctypes.CDLL:
     L.ara_server_stats.restype = i32
     L.ara_run_ylt_requests.argtypes = [P, i64, P, i64, P, i32, P, P, P, P, P, P]
     L.ara_run_ylt_requests.restype = i32
+    L.ara_release_memory.argtypes = []
+    L.ara_release_memory.restype = i32
     L.ara_server_set_merging.argtypes = [P, i32, d]
     L.ara_server_set_merging.restype = i32
     L.ara_server_counters.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -578,6 +580,11 @@ def risk_metrics_static(ylt, return_periods: Sequence[float] = (), tvar_levels: 
                                        _np_ptr(tvar), _np_ptr(mean), _stream_handle(stream))
     _check(st, "ara_risk_metrics_static")
     return (pml, tvar, mean) if want_mean else (pml, tvar)
+
+
+def release_memory():
+    """Return the idle memory of the library's pools to the system (ara_release_memory)."""
+    _check(lib().ara_release_memory(), "ara_release_memory")
 
 
 def launch_count() -> int:

@@ -408,7 +408,7 @@ extern "C" ara_status ara_adjoint(ara_portfolio* pf_, int64_t n_trials, const in
   const size_t o_hm = take(4 * (size_t)C), o_hg = take(4 * (size_t)C), o_he = take(4 * (size_t)C);
   const size_t o_acc = take(sizeof(AdjCounts)), o_slots = take(sizeof(SlotCounts) * ADJ_MAX_SLOTS);
   char* scratch = nullptr;
-  cudaError_t ce = cudaMallocAsync((void**)&scratch, off, s);
+  cudaError_t ce = dmalloc_async((void**)&scratch, off, s);
   if (ce != cudaSuccess) {
     free_select_result(sr, s);
     return ce == cudaErrorMemoryAllocation ? ARA_ENOMEM : ARA_ECUDA;
@@ -573,7 +573,7 @@ extern "C" ara_status ara_adjoint_accumulate(ara_portfolio* pf_, int64_t n_trial
   const size_t bytes = sizeof(double) * (size_t)(2 * 2 * std::max<int64_t>(K, 1) + 2 * 4 * n_sel +
                                                  2 * std::max<int64_t>(M, 1));
   double* buf = nullptr;
-  ARA_TRY(cudaMallocAsync((void**)&buf, bytes, s));
+  ARA_TRY(dmalloc_async((void**)&buf, bytes, s));
   double* ge = buf;
   double* gl = ge + 2 * 2 * std::max<int64_t>(K, 1);
   double* gx = gl + 2 * 4 * n_sel;

@@ -86,6 +86,58 @@ void timing_add_host(int k, double ms) {
   g_count[k] += 1;
 }
 
+namespace {
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxPoolDevices];
+}  // namespace
+
+static cudaMemPool_t library_pool(int dev) {
+  if (dev < 0 || dev >= kMaxPoolDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t mp = nullptr;
+    if (cudaMemPoolCreate(&mp, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;   // keep freed memory until ara_release_memory
+    cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = mp;
+  }
+  return g_pools[dev];
+}
+
+cudaError_t dmalloc_async(void** ptr, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t mp = library_pool(dev);
+  if (!mp) return cudaMallocAsync(ptr, bytes, s);
+  return cudaMallocFromPoolAsync(ptr, bytes, mp, s);
+}
+
+int64_t pool_idle_bytes(int dev) {
+  if (dev < 0 || dev >= kMaxPoolDevices) return 0;
+  cudaMemPool_t mp;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    mp = g_pools[dev];
+  }
+  if (!mp) return 0;
+  uint64_t reserved = 0, used = 0;
+  if (cudaMemPoolGetAttribute(mp, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+      cudaMemPoolGetAttribute(mp, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess)
+    return 0;
+  return reserved > used ? (int64_t)(reserved - used) : 0;
+}
+
 bool timing_suspend() {
   std::lock_guard<std::mutex> lk(g_tmu);
   const bool was = g_timing;
@@ -231,6 +283,14 @@ ara_status ara_set_stream_shape(int32_t index) {
   if (index < 0 || index >= n_bulk_shapes()) return ARA_EINVAL;
   set_bulk_shape(index);
   return ARA_OK;
+}
+
+ara_status ara_release_memory(void) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  ara_status st = ARA_OK;
+  for (int d = 0; d < kMaxPoolDevices; ++d)
+    if (g_pools[d] && cudaMemPoolTrimTo(g_pools[d], 0) != cudaSuccess) st = ARA_ECUDA;
+  return st;
 }
 
 void ara_timing_enable(int32_t on) {
@@ -490,7 +550,7 @@ ara_status ara_create_layer_set(ara_portfolio* pool, int32_t n_layers, const int
     free_portfolio(p);
     return e;
   };
-  auto amalloc = [&](void** ptr, size_t n) { return cudaMallocAsync(ptr, std::max<size_t>(n, 8), s) == cudaSuccess; };
+  auto amalloc = [&](void** ptr, size_t n) { return dmalloc_async(ptr, std::max<size_t>(n, 8), s) == cudaSuccess; };
   if (!amalloc((void**)&p->d_layer_elts, 4 * p->layer_elts.size()) ||
       !amalloc((void**)&p->d_layers, sizeof(LayerConst) * (size_t)n_layers) ||
       !amalloc((void**)&p->d_q, 8 * (size_t)n_layers * C) ||

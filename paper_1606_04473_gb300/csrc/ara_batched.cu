@@ -511,7 +511,7 @@ ara_status run_plan_async(ara_plan& P, cudaStream_t s) {
   const size_t o_bsum = take(4 * (size_t)P.n_blocks), o_tot = take(4), o_q = take(8);
   const size_t o_ent = take(8 * (size_t)std::max<int64_t>(bound, 1));
   char* buf = nullptr;
-  ARA_TRY(cudaMallocAsync((void**)&buf, off, s));
+  ARA_TRY(dmalloc_async((void**)&buf, off, s));
   P.d_ptr = (uint32_t*)(buf + o_ptr);
   P.d_rows = (uint64_t*)(buf + o_rows);
   P.d_bsum = (uint32_t*)(buf + o_bsum);

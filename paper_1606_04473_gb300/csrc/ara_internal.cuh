@@ -25,6 +25,14 @@ namespace ara {
 
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
+// Stream-ordered allocations of the library come from its own memory pool on each device, which
+// keeps freed memory for reuse instead of returning it at every synchronisation (the default
+// pool's behaviour, which made every synchronous call map its scratch again).  Free with
+// cudaFreeAsync.  ara_release_memory() returns the idle part to the system.
+cudaError_t dmalloc_async(void** ptr, size_t bytes, cudaStream_t s);
+// Bytes the library's pool on `dev` holds without using them (reusable by the library).
+int64_t pool_idle_bytes(int dev);
+
 // Device-side data error bits (atomicOr into the portfolio's error word).
 enum : uint32_t { DERR_EVENT_RANGE = 1u, DERR_OFFSETS = 2u, DERR_TIMEOUT = 4u };
 

@@ -530,7 +530,7 @@ ara_status select_one_rank(const double* d_ylt, int64_t n, int32_t n_layers, int
   const int32_t blocks = select_blocks(n, n_sms, n_layers);
   const size_t bytes = select_scratch_bytes(n_layers, 1, blocks);
   void* scratch = nullptr;
-  ARA_TRY(cudaMallocAsync(&scratch, bytes, s));
+  ARA_TRY(dmalloc_async(&scratch, bytes, s));
   SelScratch sc;
   ara_status st = launch_select(d_ylt, n, n_layers, tg, scratch, bytes, blocks, 0, s, &sc, err);
   if (st != ARA_OK) {
@@ -567,7 +567,7 @@ ara_status risk_metrics_device(const double* d_ylt, int64_t n_trials, int32_t n_
   const int32_t blocks = select_blocks(n_trials, sms, n_layers);
   const size_t bytes = select_scratch_bytes(n_layers, tg.n_t, blocks);
   void* scratch = nullptr;
-  ARA_TRY(cudaMallocAsync(&scratch, bytes, s));
+  ARA_TRY(dmalloc_async(&scratch, bytes, s));
   SelScratch sc;
   st = launch_select(d_ylt, n_trials, n_layers, tg, scratch, bytes, blocks, h_mean != nullptr, s, &sc);
   std::vector<double> out((size_t)n_layers * tg.n_t);
@@ -642,7 +642,7 @@ extern "C" ara_status ara_risk_metrics_async(const double* d_ylt, int64_t n_tria
   const int32_t blocks = select_blocks(n_trials, sms, n_layers);
   const size_t bytes = select_scratch_bytes(n_layers, tg.n_t, blocks);
   void* scratch = nullptr;
-  if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) return ARA_ENOMEM;
+  if (dmalloc_async(&scratch, bytes, s) != cudaSuccess) return ARA_ENOMEM;
   ara_status r = ARA_OK;
   SelScratch sc;
   if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s) != cudaSuccess) r = ARA_ECUDA;

@@ -139,9 +139,9 @@ ara_status finish_request(ara_server& S, Request& r, ara_portfolio* ls, int32_t 
     std::vector<int32_t> sel(nl);
     for (int32_t i = 0; i < nl; ++i) sel[i] = slot0 + i;
     double *ge = nullptr, *gl = nullptr, *gx = nullptr;
-    if (cudaMallocAsync((void**)&ge, 8 * (size_t)std::max<int64_t>(4 * K, 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&gl, 8 * (size_t)(8 * nl), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&gx, 8 * (size_t)std::max<int64_t>(2 * M, 1), s) != cudaSuccess) {
+    if (dmalloc_async((void**)&ge, 8 * (size_t)std::max<int64_t>(4 * K, 1), s) != cudaSuccess ||
+        dmalloc_async((void**)&gl, 8 * (size_t)(8 * nl), s) != cudaSuccess ||
+        dmalloc_async((void**)&gx, 8 * (size_t)std::max<int64_t>(2 * M, 1), s) != cudaSuccess) {
       st = ARA_ENOMEM;
     } else {
       st = chained_pass(S, s, [&] {
@@ -183,9 +183,9 @@ void run_request(ara_server& S, Request& r, cudaStream_t s) {
   ara_status st = ara_create_layer_set(static_cast<ara_portfolio*>(S.pool), nl, r.layer_off.data(),
                                        r.layer_elts.data(), r.occ_ret.data(), r.occ_lim.data(),
                                        r.agg_ret.data(), r.agg_lim.data(), s, &ls);
-  if (st == ARA_OK && cudaMallocAsync((void**)&ylt, 8 * (size_t)nl * n, s) != cudaSuccess) st = ARA_ENOMEM;
+  if (st == ARA_OK && dmalloc_async((void**)&ylt, 8 * (size_t)nl * n, s) != cudaSuccess) st = ARA_ENOMEM;
   if (st == ARA_OK && r.want_adjoint &&
-      cudaMallocAsync((void**)&reg, (size_t)nl * n, s) != cudaSuccess)
+      dmalloc_async((void**)&reg, (size_t)nl * n, s) != cudaSuccess)
     st = ARA_ENOMEM;
   if (st == ARA_OK)
     st = chained_pass(S, s, [&] {
@@ -238,8 +238,8 @@ void run_group(ara_server& S, std::vector<std::shared_ptr<Request>>& g, cudaStre
     const int64_t nl = (int64_t)r.layer_off.size() - 1, n = r.t1 - r.t0;
     ga.t0[k] = r.t0 - u0;
     ga.t1[k] = r.t1 - u0;
-    if (cudaMallocAsync((void**)&ga.ylt[k], 8 * (size_t)(nl * n), s) != cudaSuccess ||
-        (r.want_adjoint && cudaMallocAsync((void**)&ga.reg[k], (size_t)(nl * n), s) != cudaSuccess))
+    if (dmalloc_async((void**)&ga.ylt[k], 8 * (size_t)(nl * n), s) != cudaSuccess ||
+        (r.want_adjoint && dmalloc_async((void**)&ga.reg[k], (size_t)(nl * n), s) != cudaSuccess))
       st = ARA_ENOMEM;
   }
   if (st == ARA_OK)
@@ -260,12 +260,13 @@ void run_group(ara_server& S, std::vector<std::shared_ptr<Request>>& g, cudaStre
 }
 
 // Device memory that admission may still hand out: the budget left, and no more than the device
-// has free now (less what admitted requests may still allocate).
+// has free now plus what the library's memory pool holds idle (reusable by the requests), less
+// what admitted requests may still allocate.
 int64_t admissible_bytes(ara_server& S) {
   int64_t avail = S.budget - S.in_use;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
-    avail = std::min(avail, (int64_t)(0.95 * (double)free_b) - S.in_use);
+    avail = std::min(avail, (int64_t)(0.95 * (double)free_b) + pool_idle_bytes(S.pool->device) - S.in_use);
   return avail;
 }
 
@@ -368,50 +369,6 @@ void worker_main(ara_server* S) {
   if (s) cudaStreamDestroy(s);
 }
 
-// While a server runs on a device, the device's default memory pool (which the request path
-// allocates from, stream-ordered) keeps up to the server's budget of freed memory instead of
-// returning it to the system at every synchronisation: requests allocate their layer sets,
-// tables and YLTs anew, and re-mapping that memory for every request was measured at about an
-// eighth of a one-at-a-time run's time.  The pool's previous threshold is restored when the
-// last server on the device is destroyed.
-std::mutex g_pool_mu;
-struct PoolKeep {
-  int servers = 0;
-  uint64_t saved = 0;
-};
-PoolKeep g_pool_keep[64];
-
-void keep_pool_memory(int dev, int64_t budget) {
-  if (dev < 0 || dev >= 64) return;
-  std::lock_guard<std::mutex> lk(g_pool_mu);
-  cudaMemPool_t mp;
-  if (cudaDeviceGetDefaultMemPool(&mp, dev) != cudaSuccess) return;
-  PoolKeep& k = g_pool_keep[dev];
-  uint64_t cur = 0;
-  if (k.servers == 0) {
-    if (cudaMemPoolGetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &cur) != cudaSuccess) return;
-    k.saved = cur;
-  }
-  k.servers += 1;
-  cudaMemPoolGetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &cur);
-  uint64_t want = (uint64_t)std::max<int64_t>(budget, 0);
-  if (want > cur) cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &want);
-}
-
-void release_pool_memory(int dev) {
-  if (dev < 0 || dev >= 64) return;
-  std::lock_guard<std::mutex> lk(g_pool_mu);
-  PoolKeep& k = g_pool_keep[dev];
-  if (k.servers <= 0) return;
-  if (--k.servers == 0) {
-    cudaMemPool_t mp;
-    if (cudaDeviceGetDefaultMemPool(&mp, dev) == cudaSuccess) {
-      cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &k.saved);
-      cudaMemPoolTrimTo(mp, (size_t)k.saved);
-    }
-  }
-}
-
 // Warm-up at creation: two small requests with every output (metrics and adjoint) run alone,
 // batched, and merged, so that the first real requests pay no one-time costs (kernel loading,
 // the stream-ordered allocator's first reservations).
@@ -486,10 +443,8 @@ ara_status ara_server_create(ara_portfolio* pool, int64_t n_trials, const int64_
       delete S;
       return ARA_ECUDA;
     }
-    keep_pool_memory(pool->device, memory_budget);
     const ara_status st = warm_up(*S);
     if (st != ARA_OK) {
-      release_pool_memory(pool->device);
       cudaEventDestroy(S->pass_done);
       delete S;
       return st;
@@ -621,7 +576,6 @@ void ara_server_destroy(ara_server* S) {
   {
     DeviceGuard g(S->pool->device);
     if (S->pass_done) cudaEventDestroy(S->pass_done);
-    release_pool_memory(S->pool->device);
   }
   delete S;
 }

@@ -149,3 +149,16 @@ def test_layers_stopping_after_different_passes():
     rows[1][: n // 2] = 4.5e6                     # tie group holding every target
     rows[2][::2] = np.nextafter(rows[2][1::2], 0)  # near-equal pairs: unique only in the last bits
     check(np.stack(rows), rps=[1.0, 2.0, 100.0, 250.0, float(n)], levels=[0.0, 0.5, 0.99])
+
+
+def test_results_unchanged_after_releasing_pooled_memory():
+    """Scratch comes from the library's own memory pool, which keeps freed memory for the next
+    call; ara_release_memory hands the idle part back.  Calls before and after (the pool then
+    maps fresh memory) give the same, oracle-checked results."""
+    rng = np.random.default_rng(44)
+    y = rng.lognormal(14, 2, (3, 50_000))
+    check(y)
+    ara.release_memory()
+    check(y)
+    check(y)
+    ara.release_memory()
