@@ -321,6 +321,10 @@ ARA_API ara_status ara_server_create(ara_portfolio* pool, int64_t n_trials,
                                      const int64_t* d_trial_offsets, int64_t n_events,
                                      const int32_t* d_event_ids, int32_t max_concurrent,
                                      int64_t memory_budget, ara_server** out);
+/* The device memory the server estimates a query may hold at once (the figure admission uses);
+ * the query is validated as by ara_server_submit and not queued.  Errors: ARA_EINVAL. */
+ARA_API ara_status ara_server_estimate_bytes(ara_server* server, const ara_query* query,
+                                             int64_t* bytes);
 /* Queue a query (validated and copied now; ARA_EINVAL on bad arguments); returns a ticket. */
 ARA_API ara_status ara_server_submit(ara_server* server, const ara_query* query, int64_t* ticket);
 /*

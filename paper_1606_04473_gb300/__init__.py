@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
     L.ara_run_ylt_requests.restype = i32
     L.ara_release_memory.argtypes = []
     L.ara_release_memory.restype = i32
+    L.ara_server_estimate_bytes.argtypes = [P, ctypes.POINTER(Query), ctypes.POINTER(i64)]
+    L.ara_server_estimate_bytes.restype = i32
     L.ara_server_set_merging.argtypes = [P, i32, d]
     L.ara_server_set_merging.restype = i32
     L.ara_server_counters.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -464,9 +466,11 @@ class Server:
                "ara_server_counters")
         return {"passes": a.value, "merged_requests": b.value, "head_passed": c.value}
 
-    def submit(self, layer_elts, occ_ret, occ_lim, agg_ret, agg_lim, trials, return_periods=(),
+    @staticmethod
+    def _query(layer_elts, occ_ret, occ_lim, agg_ret, agg_lim, trials, return_periods=(),
                tvar_levels=(), want_mean=False, want_adjoint=False, adjoint_level=0.99, flags=0,
-               tenant=0) -> int:
+               tenant=0):
+        """(ara_query, the arrays it points into: keep them alive while it is used)."""
         loff = np.zeros(len(layer_elts) + 1, dtype=np.int32)
         loff[1:] = np.cumsum([len(l) for l in layer_elts])
         lel = np.ascontiguousarray([j for l in layer_elts for j in l] or [0], dtype=np.int32)
@@ -476,6 +480,22 @@ class Server:
         q = Query(len(layer_elts), *[a.ctypes.data for a in arrs[:6]], int(trials[0]), int(trials[1]),
                   len(return_periods), arrs[6].ctypes.data, len(tvar_levels), arrs[7].ctypes.data,
                   int(want_mean), int(want_adjoint), float(adjoint_level), int(flags), int(tenant))
+        return q, arrs
+
+    def estimate_bytes(self, **query) -> int:
+        """The device memory the server's admission assumes for this query
+        (ara_server_estimate_bytes)."""
+        q, _arrs = self._query(**query)
+        b = ctypes.c_int64()
+        _check(lib().ara_server_estimate_bytes(self._h, ctypes.byref(q), ctypes.byref(b)),
+               "ara_server_estimate_bytes")
+        return b.value
+
+    def submit(self, layer_elts, occ_ret, occ_lim, agg_ret, agg_lim, trials, return_periods=(),
+               tvar_levels=(), want_mean=False, want_adjoint=False, adjoint_level=0.99, flags=0,
+               tenant=0) -> int:
+        q, arrs = self._query(layer_elts, occ_ret, occ_lim, agg_ret, agg_lim, trials, return_periods,
+                              tvar_levels, want_mean, want_adjoint, adjoint_level, flags, tenant)
         t = ctypes.c_int64()
         _check(lib().ara_server_submit(self._h, ctypes.byref(q), ctypes.byref(t)), "ara_server_submit")
         self._shapes[t.value] = (len(layer_elts), len(return_periods), len(tvar_levels), want_mean,

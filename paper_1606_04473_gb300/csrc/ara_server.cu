@@ -455,8 +455,12 @@ ara_status ara_server_create(ara_portfolio* pool, int64_t n_trials, const int64_
   return ARA_OK;
 }
 
-ara_status ara_server_submit(ara_server* S, const ara_query* q, int64_t* ticket) {
-  if (!S || !q || !ticket) return ARA_EINVAL;
+}  // extern "C"
+
+namespace {
+// Validate a query and copy it into a request (no ticket, not queued).
+ara_status make_request(ara_server* S, const ara_query* q, std::shared_ptr<Request>& out) {
+  if (!S || !q) return ARA_EINVAL;
   const Portfolio& pool = *S->pool;
   if (q->n_layers < 1 || !q->layer_elt_offsets || q->trial_begin < 0 ||
       q->trial_end <= q->trial_begin || q->trial_end > S->n_trials)
@@ -495,6 +499,27 @@ ara_status ara_server_submit(ara_server* S, const ara_query* q, int64_t* ticket)
   if (r->flags & ~(ARA_RUN_BATCHED | ARA_RUN_LDG | ARA_RUN_NO_FILTER)) return ARA_EINVAL;
   r->mem = estimate_bytes(pool, *r);
   for (int32_t j : r->layer_elts) r->table_bound += 8 * (pool.rec_off[j + 1] - pool.rec_off[j]);
+  out = r;
+  return ARA_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ara_status ara_server_estimate_bytes(ara_server* S, const ara_query* q, int64_t* bytes) {
+  if (!bytes) return ARA_EINVAL;
+  std::shared_ptr<Request> r;
+  const ara_status st = make_request(S, q, r);
+  if (st != ARA_OK) return st;
+  *bytes = r->mem;
+  return ARA_OK;
+}
+
+ara_status ara_server_submit(ara_server* S, const ara_query* q, int64_t* ticket) {
+  if (!ticket) return ARA_EINVAL;
+  std::shared_ptr<Request> r;
+  const ara_status st = make_request(S, q, r);
+  if (st != ARA_OK) return st;
   r->t_submit = now_s();
   {
     std::lock_guard<std::mutex> lk(S->mu);

@@ -179,3 +179,38 @@ def test_server_merging_arguments(world):
             srv.set_merging(*bad)
     srv.set_merging(1)
     srv.close()
+
+
+def test_blocked_request_is_passed_by_smaller_ones_a_bounded_number_of_times(world):
+    """Admission: while a long request runs, a queued request too large for the rest of the
+    budget is passed by smaller queued requests that fit (at most 4 times), and still runs
+    afterwards; every result equals the same request served alone."""
+    pool_tables, yet, pool, off, ev = world
+    rng = np.random.default_rng(29)
+    big_layers = [sorted(rng.choice(POOL, size=10, replace=False).tolist()) for _ in range(24)]
+    base = random_queries(1, 31, yet.n_trials)[0]
+    long_q = dict(base, layer_elts=big_layers[:6], occ_ret=[2e4] * 6, occ_lim=[2e6] * 6,
+                  agg_ret=[5e6] * 6, agg_lim=[2e8] * 6, trials=(0, yet.n_trials), want_adjoint=True)
+    head_q = dict(base, layer_elts=big_layers, occ_ret=[2e4] * 24, occ_lim=[2e6] * 24,
+                  agg_ret=[5e6] * 24, agg_lim=[2e8] * 24, trials=(0, yet.n_trials), want_adjoint=False)
+    small = [dict(base, layer_elts=[big_layers[k][:3]], occ_ret=[2e4], occ_lim=[2e6], agg_ret=[5e6],
+                  agg_lim=[2e8], trials=(100 * k, 100 * k + 300), want_adjoint=False)
+             for k in range(6)]
+    probe = ara.Server(pool, off, ev, max_concurrent=1)
+    est = {name: probe.estimate_bytes(**q) for name, q in
+           (("long", long_q), ("head", head_q), ("small", small[0]))}
+    probe.close()
+    assert est["head"] > 2 * est["small"]
+    budget = est["long"] + est["small"] + 4096     # the head does not fit beside the long one
+    srv = ara.Server(pool, off, ev, max_concurrent=2, memory_budget=budget, max_merge=1)
+    tickets = [srv.submit(**long_q), srv.submit(**head_q)] + [srv.submit(**q) for q in small]
+    res = [srv.wait(t) for t in tickets]
+    cnt = srv.counters()
+    srv.close()
+    assert 1 <= cnt["head_passed"] <= 4
+    alone = ara.Server(pool, off, ev, max_concurrent=1, max_merge=1)
+    for q, m in zip([long_q, head_q] + small, res):
+        a = alone.wait(alone.submit(**q))
+        for k in ("pml", "tvar", "mean", "grad_layer"):
+            assert (a[k] is None and m[k] is None) or np.array_equal(a[k], m[k]), k
+    alone.close()
