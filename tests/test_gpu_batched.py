@@ -186,3 +186,73 @@ def test_requests_in_one_pass_reject_bad_arguments(case):
             g.run_ylt_requests(off, ids, rq)
         assert e.value.status in (ara.ARA_EINVAL, ara.ARA_ERANGE)
     g.close()
+
+
+def test_batched_workload_full_size_sampled():
+    """The batched workload at its full size (64 layers of U{3..30} ELTs from a pool of 200,
+    2,000,000-event catalogue, 2x10^5 trials of Poisson(U[200, 2000]) events) through the
+    autotuned plan that bench.py times: 256 sampled trials of every layer against the oracle
+    (which evaluates only those trials), and the selected layers' rows equal to single-layer
+    runs bit for bit."""
+    pf = synth.batched_portfolio(0)
+    yet = synth.batched_yet(0, n_trials=200_000)
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    plan = ara.BatchedPlan(g, off, ids, autotune=True)
+    y = plan.launch()
+    g.check()
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(yet.n_trials, size=256, replace=False))
+    ref, agg = oracle.ylt(pf, yet, trials=sample, return_agg=True)
+    got = y[:, torch.from_numpy(sample).cuda()].cpu().numpy()
+    err = np.abs(got - ref)
+    assert np.all(err <= 1e-6 * np.abs(ref) + 1e-12 * np.abs(agg))
+    assert np.count_nonzero(ref) > 0.1 * ref.size
+    for l in (0, 31, 63):
+        single = g.run_ylt(off, ids, layers=[l])
+        assert torch.equal(single[0], y[l])
+    plan.close()
+    g.close()
+
+
+def test_merged_requests_on_the_serving_pool_sampled():
+    """Four requests of the serving trace (their own layers of the 500-ELT pool, 2,000,000-event
+    catalogue) merged in one pass over their slices (scaled from the trace's 10^6 trials to a
+    2x10^5-trial Poisson(1000) YET): every request's YLT equals its run alone bit for bit, and
+    128 sampled trials of each match the oracle."""
+    pool_t = synth.serving_pool(0)
+    n = 200_000
+    yet = synth.serving_yet(0, n_trials=n)
+    trace = synth.serving_trace(pool_t, 1_000_000, 8, 200.0, seed=0)[:4]
+    for q in trace:   # the trace's slices of a 10^6-trial YET, scaled to this one
+        q["trials"] = (q["trials"][0] * n // 1_000_000, max(q["trials"][1] * n // 1_000_000,
+                                                             q["trials"][0] * n // 1_000_000 + 1))
+    layers = [l for q in trace for l in q["layer_elts"]]
+    terms = {k: np.asarray([x for q in trace for x in q[k]]) for k in ("occ_ret", "occ_lim", "agg_ret", "agg_lim")}
+    tab = synth.Portfolio(pool_t.catalogue, pool_t.elt_ids, pool_t.elt_losses, pool_t.elt_ret,
+                          pool_t.elt_lim, layers, terms["occ_ret"], terms["occ_lim"],
+                          terms["agg_ret"], terms["agg_lim"], losses_f32=True)
+    if sum(len(q["layer_elts"]) for q in trace) > 255:
+        pytest.skip("more than 255 layers in the group")
+    g = ara.Portfolio.from_tables(tab)
+    off, ids = dev(yet)
+    reqs, l0 = [], 0
+    for q in trace:
+        nl = len(q["layer_elts"])
+        reqs.append((l0, l0 + nl, q["trials"][0], q["trials"][1]))
+        l0 += nl
+    ys = g.run_ylt_requests(off, ids, reqs)
+    g.check()
+    rng = np.random.default_rng(7)
+    for (a, b, t0, t1), y in zip(reqs, ys):
+        alone = g.run_ylt(off[t0:t1 + 1], ids, layers=list(range(a, b)))
+        assert torch.equal(y, alone)
+        sample = np.sort(rng.choice(np.arange(t0, t1), size=min(128, t1 - t0), replace=False))
+        sub = tab.with_terms(tab.terms_dict())
+        sub.layer_elts = tab.layer_elts[a:b]
+        for name in ("occ_ret", "occ_lim", "agg_ret", "agg_lim"):
+            setattr(sub, name, np.asarray(getattr(tab, name))[a:b])
+        ref, agg = oracle.ylt(sub, yet, trials=sample, return_agg=True)
+        got = y[:, torch.from_numpy(sample - t0).cuda()].cpu().numpy()
+        assert np.all(np.abs(got - ref) <= 1e-6 * np.abs(ref) + 1e-12 * np.abs(agg))
+    g.close()
