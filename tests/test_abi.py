@@ -114,3 +114,32 @@ def test_run_rejects_null_portfolio(L):
     assert L.ara_check(None, None) == ara.ARA_EINVAL
     ms, n = ctypes.c_double(), ctypes.c_int64()
     assert L.ara_timing_read(99, ctypes.byref(ms), ctypes.byref(n)) == ara.ARA_EINVAL
+
+
+def test_new_entry_points_reject_null_handles_on_host(L):
+    """The multi-request pass, the server's merging and estimate calls, and the plan table reject
+    missing handles and arguments before touching a device; releasing pooled memory with no pool
+    created is a no-op."""
+    p = ctypes.c_void_p(256)          # never dereferenced: the handle check fails first
+    first = np.array([0, 1], dtype=np.int32)
+    tb, te = np.array([0], dtype=np.int64), np.array([1], dtype=np.int64)
+    ptrs = (ctypes.c_void_p * 1)(256)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    assert L.ara_run_ylt_requests(None, 1, p, 0, p, 1, P(first), P(tb), P(te),
+                                  ctypes.cast(ptrs, ctypes.c_void_p), None, None) == ara.ARA_EINVAL
+    assert L.ara_server_set_merging(None, 2, 0.3) == ara.ARA_EINVAL
+    b = ctypes.c_int64()
+    assert L.ara_server_estimate_bytes(None, None, ctypes.byref(b)) == ara.ARA_EINVAL
+    n = ctypes.c_int64()
+    assert L.ara_server_counters(None, ctypes.byref(n), ctypes.byref(n), ctypes.byref(n)) == ara.ARA_EINVAL
+    assert L.ara_plan_table(None, None, ctypes.byref(n)) == ara.ARA_EINVAL
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        assert L.ara_release_memory() == ara.ARA_OK
+
+
+def test_timing_classes_of_the_host_pipeline_are_readable(L):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    for k in (ara.ARA_K_TRANSFER, ara.ARA_K_HOST_CHECK):
+        assert L.ara_timing_read(k, ctypes.byref(ms), ctypes.byref(n)) == ara.ARA_OK
+    assert L.ara_timing_read(7, ctypes.byref(ms), ctypes.byref(n)) == ara.ARA_EINVAL
