@@ -196,17 +196,19 @@ def stream_kernel_name(flags):
 
 
 def ncu_profile_figures():
-    """Per-occurrence figures of the YET-stream kernel from the committed ncu summary
-    (profiles/k_ylt_bulk_paper_scale.md, lines 'key: value'): dram_bytes_per_event,
-    l2_hit_rate_pct, gather_sectors_per_event.  Empty when the summary is absent or was taken of
+    """Per-occurrence figures of the YET-stream kernel from the committed ncu capture figures
+    (profiles/k_ylt_bulk_paper_scale.txt, lines 'key: value'): dram_bytes_per_event,
+    l2_hit_rate_pct, gather_sectors_per_event.  Empty when the file is absent or was taken of
     another kernel source (its 'kernel_source_sha' line differs)."""
-    path = os.path.join(ROOT, "profiles", "k_ylt_bulk_paper_scale.md")
+    path = os.path.join(ROOT, "profiles", "k_ylt_bulk_paper_scale.txt")
     out = {}
     try:
         kv = {}
         with open(path) as f:
             for line in f:
-                line = line.strip().lstrip("-* ").strip()
+                line = line.strip()
+                if line.startswith("#"):
+                    continue
                 if ":" in line:
                     k, v = line.split(":", 1)
                     kv[k.strip().strip("`")] = v.strip().strip("`")
@@ -473,7 +475,7 @@ def run_ours(args, rank, ws, local):
             "frac": round(achieved / peak, 4), "traffic": (tpe * n_events if tpe else None),
             "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture of "
                                "this kernel source at 1e8 occurrences "
-                               "(profiles/k_ylt_bulk_paper_scale.md), scaled per occurrence to "
+                               "(profiles/k_ylt_bulk_paper_scale.txt), scaled per occurrence to "
                                "this launch" if tpe else "no capture of the current kernel source"),
             "l2_hit_rate_pct": prof.get("l2_hit_rate_pct"),
             "gather_sectors_per_occurrence": prof.get("gather_sectors_per_event"),

@@ -1,6 +1,6 @@
 """CPU checks of bench.py's bookkeeping: the kernel-source hash that keys the recorded DRAM
-traffic ignores comments and blank lines but not code, and a profile summary's traffic line is
-read only while its hash matches the sources."""
+traffic ignores comments and blank lines but not code, and the recorded capture figures are
+read only while their hash matches the sources."""
 import os
 import shutil
 
@@ -33,11 +33,11 @@ def test_hash_ignores_comments_and_blank_lines(tree):
 
 
 def test_profile_figures_are_read_only_for_the_matching_source(tree):
-    prof = tree / "profiles" / "k_ylt_bulk_paper_scale.md"
-    prof.write_text(f"- kernel_source_sha: {bench.kernel_source_sha()}\n- dram_bytes_per_event: 4.25\n"
-                    "- l2_hit_rate_pct: 61.5 (lts__t_sector_hit_rate.pct)\n")
+    prof = tree / "profiles" / "k_ylt_bulk_paper_scale.txt"
+    prof.write_text(f"# figures\nkernel_source_sha: {bench.kernel_source_sha()}\ndram_bytes_per_event: 4.25\n"
+                    "l2_hit_rate_pct: 61.5 (lts__t_sector_hit_rate.pct)\n")
     fig = bench.ncu_profile_figures()
     assert fig["dram_bytes_per_event"] == pytest.approx(4.25)
     assert fig["l2_hit_rate_pct"] == pytest.approx(61.5)
-    prof.write_text("- kernel_source_sha: 0000000000000000\n- dram_bytes_per_event: 4.25\n")
+    prof.write_text("kernel_source_sha: 0000000000000000\ndram_bytes_per_event: 4.25\n")
     assert bench.ncu_profile_figures() == {}
