@@ -142,6 +142,11 @@ ARA_API ara_status ara_create_layer_set(ara_portfolio* pool, int32_t n_layers,
                                  occurrence loss net of ELT and occurrence terms (the loss behind
                                  occurrence exceedance curves); aggregate terms not applied,
                                  regimes all 0.  Only with the default folded path */
+#define ARA_RUN_PREPARED 256 /* the fold of the selected layers (per-ELT and occurrence terms,
+                                 and the coarse hit bitmap) was queued earlier by
+                                 ara_prepare_ylt into fold slot 0 (or 1 with ARA_RUN_SLOT1):
+                                 the run only streams the YET.  Folded paths only */
+#define ARA_RUN_SLOT1   512   /* with ARA_RUN_PREPARED: use fold slot 1 */
 #define ARA_RUN_HOST_DIRECT 16 /* ara_run_ylt_host only: the kernel reads the (pinned, device-
                                  mapped) host YET in place over the CPU-GPU link instead of
                                  staging it with copies; ARA_EINVAL if the host arrays are not
@@ -166,13 +171,34 @@ ARA_API ara_status ara_create_layer_set(ara_portfolio* pool, int32_t n_layers,
  *   d_regimes        device [n_layer_sel][n_trials] uint8 or NULL: the aggregate clamp's
  *                    regime per trial (0: S <= AggR or kink, 1: AggR < S < AggR + AggL,
  *                    2: S > AggR + AggL), recorded for ara_adjoint
- *   flags            ARA_RUN_* (one of FOLDED / PER_ELT, optionally NO_FILTER, F64_SUM)
- * Errors: ARA_EINVAL, ARA_ECUDA; data errors via ara_check().
+ *   flags            ARA_RUN_* (one of FOLDED / PER_ELT, optionally NO_FILTER, F64_SUM; PREPARED
+ *                    and SLOT1 to stream against a fold queued by ara_prepare_ylt)
+ * Errors: ARA_EINVAL (also: ARA_RUN_SLOT1 before slot 1 was ever prepared), ARA_ECUDA; data
+ * errors via ara_check().
  */
 ARA_API ara_status ara_run_ylt(ara_portfolio* pf, int64_t n_trials, const int64_t* d_trial_offsets,
                        int64_t n_events, const int32_t* d_event_ids, const float* d_timestamps,
                        int32_t n_layer_sel, const int32_t* layer_sel, double* d_ylt,
                        uint8_t* d_regimes, int32_t flags, void* stream);
+
+/*
+ * The fold of a run queued on its own: for the selected layers, the per-ELT and occurrence
+ * terms of every catalogue event (Algorithm 3's ELT loop and occurrence terms, which depend on
+ * the event alone, Section IV-B) into fold slot `slot` (0 or 1) of the portfolio, with the hit
+ * bitmaps the stream kernel of `flags` reads.  A later ara_run_ylt with ARA_RUN_PREPARED (and
+ * ARA_RUN_SLOT1 for slot 1), the same layers and the same other flags streams the YET against it
+ * without folding again; ordering is the caller's (same stream, or an event).  Two slots let the
+ * fold of one run proceed on another stream while the previous run streams from the other slot
+ * (the paper has no counterpart; this is a pipelining of Algorithm 1's loop over runs).  The
+ * first use of slot 1 allocates it (catalogue x ~8.3 bytes per layer; synchronises `stream`).
+ * A slot holds the fold of the last prepare (or, slot 0, of the last unprepared run) of each
+ * layer: a prepared run after the portfolio's slot was overwritten reads that newer fold.
+ *   flags      ARA_RUN_* of the run to come (NO_FILTER, F64_SUM, LDG, OEP); not PER_ELT,
+ *              BATCHED, HOST_DIRECT, PREPARED or SLOT1
+ * Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA.
+ */
+ARA_API ara_status ara_prepare_ylt(ara_portfolio* pf, int32_t n_layer_sel, const int32_t* layer_sel,
+                                   int32_t slot, int32_t flags, void* stream);
 
 /*
  * The whole analysis from host memory: Algorithm 1 with the transfer of Algorithm 2 and the

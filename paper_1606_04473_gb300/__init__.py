@@ -45,6 +45,7 @@ class Query(ctypes.Structure):
                 ("flags", ctypes.c_int32), ("tenant", ctypes.c_int32)]
 ARA_K_FOLD, ARA_K_YLT, ARA_K_SELECT, ARA_K_ADJOINT, ARA_K_BATCHED = 0, 1, 2, 3, 4
 ARA_K_TRANSFER, ARA_K_HOST_CHECK = 5, 6
+ARA_RUN_PREPARED, ARA_RUN_SLOT1 = 256, 512
 ARA_PLAN_AUTOTUNE = 1
 
 _lib = None
@@ -105,6 +106,8 @@ def lib() -> ctypes.CDLL:
     L.ara_server_stats.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64),
                                    ctypes.POINTER(i64)]
     L.ara_server_stats.restype = i32
+    L.ara_prepare_ylt.argtypes = [P, i32, P, i32, i32, P]
+    L.ara_prepare_ylt.restype = i32
     L.ara_run_ylt_requests.argtypes = [P, i64, P, i64, P, i32, P, P, P, P, P, P]
     L.ara_run_ylt_requests.restype = i32
     L.ara_release_memory.argtypes = []
@@ -243,6 +246,13 @@ class Portfolio:
                                int(flags), _stream_handle(stream))
         _check(st, "ara_run_ylt")
         return out
+
+    def prepare_ylt(self, layers=None, slot: int = 0, flags: int = 0, stream=None):
+        """Queue the fold of the selected layers into fold slot 0 or 1 (ara_prepare_ylt); a later
+        run_ylt with flags ARA_RUN_PREPARED (| ARA_RUN_SLOT1 for slot 1) streams against it."""
+        n_sel, sel_p, _n_out, _sel = self._sel(layers)
+        _check(lib().ara_prepare_ylt(self._h, n_sel, sel_p, int(slot), int(flags),
+                                     _stream_handle(stream)), "ara_prepare_ylt")
 
     def run_ylt_requests(self, offsets, event_ids, requests, regimes: bool = False, stream=None):
         """Several requests in one pass (ara_run_ylt_requests): requests is a list of

@@ -215,6 +215,9 @@ static void free_portfolio(ara_portfolio* p) {
   }
   if (p->d_res) cudaFree(p->d_res);
   if (p->h_res) cudaFreeHost(p->h_res);
+  void* alt[] = {p->d_q_alt, p->d_bits_alt, p->d_cbits_alt};
+  for (void* q : alt)
+    if (q) cudaFree(q);
   if (p->d_sel_scratch) cudaFree(p->d_sel_scratch);
   for (int i = 0; i < 2; ++i) {
     if (p->ev_copied[i]) cudaEventDestroy(p->ev_copied[i]);
@@ -587,9 +590,15 @@ static ara_status check_selection(const Portfolio& pf, int32_t n_sel, const int3
 
 static ara_status check_flags(const Portfolio& pf, int32_t flags) {
   if (flags & ~(ARA_RUN_PER_ELT | ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG |
-                ARA_RUN_HOST_DIRECT | ARA_RUN_BATCHED | ARA_RUN_OEP))
+                ARA_RUN_HOST_DIRECT | ARA_RUN_BATCHED | ARA_RUN_OEP | ARA_RUN_PREPARED | ARA_RUN_SLOT1))
     return ARA_EINVAL;
-  if ((flags & ARA_RUN_OEP) && (flags & ~ARA_RUN_OEP)) return ARA_EINVAL;   // default path only
+  // a prepared fold slot serves the folded paths run from device memory
+  if ((flags & (ARA_RUN_PREPARED | ARA_RUN_SLOT1)) &&
+      (flags & (ARA_RUN_PER_ELT | ARA_RUN_BATCHED | ARA_RUN_HOST_DIRECT)))
+    return ARA_EINVAL;
+  if ((flags & ARA_RUN_SLOT1) && !(flags & ARA_RUN_PREPARED)) return ARA_EINVAL;
+  if ((flags & ARA_RUN_OEP) && (flags & ~(ARA_RUN_OEP | ARA_RUN_PREPARED | ARA_RUN_SLOT1)))
+    return ARA_EINVAL;   // default path only
   if ((flags & ARA_RUN_BATCHED) &&
       (flags & (ARA_RUN_PER_ELT | ARA_RUN_NO_FILTER | ARA_RUN_F64_SUM | ARA_RUN_LDG | ARA_RUN_HOST_DIRECT)))
     return ARA_EINVAL;
@@ -598,6 +607,38 @@ static ara_status check_flags(const Portfolio& pf, int32_t flags) {
     return ARA_EINVAL;
   if ((flags & ARA_RUN_PER_ELT) && !pf.d_dense) return ARA_EINVAL;
   return ARA_OK;
+}
+
+ara_status ara_prepare_ylt(ara_portfolio* pf, int32_t n_sel, const int32_t* layer_sel, int32_t slot,
+                           int32_t flags, void* stream) {
+  if (!pf || slot < 0 || slot > 1) return ARA_EINVAL;
+  std::vector<int32_t> sel;
+  ara_status st = check_selection(*pf, n_sel, layer_sel, sel);
+  if (st != ARA_OK) return st;
+  if (flags & (ARA_RUN_PREPARED | ARA_RUN_SLOT1 | ARA_RUN_PER_ELT | ARA_RUN_BATCHED | ARA_RUN_HOST_DIRECT))
+    return ARA_EINVAL;
+  if ((st = check_flags(*pf, flags)) != ARA_OK) return st;
+  if (sel.empty()) return ARA_OK;
+  DeviceGuard g(pf->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (slot == 1 && !pf->d_q_alt) {   // the second workspace, allocated on first use
+    const size_t nl = (size_t)std::max(pf->n_layers, 1), C = (size_t)pf->catalogue;
+    ARA_TRY(cudaStreamSynchronize(s));
+    if (cudaMalloc(&pf->d_q_alt, sizeof(uint64_t) * nl * C) != cudaSuccess ||
+        cudaMalloc(&pf->d_bits_alt, sizeof(uint32_t) * nl * (size_t)pf->bm_words) != cudaSuccess ||
+        cudaMalloc(&pf->d_cbits_alt, sizeof(uint32_t) * nl * (size_t)pf->cbits_stride) != cudaSuccess) {
+      cudaGetLastError();
+      if (pf->d_q_alt) cudaFree(pf->d_q_alt);
+      if (pf->d_bits_alt) cudaFree(pf->d_bits_alt);
+      if (pf->d_cbits_alt) cudaFree(pf->d_cbits_alt);
+      pf->d_q_alt = nullptr;
+      pf->d_bits_alt = nullptr;
+      pf->d_cbits_alt = nullptr;
+      return ARA_ENOMEM;
+    }
+  }
+  if ((st = launch_fold(*pf, (int32_t)sel.size(), sel.data(), flags, s, slot)) != ARA_OK) return st;
+  return launch_coarsen(*pf, (int32_t)sel.size(), sel.data(), flags, s, slot);
 }
 
 ara_status ara_run_ylt(ara_portfolio* pf, int64_t n_trials, const int64_t* d_offsets,
@@ -616,10 +657,15 @@ ara_status ara_run_ylt(ara_portfolio* pf, int64_t n_trials, const int64_t* d_off
   if (((uintptr_t)d_ids & 3) || ((uintptr_t)d_offsets & 7) || ((uintptr_t)d_ylt & 7)) return ARA_EINVAL;
   DeviceGuard g(pf->device);
   cudaStream_t s = (cudaStream_t)stream;
-  if (!(flags & (ARA_RUN_PER_ELT | ARA_RUN_BATCHED))) {
+  const bool prepared = (flags & ARA_RUN_PREPARED) != 0;
+  const int slot = (flags & ARA_RUN_SLOT1) ? 1 : 0;
+  if (slot == 1 && !pf->d_q_alt) return ARA_EINVAL;   // slot 1 never prepared
+  if (!prepared && !(flags & (ARA_RUN_PER_ELT | ARA_RUN_BATCHED))) {
     if ((st = launch_fold(*pf, (int32_t)sel.size(), sel.data(), flags, s)) != ARA_OK) return st;
   }
   YltArgs a{};
+  a.slot = slot;
+  a.prepared = prepared;
   a.n_trials = n_trials;
   a.offsets = d_offsets;
   a.id_base = 0;
@@ -698,7 +744,7 @@ ara_status ara_run_ylt_host(ara_portfolio* pf, int64_t n_trials, const int64_t* 
   if (metrics && (sel.empty() || (n_rp > 0 && !h_pml) || (n_tvar > 0 && !h_tvar) ||
                   validate_metrics(n_trials, n_rp, rps, n_tvar, levels) != ARA_OK))
     return ARA_EINVAL;
-  if (flags & ARA_RUN_BATCHED) return ARA_EINVAL;
+  if (flags & (ARA_RUN_BATCHED | ARA_RUN_PREPARED | ARA_RUN_SLOT1)) return ARA_EINVAL;
   if (h_off[0] != 0) return ARA_EINVAL;
   // Host check that the offsets never decrease (no early exit, so the scan vectorises), timed
   // under ARA_K_HOST_CHECK.

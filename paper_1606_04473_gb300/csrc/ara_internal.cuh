@@ -115,6 +115,11 @@ struct Portfolio {
   int64_t bm_words = 0;             // words per layer (padded to a multiple of 4)
   uint32_t* d_cbits = nullptr;      // [n_layers][cbits_stride]: coarse bitmap (1 bit / 2^k events)
   int64_t cbits_stride = 0;
+  // a second fold workspace (slot 1 of ara_prepare_ylt), allocated on first use, so that the
+  // fold of one run can proceed while another run streams from the first
+  uint64_t* d_q_alt = nullptr;
+  uint32_t* d_bits_alt = nullptr;
+  uint32_t* d_cbits_alt = nullptr;
   uint32_t* d_err = nullptr;        // device error word
   // host-input pipeline resources (grown on demand)
   cudaStream_t copy_stream = nullptr;
@@ -148,10 +153,26 @@ struct YltArgs {
   uint8_t* regimes;         // row i at regimes + i * row_stride, or nullptr
   int64_t row_stride;       // elements between the rows of consecutive selected layers
   int32_t flags;
+  int32_t slot = 0;         // fold workspace slot (0 or 1)
+  bool prepared = false;    // fold and coarse bitmap already in the slot (ara_prepare_ylt)
 };
 
+// The fold workspace of a slot: q tables, exact and coarse hit bitmaps of every layer.
+struct FoldSlot {
+  uint64_t* q;
+  uint32_t* bits;
+  uint32_t* cbits;
+};
+inline FoldSlot fold_slot(const struct Portfolio& pf, int slot) {
+  return slot ? FoldSlot{pf.d_q_alt, pf.d_bits_alt, pf.d_cbits_alt} : FoldSlot{pf.d_q, pf.d_bits, pf.d_cbits};
+}
+
 ara_status launch_fold(Portfolio& pf, int32_t n_sel, const int32_t* sel_host, int32_t flags,
-                       cudaStream_t s);
+                       cudaStream_t s, int slot = 0);
+// The coarse hit bitmaps the default stream kernel reads (when the exact bitmap does not fit in
+// shared memory), built from the slot's exact bitmaps.
+ara_status launch_coarsen(Portfolio& pf, int32_t n_sel, const int32_t* sel_host, int32_t flags,
+                          cudaStream_t s, int slot);
 // Fold into caller-chosen outputs (see k_fold): used by the adjoint for occurrence regimes and
 // by the batched plan for every selected layer at once.
 struct FoldOutHost {

@@ -870,10 +870,12 @@ ara_status launch_fold_to(Portfolio& pf, int32_t n_sel, const int32_t* sel_host,
 }
 
 ara_status launch_fold(Portfolio& pf, int32_t n_sel, const int32_t* sel_host, int32_t flags,
-                       cudaStream_t s) {
+                       cudaStream_t s, int slot) {
+  const FoldSlot ws = fold_slot(pf, slot);
+  if (!ws.q || !ws.bits) return ARA_EINVAL;
   FoldOutHost o{};
-  o.q = pf.d_q;
-  o.bits = pf.d_bits;
+  o.q = ws.q;
+  o.bits = ws.bits;
   o.q_stride = pf.catalogue;
   o.bits_stride = pf.bm_words;
   o.f64_table = (flags & ARA_RUN_F64_SUM) ? 1 : 0;
@@ -950,11 +952,41 @@ void bulk_shape(int32_t i, int32_t* warps, int32_t* stages) {
   *stages = kBulkShapes[i][1] * 10000 + kBulkShapes[i][2];   // stages * 10000 + chunk IDs
 }
 
-ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
-  const bool ldg = (a.flags & ARA_RUN_LDG) != 0;
-  // shared-memory budget of the hit bitmap: what the block may use beyond the staging ring
+// Shift of the hit bitmap the stream kernel of these run flags keeps in shared memory: what the
+// block may use beyond the staging ring (the register-staged kernel has no ring).
+static int run_bitmap_shift(const Portfolio& pf, int32_t flags) {
+  const bool ldg = (flags & ARA_RUN_LDG) != 0;
   const int64_t max_smem_bitmap =
       ldg ? 200 * 1024 : (int64_t)pf.max_smem_block - bulk_ring_bytes() - 128;
+  return bitmap_shift(pf.catalogue, max_smem_bitmap);
+}
+
+ara_status launch_coarsen(Portfolio& pf, int32_t n_sel, const int32_t* sel_host, int32_t flags,
+                          cudaStream_t s, int slot) {
+  const bool ldg = (flags & ARA_RUN_LDG) != 0, per_elt = (flags & ARA_RUN_PER_ELT) != 0;
+  const bool nof = (flags & ARA_RUN_NO_FILTER) != 0;
+  const int shift = run_bitmap_shift(pf, flags);
+  if (ldg || per_elt || nof || shift == 0) return ARA_OK;   // no coarse bitmap is read
+  if (shift > 26) return ARA_EINVAL;
+  const FoldSlot ws = fold_slot(pf, slot);
+  if (!ws.bits || !ws.cbits) return ARA_EINVAL;
+  const int64_t cwords_pad = (coarse_words(pf.catalogue, shift) + 3) / 4 * 4;
+  if (cwords_pad > pf.cbits_stride) return ARA_EINVAL;
+  for (int32_t i = 0; i < n_sel; ++i) {
+    const int layer = sel_host[i];
+    LaunchScope ls(ARA_K_FOLD, s);
+    k_coarsen<<<(unsigned)std::min<int64_t>((cwords_pad + 255) / 256, 4096), 256, 0, s>>>(
+        ws.bits + (int64_t)layer * pf.bm_words, pf.bm_words, shift,
+        ws.cbits + (int64_t)layer * pf.cbits_stride, cwords_pad);
+    ARA_TRY(cudaGetLastError());
+  }
+  return ARA_OK;
+}
+
+ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
+  const bool ldg = (a.flags & ARA_RUN_LDG) != 0;
+  const FoldSlot ws = fold_slot(pf, a.slot);
+  if (!ws.q || !ws.bits) return ARA_EINVAL;
   StreamParams sp{};
   sp.n_trials = a.n_trials;
   sp.offsets = a.offsets;
@@ -963,13 +995,17 @@ ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   sp.ids = a.ids;
   sp.mis = (int32_t)(((uintptr_t)a.ids >> 2) & 3);
   sp.catalogue = pf.catalogue;
-  sp.shift = bitmap_shift(pf.catalogue, max_smem_bitmap);
+  sp.shift = run_bitmap_shift(pf, a.flags);
   if (sp.shift > 26) return ARA_EINVAL;   // the bulk lookup's multiplier is 2^(27 - shift)
   sp.smem_words = coarse_words(pf.catalogue, sp.shift);
   sp.bm_words = pf.bm_words;
   sp.err = pf.d_err;
-  // the bulk kernel copies a ready bitmap: exact when it fits, else the coarse one built here
-  const int64_t cwords_pad = (sp.smem_words + 3) / 4 * 4;
+  // the bulk kernel copies a ready bitmap: exact when it fits, else the coarse one (built here,
+  // or by ara_prepare_ylt for a prepared run)
+  if (!a.prepared) {
+    const ara_status st0 = launch_coarsen(pf, a.n_sel, a.sel, a.flags, s, a.slot);
+    if (st0 != ARA_OK) return st0;
+  }
   sp.wait_limit_ns = g_wait_limit_ns.load();
   sp.debug_extra_tx = g_debug_extra_tx.load();
   sp.word_bytes = 4;
@@ -978,18 +1014,10 @@ ara_status launch_ylt(Portfolio& pf, const YltArgs& a, cudaStream_t s) {
   const bool f64 = (a.flags & ARA_RUN_F64_SUM) != 0;
   for (int32_t i = 0; i < a.n_sel; ++i) {
     const int layer = a.sel[i];
-    sp.q = pf.d_q + (int64_t)layer * pf.catalogue;
-    sp.bits = pf.d_bits + (int64_t)layer * pf.bm_words;
+    sp.q = ws.q + (int64_t)layer * pf.catalogue;
+    sp.bits = ws.bits + (int64_t)layer * pf.bm_words;
     sp.layer = pf.d_layers + layer;
-    if (!ldg && !per_elt && !nof && sp.shift > 0 && a.n_trials > 0) {
-      uint32_t* cb = pf.d_cbits + (int64_t)layer * pf.cbits_stride;
-      if (cwords_pad > pf.cbits_stride) return ARA_EINVAL;
-      LaunchScope ls(ARA_K_FOLD, s);
-      k_coarsen<<<(unsigned)std::min<int64_t>((cwords_pad + 255) / 256, 4096), 256, 0, s>>>(
-          pf.d_bits + (int64_t)layer * pf.bm_words, pf.bm_words, sp.shift, cb, cwords_pad);
-      ARA_TRY(cudaGetLastError());
-      sp.bits = cb;
-    }
+    if (!ldg && !per_elt && !nof && sp.shift > 0) sp.bits = ws.cbits + (int64_t)layer * pf.cbits_stride;
     sp.ylt = a.ylt + (int64_t)i * a.row_stride;
     sp.regimes = a.regimes ? a.regimes + (int64_t)i * a.row_stride : nullptr;
     if (a.n_trials == 0) continue;

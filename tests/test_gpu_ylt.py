@@ -474,3 +474,78 @@ def test_fp32_storage_widens_exactly():
         g.close()
     assert torch.equal(out[0], out[1])
     assert (out[0][0] > 0).any() and (out[0][1] > 0).any()
+
+
+@pytest.mark.parametrize("flags", [0, 2, 4, 8, 64])
+def test_prepared_fold_slots_equal_unprepared_runs(mid, flags):
+    """ara_prepare_ylt queues the fold (and coarse bitmap) into slot 0 or 1; runs with
+    ARA_RUN_PREPARED (| ARA_RUN_SLOT1) stream against it and equal an ordinary run bit for bit,
+    for both slots, a layer subset, and with the two slots holding different layer sets."""
+    pf, yet, ref, agg = mid
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    want = g.run_ylt(off, ids, flags=flags).clone()
+    g.prepare_ylt(slot=0, flags=flags)
+    a = g.run_ylt(off, ids, flags=flags | ara.ARA_RUN_PREPARED).clone()
+    g.prepare_ylt(layers=[3, 1], slot=1, flags=flags)
+    b = g.run_ylt(off, ids, layers=[3, 1], flags=flags | ara.ARA_RUN_PREPARED | ara.ARA_RUN_SLOT1)
+    c = g.run_ylt(off, ids, flags=flags | ara.ARA_RUN_PREPARED)       # slot 0 still holds all
+    g.check()
+    assert torch.equal(a, want) and torch.equal(c, want)
+    assert torch.equal(b[0], want[3]) and torch.equal(b[1], want[1])
+    if flags != 64:
+        assert_ylt_close(a.cpu().numpy(), ref, agg)
+    g.close()
+
+
+def test_prepared_fold_pipelined_over_two_streams_at_paper_scale_catalogue():
+    """The paper-scale portfolio (2,000,000-event catalogue: the stream kernel reads the coarse
+    bitmap, built by the prepare) on 3,000 trials x 1,000 events: folds queued on a second
+    stream into alternating slots while the first stream runs the YET against the other slot,
+    as bench.py schedules its steps; every run equals an ordinary run bit for bit."""
+    pf = synth.paper_scale_portfolio(0)
+    yet = synth.paper_scale_yet(0, n_trials=3000)
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    want = g.run_ylt(off, ids).clone()
+    A = torch.cuda.current_stream()
+    C = torch.cuda.Stream()
+    outs = [torch.empty_like(want) for _ in range(6)]
+    ev_fold = [torch.cuda.Event() for _ in range(6)]
+    ev_run = [torch.cuda.Event() for _ in range(6)]
+    for k in range(6):
+        s = k % 2
+        if k >= 2:
+            C.wait_event(ev_run[k - 2])          # the run two steps back read this slot
+        g.prepare_ylt(slot=s, stream=C)
+        ev_fold[k].record(C)
+        A.wait_event(ev_fold[k])
+        g.run_ylt(off, ids, out=outs[k], flags=ara.ARA_RUN_PREPARED | (ara.ARA_RUN_SLOT1 if s else 0))
+        ev_run[k].record(A)
+    torch.cuda.synchronize()
+    g.check()
+    for o in outs:
+        assert torch.equal(o, want)
+    sample = np.arange(0, 3000, 97)
+    ref, agg = oracle.ylt(pf, yet, trials=sample, return_agg=True)
+    assert_ylt_close(want[:, torch.from_numpy(sample).cuda()].cpu().numpy(), ref, agg)
+    g.close()
+
+
+def test_prepared_fold_flag_rules(mid):
+    pf, yet, _, _ = mid
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    P, S1 = ara.ARA_RUN_PREPARED, ara.ARA_RUN_SLOT1
+    for flags in (S1, P | ara.ARA_RUN_BATCHED):
+        with pytest.raises(ara.AraError) as e:
+            g.run_ylt(off, ids, flags=flags)
+        assert e.value.status == ara.ARA_EINVAL
+    with pytest.raises(ara.AraError):           # slot 1 never prepared on this portfolio
+        g.run_ylt(off, ids, flags=P | S1)
+    for bad in ((2, 0), (0, ara.ARA_RUN_BATCHED), (0, P)):
+        with pytest.raises(ara.AraError):
+            g.prepare_ylt(slot=bad[0], flags=bad[1])
+    with pytest.raises(ara.AraError):
+        g.run_ylt_host(yet.offsets, yet.event_ids, flags=P)
+    g.close()
