@@ -541,10 +541,13 @@ ARA_API ara_status ara_set_stream_shape(int32_t index);
  *                          which exercises the timeout path without any fault.
  *   ARA_DBG_SKIP_BARRIER_ARRIVAL  1: the selection's blocks do not arrive at its grid
  *                          barriers, so every barrier wait runs out (0 = normal).
+ *   ARA_DBG_ADJOINT_PER_LAYER  1: ara_adjoint of several layers takes one histogram pass per
+ *                          layer instead of one pass for all (0 = normal); same results.
  * ARA_EINVAL for an unknown key or value. */
 #define ARA_DBG_WAIT_LIMIT_NS  1
 #define ARA_DBG_STARVE_COPIES  2
 #define ARA_DBG_SKIP_BARRIER_ARRIVAL 3
+#define ARA_DBG_ADJOINT_PER_LAYER 4
 ARA_API ara_status ara_debug_set(int32_t key, int64_t value);
 
 /* kernel classes for timing */

@@ -634,6 +634,7 @@ def set_stream_shape(index: int):
 
 
 ARA_DBG_WAIT_LIMIT_NS, ARA_DBG_STARVE_COPIES, ARA_DBG_SKIP_BARRIER_ARRIVAL = 1, 2, 3
+ARA_DBG_ADJOINT_PER_LAYER = 4
 
 
 def debug_set(key: int, value: int):

@@ -15,6 +15,7 @@
 // the only roundings are the final divisions by N and m and the products by f.
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "ara_internal.cuh"
@@ -22,6 +23,10 @@
 namespace ara {
 
 constexpr unsigned FULLM = 0xffffffffu;
+
+static std::atomic<int32_t> g_adjoint_per_layer{0};
+void set_adjoint_per_layer(int32_t on) { g_adjoint_per_layer.store(on); }
+int32_t adjoint_per_layer() { return g_adjoint_per_layer.load(); }
 constexpr int ADJ_MAX_SLOTS = 256;
 
 struct AdjCounts {          // per layer
@@ -360,6 +365,378 @@ __global__ void __launch_bounds__(256) k_adj_scatter(AdjScatterParams p) {
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Several layers in one pass over the YET.  Event-major rows list, for every catalogue event, the
+// selected layers (slots, ascending) whose occurrence regime for the event is not 0, and the
+// histograms are kept per row entry, so no count is made for an event of regime 0.  A trial is
+// read once if any slot has it in the aggregate interior, and each of its occurrences adds to
+// the entries of exactly those slots.  The counts equal those of the per-layer passes.
+// ------------------------------------------------------------------------------------------
+constexpr int ADJB_WARPS = 32;
+constexpr int ADJB_MAX_SEL = 255;   // slots fit in one byte
+
+// Row descriptor (first entry | length << 32) and the slot of every entry.  Entries at or beyond
+// cap are not written (cap bounds the allocation; a larger table is reported as a data error).
+__global__ void __launch_bounds__(256)
+k_adjb_fill(int32_t n_sel, const uint32_t* __restrict__ bits, int64_t bits_stride, int64_t C,
+            const uint32_t* __restrict__ ptr, uint32_t cap, uint8_t* __restrict__ ent,
+            uint64_t* __restrict__ rows, uint32_t* __restrict__ err) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= C) return;
+  uint32_t pos = ptr[e];
+  uint32_t end = ptr[e + 1];
+  if (end > cap) {
+    atomicOr(err, DERR_EVENT_RANGE);
+    end = cap;
+    pos = min(pos, cap);
+  }
+  rows[e] = (uint64_t)pos | ((uint64_t)(end - pos) << 32);
+  const uint32_t* b = bits + (e >> 5);
+  const int sh = (int)(e & 31);
+  for (int i = 0; i < n_sel && pos < end; ++i)
+    if ((__ldg(b + (int64_t)i * bits_stride) >> sh) & 1u) ent[pos++] = (uint8_t)i;
+}
+
+// Class of every (trial, slot), trial-major [n_trials][n_sel]: 0 outside the slot's aggregate
+// interior; 1 interior, below TVaR's threshold value v; 2 above v; 3 equal to v.  Also each
+// slot's trial counts by aggregate regime and position against v (AdjCounts.agg).
+__global__ void __launch_bounds__(256)
+k_adjb_class(int64_t n_trials, int32_t n_sel, const uint8_t* __restrict__ regimes,
+             const double* __restrict__ ylt, const uint64_t* __restrict__ thr_key,
+             int64_t thr_stride, uint8_t* __restrict__ cls, AdjCounts* __restrict__ acc) {
+  const int i = blockIdx.y;
+  const uint64_t thr = thr_key[(int64_t)i * thr_stride];
+  const uint8_t* rg_row = regimes + (int64_t)i * n_trials;
+  const double* y_row = ylt + (int64_t)i * n_trials;
+  unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_trials;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t rg = rg_row[t];
+    uint8_t c = 0;
+    if (rg != 0) {
+      const uint64_t key = adj_key(y_row[t]);
+      const bool above = key > thr, equal = key == thr;
+      const int o = rg == 1 ? 0 : 3;
+      v[o] += 1;
+      v[o + 1] += above ? 1 : 0;
+      v[o + 2] += equal ? 1 : 0;
+      if (rg == 1) c = above ? 2 : (equal ? 3 : 1);
+    }
+    cls[t * n_sel + i] = c;
+  }
+  block_add<6>(v, &acc[i].agg[0][0]);
+}
+
+struct AdjbHistParams {
+  int64_t n_trials;
+  const int64_t* offsets;
+  int64_t n_events;
+  const int32_t* ids;
+  int64_t catalogue;
+  int32_t n_sel;
+  uint32_t cap;               // entries allocated
+  const uint8_t* cls;         // [n_trials][n_sel]
+  const uint64_t* rows;       // [catalogue]
+  const uint8_t* ent;         // [cap]
+  uint32_t* h_mean;           // [cap] each
+  uint32_t* h_gt;
+  uint32_t* h_eq;
+  uint32_t* err;
+};
+
+// One warp per trial, dealt round-robin over the grid.  The trial's class row goes to the warp's
+// shared memory; a trial interior for no slot is skipped without reading its events.  Eight IDs
+// per lane are loaded at once, then their row descriptors, then the row entries are walked.
+__global__ void __launch_bounds__(ADJB_WARPS * 32) k_adjb_hist(AdjbHistParams p) {
+  __shared__ uint8_t cls_s[ADJB_WARPS][ADJB_MAX_SEL + 1];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  uint8_t* const cs = cls_s[wl];
+  const uint32_t cat = (uint32_t)p.catalogue;
+  bool bad_id = false, bad_off = false;
+  for (int64_t t = warp; t < p.n_trials; t += nwarps) {
+    unsigned any = 0;
+    for (int i = lane; i < p.n_sel; i += 32) {
+      const uint8_t c = p.cls[t * p.n_sel + i];
+      cs[i] = c;
+      any |= c;
+    }
+    __syncwarp();
+    if (!__any_sync(FULLM, any != 0)) continue;
+    const int64_t beg = __ldg(p.offsets + t), end = __ldg(p.offsets + t + 1);
+    if (!(0 <= beg && beg <= end && end <= p.n_events)) {
+      bad_off = true;
+      continue;
+    }
+    for (int64_t o = beg; o < end; o += 32 * 8) {
+      int ev[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j = o + 32 * u + lane;
+        ev[u] = j < end ? __ldcs(p.ids + j) : -1;
+      }
+      uint64_t rw[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j = o + 32 * u + lane;
+        const bool in = j < end, ok = (uint32_t)ev[u] < cat;
+        bad_id |= in && !ok;
+        rw[u] = (in && ok) ? __ldg(p.rows + (uint32_t)ev[u]) : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const uint32_t first = (uint32_t)rw[u], len = (uint32_t)(rw[u] >> 32);
+        for (uint32_t k = 0; k < len; ++k) {
+          const uint32_t x = first + k;
+          if (x >= p.cap) break;
+          const uint8_t c = cs[p.ent[x]];
+          if (c) {
+            atomicAdd(p.h_mean + x, 1u);
+            if (c == 2) atomicAdd(p.h_gt + x, 1u);
+            else if (c == 3) atomicAdd(p.h_eq + x, 1u);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (bad_id) atomicOr(p.err, DERR_EVENT_RANGE);
+  if (bad_off) atomicOr(p.err, DERR_OFFSETS);
+}
+
+// Sums over catalogue events of every slot's histograms, split by occurrence regime
+// (AdjCounts.occ of each slot), from the entry histograms.
+__global__ void __launch_bounds__(256)
+k_adjb_events(int64_t C, int32_t n_sel, uint32_t cap, const uint64_t* __restrict__ rows,
+              const uint8_t* __restrict__ ent, const uint8_t* __restrict__ reg_all,
+              const uint32_t* __restrict__ hm, const uint32_t* __restrict__ hg,
+              const uint32_t* __restrict__ he, AdjCounts* __restrict__ acc) {
+  extern __shared__ unsigned long long sacc[];   // [n_sel][6]
+  for (int i = threadIdx.x; i < 6 * n_sel; i += blockDim.x) sacc[i] = 0ull;
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < C;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t rw = rows[e];
+    const uint32_t first = (uint32_t)rw, len = (uint32_t)(rw >> 32);
+    for (uint32_t k = 0; k < len; ++k) {
+      const uint32_t x = first + k;
+      if (x >= cap) break;
+      const int sl = ent[x];
+      const uint8_t r = reg_all[(int64_t)sl * C + e];
+      const int o = sl * 6 + (r == 1 ? 0 : 3);
+      const uint32_t a = hm[x], b = hg[x], c = he[x];
+      if (a) atomicAdd(&sacc[o + 0], (unsigned long long)a);
+      if (b) atomicAdd(&sacc[o + 1], (unsigned long long)b);
+      if (c) atomicAdd(&sacc[o + 2], (unsigned long long)c);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 6 * n_sel; i += blockDim.x)
+    if (sacc[i]) atomicAdd(&acc[i / 6].occ[0][0] + (i % 6), sacc[i]);
+}
+
+// k_adj_records for slot `slot` of a multi-layer pass: an event's histogram values are those of
+// its row entry for the slot (present whenever the event's occurrence regime is not 0).
+struct AdjbRecParams {
+  AdjRecParams r;
+  const uint64_t* rows;
+  const uint8_t* ent;
+  const uint32_t* hm;
+  const uint32_t* hg;
+  const uint32_t* he;
+  uint32_t cap;
+  int32_t slot;
+};
+
+__global__ void __launch_bounds__(256) k_adjb_records(AdjbRecParams q) {
+  const AdjRecParams& p = q.r;
+  const int k = blockIdx.y;
+  const int j = p.elt[k];
+  const double R = p.elt_ret[j], L = p.elt_lim[j];
+  const double invN = 1.0 / (double)p.n_trials, invM = 1.0 / (double)p.m;
+  const unsigned long long cg = *p.sel_gt, ce = *p.sel_eq;
+  const double f = ce ? (double)(p.m - (int64_t)cg) / (double)ce : 0.0;
+  unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t r = p.rec_off[j] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < p.rec_off[j + 1];
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int e = p.rec_ids[r];
+    const double x = p.loss32 ? (double)p.loss32[r] : p.loss64[r];
+    const double ex = __dsub_rn(x, R);
+    const int rj = (ex > 0.0 && ex < L) ? 1 : (ex > L ? 2 : 0);
+    double gm = 0.0, gt = 0.0;
+    if (p.reg[e] == 1 && rj != 0) {
+      const uint64_t rw = q.rows[e];
+      const uint32_t first = (uint32_t)rw, len = (uint32_t)(rw >> 32);
+      uint32_t a = 0, b = 0, c = 0;
+      for (uint32_t t = 0; t < len; ++t) {
+        const uint32_t xi = first + t;
+        if (xi >= q.cap) break;
+        if (q.ent[xi] == q.slot) {
+          a = q.hm[xi];
+          b = q.hg[xi];
+          c = q.he[xi];
+          break;
+        }
+      }
+      const int o = (rj == 1) ? 0 : 3;
+      v[o + 0] += a;
+      v[o + 1] += b;
+      v[o + 2] += c;
+      if (rj == 1) {
+        gm = (double)a * invN;
+        gt = ((double)b + f * (double)c) * invM;
+      }
+    }
+    const int64_t pos = p.base[k] + p.rec_orig[r];
+    p.grad_loss_mean[pos] = gm;
+    p.grad_loss_tvar[pos] = gt;
+  }
+  block_add<6>(v, &p.slots[k].rl[0][0]);
+}
+
+// The adjoint of several layers with one histogram pass (the kernels above).  Returns ARA_ERANGE
+// without queueing anything when the layers' table would not fit 32-bit entry indices; the
+// caller then takes the per-layer path.
+static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, int64_t n_trials,
+                                const int64_t* d_offsets, int64_t n_events, const int32_t* d_ids,
+                                const double* d_ylt, const uint8_t* d_regimes, int64_t m,
+                                const SelectResult& sr, double* d_grad_elt, double* d_grad_layer,
+                                double* d_grad_loss, int64_t total_slots, int64_t total_loss,
+                                cudaStream_t s) {
+  const int32_t n_sel = (int32_t)sel.size();
+  const int64_t C = pf.catalogue, bmw = pf.bm_words;
+  int64_t bound = 0;   // every entry is an event of one of the slot's ELTs
+  for (int32_t l : sel)
+    for (int k = pf.layer_off[l]; k < pf.layer_off[l + 1]; ++k) {
+      const int j = pf.layer_elts[k];
+      bound += pf.rec_off[j + 1] - pf.rec_off[j];
+    }
+  if (bound >= (int64_t)UINT32_MAX || n_sel > ADJB_MAX_SEL) return ARA_ERANGE;
+  bound = std::max<int64_t>(bound, 1);
+  const int64_t n_blocks = (C + 1023) / 1024;
+  size_t off = 0;
+  auto take = [&](size_t n) { size_t o = (off + 255) / 256 * 256; off = o + n; return o; };
+  const size_t o_reg = take((size_t)n_sel * C), o_bits = take(4 * (size_t)n_sel * bmw);
+  const size_t o_ptr = take(4 * (size_t)(C + 1)), o_bsum = take(4 * (size_t)n_blocks), o_tot = take(4);
+  const size_t o_rows = take(8 * (size_t)C), o_ent = take((size_t)bound);
+  const size_t o_cls = take((size_t)n_trials * n_sel);
+  const size_t o_hm = take(4 * (size_t)bound), o_hg = take(4 * (size_t)bound), o_he = take(4 * (size_t)bound);
+  const size_t o_acc = take(sizeof(AdjCounts) * (size_t)n_sel);
+  const size_t o_slots = take(sizeof(SlotCounts) * (size_t)std::max<int64_t>(total_slots, 1));
+  char* scratch = nullptr;
+  ARA_TRY(dmalloc_async((void**)&scratch, off, s));
+  uint8_t* reg_all = (uint8_t*)(scratch + o_reg);
+  uint32_t* bits = (uint32_t*)(scratch + o_bits);
+  uint32_t* ptr = (uint32_t*)(scratch + o_ptr);
+  uint64_t* rows = (uint64_t*)(scratch + o_rows);
+  uint8_t* ent = (uint8_t*)(scratch + o_ent);
+  uint8_t* cls = (uint8_t*)(scratch + o_cls);
+  uint32_t* hm = (uint32_t*)(scratch + o_hm);
+  uint32_t* hg = (uint32_t*)(scratch + o_hg);
+  uint32_t* he = (uint32_t*)(scratch + o_he);
+  AdjCounts* acc = (AdjCounts*)(scratch + o_acc);
+  SlotCounts* slots = (SlotCounts*)(scratch + o_slots);
+  const uint32_t cap = (uint32_t)bound;
+  ara_status st = ARA_OK;
+  // 1. occurrence regimes of every catalogue event for every slot, and the bitmaps of regime != 0
+  FoldOutHost fo;
+  fo.bits = bits;
+  fo.regime = reg_all;
+  fo.bits_stride = bmw;
+  fo.regime_stride = C;
+  fo.by_slot = 1;
+  fo.bits_from_regime = 1;
+  st = launch_fold_to(pf, n_sel, sel.data(), fo, s);
+  if (st == ARA_OK && cudaMemsetAsync(scratch + o_hm, 0, off - o_hm, s) != cudaSuccess) st = ARA_ECUDA;
+  int n_rec_launches = 0;
+  for (int32_t l : sel) n_rec_launches += (pf.layer_off[l + 1] > pf.layer_off[l]) ? 1 : 0;
+  if (st == ARA_OK) {
+    LaunchScope ls(ARA_K_ADJOINT, s, 8 + n_rec_launches + n_sel);
+    // 2. event-major rows of the slots with a non-zero occurrence regime
+    st = launch_event_scan(bits, bmw, n_sel, C, ptr, (uint32_t*)(scratch + o_bsum),
+                           (uint32_t*)(scratch + o_tot), s);
+    if (st == ARA_OK) {
+      k_adjb_fill<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(n_sel, bits, bmw, C, ptr, cap, ent,
+                                                             rows, pf.d_err);
+      // 3. the class of every (trial, slot) and the trial counts
+      const unsigned cb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_trials + 255) / 256, 64));
+      k_adjb_class<<<dim3(cb, (unsigned)n_sel), 256, 0, s>>>(n_trials, n_sel, d_regimes, d_ylt,
+                                                             sr.thr_key, sr.thr_stride, cls, acc);
+      // 4. one pass over the trials interior for any slot
+      AdjbHistParams hp{};
+      hp.n_trials = n_trials;
+      hp.offsets = d_offsets;
+      hp.n_events = n_events;
+      hp.ids = d_ids ? d_ids : reinterpret_cast<const int32_t*>(d_offsets);
+      hp.catalogue = C;
+      hp.n_sel = n_sel;
+      hp.cap = cap;
+      hp.cls = cls;
+      hp.rows = rows;
+      hp.ent = ent;
+      hp.h_mean = hm;
+      hp.h_gt = hg;
+      hp.h_eq = he;
+      hp.err = pf.d_err;
+      k_adjb_hist<<<(unsigned)(pf.n_sms * 2), ADJB_WARPS * 32, 0, s>>>(hp);
+      // 5. per-slot sums of the histograms by occurrence regime
+      k_adjb_events<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((C + 255) / 256, 4 * pf.n_sms)),
+                      256, (size_t)6 * n_sel * sizeof(unsigned long long), s>>>(C, n_sel, cap, rows, ent,
+                                                                                 reg_all, hm, hg, he, acc);
+      // 6. per layer: record gradients and slot counts, then the final combination
+      int64_t elt_slot0 = 0, loss_base0 = 0;
+      for (int32_t i = 0; i < n_sel; ++i) {
+        const LayerConst& lc = pf.layers[sel[i]];
+        const int n_le = lc.elt_end - lc.elt_begin;
+        AdjbRecParams q{};
+        AdjRecParams& rp = q.r;
+        rp.rec_off = pf.d_rec_off;
+        rp.rec_ids = pf.d_rec_ids;
+        rp.loss32 = pf.d_rec_loss32;
+        rp.loss64 = pf.d_rec_loss;
+        rp.rec_orig = pf.d_rec_orig;
+        rp.elt_ret = pf.d_elt_ret;
+        rp.elt_lim = pf.d_elt_lim;
+        rp.reg = reg_all + (int64_t)i * C;
+        rp.sel_gt = sr.gt + i;
+        rp.sel_eq = sr.eq + i;
+        rp.n_trials = n_trials;
+        rp.m = m;
+        rp.grad_loss_mean = d_grad_loss;
+        rp.grad_loss_tvar = d_grad_loss + total_loss;
+        rp.slots = slots + elt_slot0;
+        rp.n_slots = n_le;
+        int64_t b = loss_base0;
+        for (int k = 0; k < n_le; ++k) {
+          const int j = pf.layer_elts[lc.elt_begin + k];
+          rp.elt[k] = j;
+          rp.base[k] = b;
+          b += pf.rec_off[j + 1] - pf.rec_off[j];
+        }
+        q.rows = rows;
+        q.ent = ent;
+        q.hm = hm;
+        q.hg = hg;
+        q.he = he;
+        q.cap = cap;
+        q.slot = i;
+        if (n_le > 0) k_adjb_records<<<dim3(16, n_le), 256, 0, s>>>(q);
+        k_adj_finish<<<1, 256, 0, s>>>(acc + i, slots + elt_slot0, n_le, sr.gt + i, sr.eq + i,
+                                       n_trials, m, d_grad_layer + (int64_t)i * 4,
+                                       d_grad_layer + (int64_t)(n_sel + i) * 4,
+                                       d_grad_elt + 2 * elt_slot0,
+                                       d_grad_elt + 2 * (total_slots + elt_slot0));
+        loss_base0 = b;
+        elt_slot0 += n_le;
+      }
+      if (cudaGetLastError() != cudaSuccess) st = ARA_ECUDA;
+    }
+  }
+  cudaFreeAsync(scratch, s);
+  return st;
+}
+
 }  // namespace ara
 
 using namespace ara;
@@ -399,6 +776,37 @@ extern "C" ara_status ara_adjoint(ara_portfolio* pf_, int64_t n_trials, const in
   ara_status st = select_one_rank(d_ylt, n_trials, n_sel, m, pf->n_sms, s, &sr, pf->d_err);
   if (st != ARA_OK) return st;
 
+  int64_t total_slots = 0, total_loss = 0;
+  for (int32_t i = 0; i < n_sel; ++i) {
+    const int l = sel[i];
+    for (int k = pf->layer_off[l]; k < pf->layer_off[l + 1]; ++k) {
+      const int j = pf->layer_elts[k];
+      total_loss += pf->rec_off[j + 1] - pf->rec_off[j];
+      ++total_slots;
+    }
+  }
+  // Several layers: one histogram pass for all of them (unless a test asks for the per-layer
+  // passes, or the layers' table exceeds 32-bit entry indices).
+  if (n_sel >= 2 && !adjoint_per_layer()) {
+    st = adjoint_multi(*pf, sel, n_trials, d_offsets, n_events, d_ids, d_ylt, d_regimes, m, sr,
+                       d_grad_elt, d_grad_layer, d_grad_loss, total_slots, total_loss, s);
+    if (st != ARA_ERANGE) {
+      std::vector<unsigned long long> gt(n_sel), eq(n_sel);
+      if (st == ARA_OK && h_ties) {
+        if (cudaMemcpyAsync(gt.data(), sr.gt, 8 * n_sel, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(eq.data(), sr.eq, 8 * n_sel, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+          st = ARA_ECUDA;
+      }
+      free_select_result(sr, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess && st == ARA_OK) st = ARA_ECUDA;
+      if (st == ARA_OK && h_ties)
+        for (int32_t i = 0; i < n_sel; ++i) h_ties[i] = (int64_t)(gt[i] + eq[i]) > m ? 1 : 0;
+      if (st != ARA_OK) return st;
+      return ara_check(pf_, stream);
+    }
+    st = ARA_OK;
+  }
+
   // scratch
   const int64_t C = pf->catalogue;
   const int64_t bmw = pf->bm_words;
@@ -433,15 +841,6 @@ extern "C" ara_status ara_adjoint(ara_portfolio* pf_, int64_t n_trials, const in
     out_st = ARA_ECUDA;
 
   int64_t elt_slot0 = 0, loss_base0 = 0;
-  int64_t total_slots = 0, total_loss = 0;
-  for (int32_t i = 0; i < n_sel; ++i) {
-    const int l = sel[i];
-    for (int k = pf->layer_off[l]; k < pf->layer_off[l + 1]; ++k) {
-      const int j = pf->layer_elts[k];
-      total_loss += pf->rec_off[j + 1] - pf->rec_off[j];
-      ++total_slots;
-    }
-  }
   for (int32_t i = 0; i < n_sel && out_st == ARA_OK; ++i) {
     const int l = sel[i];
     const LayerConst& lc = pf->layers[l];

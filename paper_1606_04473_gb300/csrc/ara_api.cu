@@ -277,6 +277,10 @@ ara_status ara_debug_set(int32_t key, int64_t value) {
       if (value != 0 && value != 1) return ARA_EINVAL;
       set_debug_skip_arrival((int32_t)value);
       return ARA_OK;
+    case ARA_DBG_ADJOINT_PER_LAYER:
+      if (value != 0 && value != 1) return ARA_EINVAL;
+      set_adjoint_per_layer((int32_t)value);
+      return ARA_OK;
     default:
       return ARA_EINVAL;
   }

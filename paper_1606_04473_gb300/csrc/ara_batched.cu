@@ -111,6 +111,20 @@ __global__ void k_bt_scan_add(uint32_t* __restrict__ ptr, int64_t n, const uint3
   if (e == n) ptr[n] = *total;
 }
 
+// Row pointers of an event-major table: ptr[e] = number of set bits of event e over all
+// n_sel bitmaps before e (exclusive scan), ptr[n] = total; block_sums holds ceil(n / 1024)
+// words of scratch, total one word.
+ara_status launch_event_scan(const uint32_t* bits, int64_t bits_stride, int32_t n_sel, int64_t n,
+                             uint32_t* ptr, uint32_t* block_sums, uint32_t* total, cudaStream_t s) {
+  const int64_t n_blocks = (n + BT_SCAN_BLOCK - 1) / BT_SCAN_BLOCK;
+  k_bt_scan_blocks<<<(unsigned)n_blocks, BT_SCAN_BLOCK, 0, s>>>(bits, bits_stride, n_sel, n, ptr,
+                                                              block_sums);
+  k_bt_scan_sums<<<1, BT_SCAN_BLOCK, 0, s>>>(block_sums, n_blocks, total);
+  k_bt_scan_add<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(ptr, n, block_sums, total);
+  ARA_TRY(cudaGetLastError());
+  return ARA_OK;
+}
+
 // ------------------------------------------------------------------------------------------
 // 3. CSR rows: one thread per event, layers in slot order (deterministic layout), and the
 //    event's row descriptor (first entry | length << 32)

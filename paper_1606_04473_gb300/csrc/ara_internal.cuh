@@ -206,6 +206,10 @@ struct GroupArgs {
   uint8_t* reg[BT_MAX_REQ] = {nullptr, nullptr, nullptr, nullptr};
 };
 ara_status run_batched_group_async(Portfolio& pf, const GroupArgs& g, cudaStream_t s);
+// Exclusive scan of the per-event count of set bits over n_sel bitmaps (the rows of an
+// event-major table): ptr [n + 1], block_sums [ceil(n / 1024)], total [1].
+ara_status launch_event_scan(const uint32_t* bits, int64_t bits_stride, int32_t n_sel, int64_t n,
+                             uint32_t* ptr, uint32_t* block_sums, uint32_t* total, cudaStream_t s);
 ara_status build_dense(Portfolio& pf, cudaStream_t s);
 // Compiled shapes (warps per block, ring stages) of the bulk-staged YET stream kernel.
 int32_t n_bulk_shapes();
@@ -218,6 +222,9 @@ uint64_t wait_limit_ns();
 // Test hook: the selection's blocks skip their grid-barrier arrivals (every wait runs out).
 void set_debug_skip_arrival(int32_t on);
 int32_t debug_skip_arrival();
+// Test hook: the adjoint of several layers takes one histogram pass per layer.
+void set_adjoint_per_layer(int32_t on);
+int32_t adjoint_per_layer();
 // Host check of risk-metric arguments (ranks within [1, n]); ARA_OK or ARA_EINVAL.
 ara_status validate_metrics(int64_t n, int32_t n_rp, const double* rps, int32_t n_tvar,
                             const double* levels);

@@ -285,3 +285,35 @@ def test_adjoint_coarse_regime_bitmap_at_the_adjoint_workload_catalogue():
         assert np.count_nonzero(ref["loss"]) > 1000 and np.all(ref["layer"][:, 0] != 0)
     assert gr["ties"].tolist() == [0, 0]
     g.close()
+
+
+@pytest.mark.parametrize("case_name", ["mid", "adjoint_workload"])
+def test_one_pass_for_all_layers_equals_per_layer_passes(mid, case_name):
+    """The adjoint of several layers takes one histogram pass over the YET for all of them
+    (event rows of the layers whose occurrence regime is non-zero, per-entry histograms); the
+    gradients equal those of one pass per layer (ARA_DBG_ADJOINT_PER_LAYER) bit for bit, for
+    both objectives, and the reported ties too."""
+    if case_name == "mid":
+        pf, yet = mid
+        sel = None
+    else:
+        pf = synth.adjoint_portfolio(0)
+        yet = synth.adjoint_yet(0, n_trials=3000)
+        sel = [0, 3, 7, 15]
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    n_sel = pf.n_layers if sel is None else len(sel)
+    reg = torch.empty((n_sel, yet.n_trials), dtype=torch.uint8, device="cuda")
+    y = g.run_ylt(off, ids, layers=sel, regimes=reg)
+    g.check()
+    one = g.adjoint(off, ids, y, reg, LEVEL, layers=sel)
+    ara.debug_set(ara.ARA_DBG_ADJOINT_PER_LAYER, 1)
+    try:
+        per = g.adjoint(off, ids, y, reg, LEVEL, layers=sel)
+    finally:
+        ara.debug_set(ara.ARA_DBG_ADJOINT_PER_LAYER, 0)
+    for k in ("elt", "layer", "loss"):
+        assert torch.equal(one[k], per[k]), k
+    assert one["ties"].tolist() == per["ties"].tolist()
+    assert torch.count_nonzero(one["loss"]).item() > 100
+    g.close()
