@@ -375,8 +375,11 @@ __global__ void __launch_bounds__(256) k_adj_scatter(AdjScatterParams p) {
 constexpr int ADJB_WARPS = 32;
 constexpr int ADJB_MAX_SEL = 255;   // slots fit in one byte
 
-// Row descriptor (first entry | length << 32) and the slot of every entry.  Entries at or beyond
-// cap are not written (cap bounds the allocation; a larger table is reported as a data error).
+// Row descriptor and the slot of every entry.  The descriptor holds the first entry (bits 0-31),
+// the length (bits 32-39) and the slots of the first three entries (bits 40-47, 48-55, 56-63),
+// so that most rows (1.4 entries on average on the adjoint workload) need no entry loads in the
+// histogram pass.  Entries at or beyond cap are not written (cap bounds the allocation; a larger
+// table is reported as a data error).
 __global__ void __launch_bounds__(256)
 k_adjb_fill(int32_t n_sel, const uint32_t* __restrict__ bits, int64_t bits_stride, int64_t C,
             const uint32_t* __restrict__ ptr, uint32_t cap, uint8_t* __restrict__ ent,
@@ -390,11 +393,17 @@ k_adjb_fill(int32_t n_sel, const uint32_t* __restrict__ bits, int64_t bits_strid
     end = cap;
     pos = min(pos, cap);
   }
-  rows[e] = (uint64_t)pos | ((uint64_t)(end - pos) << 32);
+  uint64_t desc = (uint64_t)pos | ((uint64_t)(end - pos) << 32);
   const uint32_t* b = bits + (e >> 5);
   const int sh = (int)(e & 31);
+  int k = 0;
   for (int i = 0; i < n_sel && pos < end; ++i)
-    if ((__ldg(b + (int64_t)i * bits_stride) >> sh) & 1u) ent[pos++] = (uint8_t)i;
+    if ((__ldg(b + (int64_t)i * bits_stride) >> sh) & 1u) {
+      ent[pos++] = (uint8_t)i;
+      if (k < 3) desc |= (uint64_t)i << (40 + 8 * k);
+      ++k;
+    }
+  rows[e] = desc;
 }
 
 // Class of every (trial, slot), trial-major [n_trials][n_sel]: 0 outside the slot's aggregate
@@ -486,11 +495,12 @@ __global__ void __launch_bounds__(ADJB_WARPS * 32) k_adjb_hist(AdjbHistParams p)
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const uint32_t first = (uint32_t)rw[u], len = (uint32_t)(rw[u] >> 32);
+        const uint32_t first = (uint32_t)rw[u], len = (uint32_t)(rw[u] >> 32) & 0xffu;
         for (uint32_t k = 0; k < len; ++k) {
           const uint32_t x = first + k;
           if (x >= p.cap) break;
-          const uint8_t c = cs[p.ent[x]];
+          const uint32_t sl = k < 3 ? (uint32_t)(rw[u] >> (40 + 8 * k)) & 0xffu : p.ent[x];
+          const uint8_t c = cs[sl];
           if (c) {
             atomicAdd(p.h_mean + x, 1u);
             if (c == 2) atomicAdd(p.h_gt + x, 1u);
@@ -518,7 +528,7 @@ k_adjb_events(int64_t C, int32_t n_sel, uint32_t cap, const uint64_t* __restrict
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < C;
        e += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t rw = rows[e];
-    const uint32_t first = (uint32_t)rw, len = (uint32_t)(rw >> 32);
+    const uint32_t first = (uint32_t)rw, len = (uint32_t)(rw >> 32) & 0xffu;
     for (uint32_t k = 0; k < len; ++k) {
       const uint32_t x = first + k;
       if (x >= cap) break;
@@ -536,26 +546,45 @@ k_adjb_events(int64_t C, int32_t n_sel, uint32_t cap, const uint64_t* __restrict
     if (sacc[i]) atomicAdd(&acc[i / 6].occ[0][0] + (i % 6), sacc[i]);
 }
 
-// k_adj_records for slot `slot` of a multi-layer pass: an event's histogram values are those of
-// its row entry for the slot (present whenever the event's occurrence regime is not 0).
+// k_adj_records for every ELT slot of every layer of a multi-layer pass, up to ADJ_MAX_SLOTS ELT
+// slots per launch (blockIdx.y): an event's histogram values are those of its row entry for the
+// layer (present whenever the event's occurrence regime is not 0).
 struct AdjbRecParams {
-  AdjRecParams r;
+  const int64_t* rec_off;
+  const int32_t* rec_ids;
+  const float* loss32;
+  const double* loss64;
+  const int32_t* rec_orig;
+  const double* elt_ret;
+  const double* elt_lim;
+  const uint8_t* reg_all;            // [n_sel][C]
+  int64_t C;
   const uint64_t* rows;
   const uint8_t* ent;
   const uint32_t* hm;
   const uint32_t* hg;
   const uint32_t* he;
   uint32_t cap;
-  int32_t slot;
+  const unsigned long long* sel_gt;  // [n_sel]
+  const unsigned long long* sel_eq;
+  int64_t n_trials, m;
+  double* grad_loss_mean;
+  double* grad_loss_tvar;
+  SlotCounts* slots;                 // all ELT slots, layers in selection order
+  int32_t slot0;                     // first ELT slot of this launch
+  int32_t elt[ADJ_MAX_SLOTS];
+  int64_t base[ADJ_MAX_SLOTS];
+  uint8_t layer[ADJ_MAX_SLOTS];      // selection index of the slot's layer
 };
 
-__global__ void __launch_bounds__(256) k_adjb_records(AdjbRecParams q) {
-  const AdjRecParams& p = q.r;
+__global__ void __launch_bounds__(256) k_adjb_records(AdjbRecParams p) {
   const int k = blockIdx.y;
   const int j = p.elt[k];
+  const int li = p.layer[k];
+  const uint8_t* reg = p.reg_all + (int64_t)li * p.C;
   const double R = p.elt_ret[j], L = p.elt_lim[j];
   const double invN = 1.0 / (double)p.n_trials, invM = 1.0 / (double)p.m;
-  const unsigned long long cg = *p.sel_gt, ce = *p.sel_eq;
+  const unsigned long long cg = p.sel_gt[li], ce = p.sel_eq[li];
   const double f = ce ? (double)(p.m - (int64_t)cg) / (double)ce : 0.0;
   unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t r = p.rec_off[j] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < p.rec_off[j + 1];
@@ -565,17 +594,17 @@ __global__ void __launch_bounds__(256) k_adjb_records(AdjbRecParams q) {
     const double ex = __dsub_rn(x, R);
     const int rj = (ex > 0.0 && ex < L) ? 1 : (ex > L ? 2 : 0);
     double gm = 0.0, gt = 0.0;
-    if (p.reg[e] == 1 && rj != 0) {
-      const uint64_t rw = q.rows[e];
-      const uint32_t first = (uint32_t)rw, len = (uint32_t)(rw >> 32);
+    if (reg[e] == 1 && rj != 0) {
+      const uint64_t rw = p.rows[e];
+      const uint32_t first = (uint32_t)rw, len = (uint32_t)(rw >> 32) & 0xffu;
       uint32_t a = 0, b = 0, c = 0;
       for (uint32_t t = 0; t < len; ++t) {
         const uint32_t xi = first + t;
-        if (xi >= q.cap) break;
-        if (q.ent[xi] == q.slot) {
-          a = q.hm[xi];
-          b = q.hg[xi];
-          c = q.he[xi];
+        if (xi >= p.cap) break;
+        if (p.ent[xi] == li) {
+          a = p.hm[xi];
+          b = p.hg[xi];
+          c = p.he[xi];
           break;
         }
       }
@@ -592,7 +621,51 @@ __global__ void __launch_bounds__(256) k_adjb_records(AdjbRecParams q) {
     p.grad_loss_mean[pos] = gm;
     p.grad_loss_tvar[pos] = gt;
   }
-  block_add<6>(v, &p.slots[k].rl[0][0]);
+  block_add<6>(v, &p.slots[p.slot0 + k].rl[0][0]);
+}
+
+// k_adj_finish for every layer of a multi-layer pass, one block per layer.
+struct AdjbFinishParams {
+  const AdjCounts* acc;              // [n_sel]
+  const SlotCounts* slots;           // all ELT slots
+  const unsigned long long* sel_gt;
+  const unsigned long long* sel_eq;
+  int64_t n, m, total_slots;
+  int32_t n_sel;
+  double* grad_layer;                // [2][n_sel][4]
+  double* grad_elt;                  // [2][total_slots][2]
+  int32_t slot_off[ADJB_MAX_SEL + 1];
+};
+
+__global__ void __launch_bounds__(256) k_adjb_finish(AdjbFinishParams p) {
+  const int i = blockIdx.x;
+  const double invN = 1.0 / (double)p.n, invM = 1.0 / (double)p.m;
+  const unsigned long long cg = p.sel_gt[i], ce = p.sel_eq[i];
+  const double f = ce ? (double)(p.m - (int64_t)cg) / (double)ce : 0.0;
+  auto mean_of = [&](const unsigned long long (&c)[3]) { return (double)c[0] * invN; };
+  auto tvar_of = [&](const unsigned long long (&c)[3]) {
+    return ((double)c[1] + f * (double)c[2]) * invM;
+  };
+  const AdjCounts& a = p.acc[i];
+  if (threadIdx.x == 0) {
+    double* gm = p.grad_layer + 4 * (int64_t)i;
+    double* gt = p.grad_layer + 4 * (int64_t)(p.n_sel + i);
+    gm[0] = -mean_of(a.occ[0]);
+    gm[1] = mean_of(a.occ[1]);
+    gm[2] = -mean_of(a.agg[0]);
+    gm[3] = mean_of(a.agg[1]);
+    gt[0] = -tvar_of(a.occ[0]);
+    gt[1] = tvar_of(a.occ[1]);
+    gt[2] = -tvar_of(a.agg[0]);
+    gt[3] = tvar_of(a.agg[1]);
+  }
+  for (int k = p.slot_off[i] + threadIdx.x; k < p.slot_off[i + 1]; k += blockDim.x) {
+    const SlotCounts& c = p.slots[k];
+    p.grad_elt[2 * k + 0] = -mean_of(c.rl[0]);
+    p.grad_elt[2 * k + 1] = mean_of(c.rl[1]);
+    p.grad_elt[2 * (p.total_slots + k) + 0] = -tvar_of(c.rl[0]);
+    p.grad_elt[2 * (p.total_slots + k) + 1] = tvar_of(c.rl[1]);
+  }
 }
 
 // The adjoint of several layers with one histogram pass (the kernels above).  Returns ARA_ERANGE
@@ -649,10 +722,9 @@ static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, 
   fo.bits_from_regime = 1;
   st = launch_fold_to(pf, n_sel, sel.data(), fo, s);
   if (st == ARA_OK && cudaMemsetAsync(scratch + o_hm, 0, off - o_hm, s) != cudaSuccess) st = ARA_ECUDA;
-  int n_rec_launches = 0;
-  for (int32_t l : sel) n_rec_launches += (pf.layer_off[l + 1] > pf.layer_off[l]) ? 1 : 0;
+  const int n_rec_launches = (int)((total_slots + ADJ_MAX_SLOTS - 1) / ADJ_MAX_SLOTS);
   if (st == ARA_OK) {
-    LaunchScope ls(ARA_K_ADJOINT, s, 8 + n_rec_launches + n_sel);
+    LaunchScope ls(ARA_K_ADJOINT, s, 7 + n_rec_launches);
     // 2. event-major rows of the slots with a non-zero occurrence regime
     st = launch_event_scan(bits, bmw, n_sel, C, ptr, (uint32_t*)(scratch + o_bsum),
                            (uint32_t*)(scratch + o_tot), s);
@@ -684,52 +756,69 @@ static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, 
       k_adjb_events<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((C + 255) / 256, 4 * pf.n_sms)),
                       256, (size_t)6 * n_sel * sizeof(unsigned long long), s>>>(C, n_sel, cap, rows, ent,
                                                                                  reg_all, hm, hg, he, acc);
-      // 6. per layer: record gradients and slot counts, then the final combination
-      int64_t elt_slot0 = 0, loss_base0 = 0;
+      // 6. record gradients and ELT-slot counts (up to ADJ_MAX_SLOTS slots per launch), then the
+      // final combination of every layer
+      AdjbRecParams q{};
+      q.rec_off = pf.d_rec_off;
+      q.rec_ids = pf.d_rec_ids;
+      q.loss32 = pf.d_rec_loss32;
+      q.loss64 = pf.d_rec_loss;
+      q.rec_orig = pf.d_rec_orig;
+      q.elt_ret = pf.d_elt_ret;
+      q.elt_lim = pf.d_elt_lim;
+      q.reg_all = reg_all;
+      q.C = C;
+      q.rows = rows;
+      q.ent = ent;
+      q.hm = hm;
+      q.hg = hg;
+      q.he = he;
+      q.cap = cap;
+      q.sel_gt = sr.gt;
+      q.sel_eq = sr.eq;
+      q.n_trials = n_trials;
+      q.m = m;
+      q.grad_loss_mean = d_grad_loss;
+      q.grad_loss_tvar = d_grad_loss + total_loss;
+      q.slots = slots;
+      AdjbFinishParams fp{};
+      fp.acc = acc;
+      fp.slots = slots;
+      fp.sel_gt = sr.gt;
+      fp.sel_eq = sr.eq;
+      fp.n = n_trials;
+      fp.m = m;
+      fp.total_slots = total_slots;
+      fp.n_sel = n_sel;
+      fp.grad_layer = d_grad_layer;
+      fp.grad_elt = d_grad_elt;
+      int32_t g = 0, in_launch = 0;
+      int64_t b = 0;
+      auto flush = [&]() {
+        if (in_launch > 0) k_adjb_records<<<dim3(16, (unsigned)in_launch), 256, 0, s>>>(q);
+        q.slot0 = g;
+        in_launch = 0;
+      };
+      q.slot0 = 0;
       for (int32_t i = 0; i < n_sel; ++i) {
         const LayerConst& lc = pf.layers[sel[i]];
-        const int n_le = lc.elt_end - lc.elt_begin;
-        AdjbRecParams q{};
-        AdjRecParams& rp = q.r;
-        rp.rec_off = pf.d_rec_off;
-        rp.rec_ids = pf.d_rec_ids;
-        rp.loss32 = pf.d_rec_loss32;
-        rp.loss64 = pf.d_rec_loss;
-        rp.rec_orig = pf.d_rec_orig;
-        rp.elt_ret = pf.d_elt_ret;
-        rp.elt_lim = pf.d_elt_lim;
-        rp.reg = reg_all + (int64_t)i * C;
-        rp.sel_gt = sr.gt + i;
-        rp.sel_eq = sr.eq + i;
-        rp.n_trials = n_trials;
-        rp.m = m;
-        rp.grad_loss_mean = d_grad_loss;
-        rp.grad_loss_tvar = d_grad_loss + total_loss;
-        rp.slots = slots + elt_slot0;
-        rp.n_slots = n_le;
-        int64_t b = loss_base0;
-        for (int k = 0; k < n_le; ++k) {
-          const int j = pf.layer_elts[lc.elt_begin + k];
-          rp.elt[k] = j;
-          rp.base[k] = b;
+        fp.slot_off[i] = g + in_launch;
+        for (int k = lc.elt_begin; k < lc.elt_end; ++k) {
+          const int j = pf.layer_elts[k];
+          q.elt[in_launch] = j;
+          q.base[in_launch] = b;
+          q.layer[in_launch] = (uint8_t)i;
           b += pf.rec_off[j + 1] - pf.rec_off[j];
+          if (++in_launch == ADJ_MAX_SLOTS) {
+            g += in_launch;
+            flush();
+          }
         }
-        q.rows = rows;
-        q.ent = ent;
-        q.hm = hm;
-        q.hg = hg;
-        q.he = he;
-        q.cap = cap;
-        q.slot = i;
-        if (n_le > 0) k_adjb_records<<<dim3(16, n_le), 256, 0, s>>>(q);
-        k_adj_finish<<<1, 256, 0, s>>>(acc + i, slots + elt_slot0, n_le, sr.gt + i, sr.eq + i,
-                                       n_trials, m, d_grad_layer + (int64_t)i * 4,
-                                       d_grad_layer + (int64_t)(n_sel + i) * 4,
-                                       d_grad_elt + 2 * elt_slot0,
-                                       d_grad_elt + 2 * (total_slots + elt_slot0));
-        loss_base0 = b;
-        elt_slot0 += n_le;
       }
+      fp.slot_off[n_sel] = g + in_launch;
+      g += in_launch;
+      flush();
+      k_adjb_finish<<<(unsigned)n_sel, 256, 0, s>>>(fp);
       if (cudaGetLastError() != cudaSuccess) st = ARA_ECUDA;
     }
   }
