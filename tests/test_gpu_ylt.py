@@ -86,6 +86,30 @@ def test_tiny_workload_matches_oracle(tiny, flags):
     assert_ylt_close(y.cpu().numpy(), ref, agg)
 
 
+@pytest.mark.parametrize("seed", range(5))
+def test_tiny_workload_seeds_ylt_and_metrics(seed):
+    """The tiny configuration (4 ELTs of 1,000 events over a 10,000-event catalogue, 1,000 trials
+    of Poisson(100) events, the literal absolute layer terms) at seeds 0-4.  The YLT is within the
+    stated tolerance of the oracle's; PML100, PML250 and TVaR99 are within 1e-6 of the oracle's
+    metrics of its own YLT; the PML is the exact order statistic of the GPU's YLT, TVaR within
+    1e-12 of the tail mean of that YLT, and the mean year loss within 1e-9 of the oracle's."""
+    pf, yet = synth.tiny(seed)
+    ref, agg = oracle.ylt(pf, yet, return_agg=True)
+    g = ara.Portfolio.from_tables(pf)
+    y = g.run_ylt(*dev(yet))
+    g.check()
+    y_np = y.cpu().numpy()
+    assert_ylt_close(y_np, ref, agg)
+    p, t, mean = ara.risk_metrics(y, [100.0, 250.0], [0.99], want_mean=True)
+    rp, rt = oracle.risk_metrics(ref, [100.0, 250.0], [0.99])
+    np.testing.assert_allclose(p, rp, rtol=1e-6, atol=0)
+    np.testing.assert_allclose(t, rt, rtol=1e-6, atol=0)
+    gp, gt = oracle.risk_metrics(y_np, [100.0, 250.0], [0.99])
+    assert np.array_equal(p, gp)
+    np.testing.assert_allclose(t, gt, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(mean, ref.mean(axis=1), rtol=1e-9, atol=0)
+
+
 def test_tiny_workload_per_elt_literal_path_equals_folded_bitwise(tiny):
     pf, yet, ref, agg = tiny
     g = ara.Portfolio.from_tables(pf, dense_tables=True)
