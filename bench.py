@@ -650,8 +650,28 @@ def measure_adjoint(rank: int, reps: int = 5):
     f_ms = timed(fwd)
     a_ms = timed(adj)
     g.check()
+    # the same adjoint over an event-major index of the YET (built once per YET)
+    g.yet_index(off, ids).close()                 # first build: one-time set-up costs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    yx = g.yet_index(off, ids)
+    torch.cuda.synchronize()
+    build_ms = (time.perf_counter() - t0) * 1e3
+
+    def adjx():
+        return g.adjoint(None, None, y, reg, 0.99, index=yx)
+
+    ax_ms = timed(adjx)
+    ra, rb = adj(), adjx()
+    same = all(torch.equal(ra[k], rb[k]) for k in ("elt", "layer", "loss"))
+    yx.close()
     out = {"workload": "16 layers x 15 ELTs (2M catalogue, 20k events each), 2e5 trials x 1000 events",
            "forward_ms": round(f_ms, 3), "adjoint_ms": round(a_ms, 3), "ratio": round(a_ms / f_ms, 3),
+           "indexed": {"adjoint_ms": round(ax_ms, 3), "ratio": round(ax_ms / f_ms, 3),
+                       "index_build_ms": round(build_ms, 3),
+                       "equal_to_trial_major": bool(same),
+                       "what": "ara_adjoint_indexed over an event-major index of the same YET "
+                               "(ara_yet_index_create, once per YET, not in adjoint_ms)"},
            "objectives": "mean year loss and TVaR99 per layer; gradients w.r.t. every retention, "
                          "limit and ELT loss",
            "check": check_adjoint(pf, yet, g, off, ids, y, reg)}

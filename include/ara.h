@@ -437,6 +437,45 @@ ARA_API ara_status ara_adjoint_accumulate(ara_portfolio* pf, int64_t n_trials,
                                           double* d_g_elt_lim, double* d_g_layer,
                                           double* d_g_loss, void* stream);
 
+/*
+ * Event-major index of a device YET, for adjoint passes over the same YET (Section IV-B's
+ * trial-major table, transposed).  The adjoint's histograms count, per catalogue event and
+ * layer, the occurrences of the event in trials whose aggregate loss is interior for the layer.
+ * Read trial by trial, every occurrence scatters into the histograms.  Read event by event, an
+ * event's counts stay in one thread.  The index depends on the YET alone (not on the layers or
+ * their terms): build it once, then use it for any number of ara_adjoint_indexed calls.
+ *   ara_yet_index_create  reads the YET (same arguments as ara_run_ylt) and builds the index
+ *                         on pf's device, for pf's catalogue size.  Synchronous.  Device memory:
+ *                         2 bytes per occurrence plus the padding of each group of 32 events
+ *                         to its longest list per block of trials (about 1.5x on uniform
+ *                         events), and 12 bytes per (block, group).  The index owns its
+ *                         memory; the YET may be freed or changed afterwards.
+ *                         Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA, ARA_EDATA (an event ID
+ *                         outside the catalogue, or offsets that decrease or leave
+ *                         [0, n_events]: no index is made).
+ *   ara_yet_index_destroy releases it (NULL is accepted).
+ */
+typedef struct ara_yet_index ara_yet_index;
+ARA_API ara_status ara_yet_index_create(ara_portfolio* pf, int64_t n_trials,
+                                        const int64_t* d_trial_offsets, int64_t n_events,
+                                        const int32_t* d_event_ids, void* stream,
+                                        ara_yet_index** out);
+ARA_API void ara_yet_index_destroy(ara_yet_index* yx);
+
+/*
+ * ara_adjoint over an indexed YET.  The arguments and results are those of ara_adjoint over
+ * the YET the index was built from, with the YET replaced by the index; results are bitwise
+ * equal.  pf must have the catalogue size the index was built for.  Synchronous.
+ * Errors as ara_adjoint; also ARA_EINVAL for a catalogue mismatch, and ARA_ERANGE when the
+ * selected layers' tables exceed 32-bit entry indices (ara_adjoint then takes one pass per
+ * layer; with an index, call ara_adjoint).
+ */
+ARA_API ara_status ara_adjoint_indexed(ara_portfolio* pf, const ara_yet_index* yx,
+                                       int32_t n_layer_sel, const int32_t* layer_sel,
+                                       const double* d_ylt, const uint8_t* d_regimes,
+                                       double tvar_level, double* d_grad_elt, double* d_grad_layer,
+                                       double* d_grad_loss, int32_t* h_ties, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * Risk metrics of Section IV-A (PML, TVaR), read as empirical order statistics of the YLT:
  *   PML(RP)  = the k-th largest year loss, k = ceil(N / RP)

@@ -124,6 +124,12 @@ def lib() -> ctypes.CDLL:
     L.ara_adjoint.restype = i32
     L.ara_adjoint_accumulate.argtypes = [P, i64, P, i64, P, i32, P, P, P, d, P, P, P, P, P, P]
     L.ara_adjoint_accumulate.restype = i32
+    L.ara_yet_index_create.argtypes = [P, i64, P, i64, P, P, ctypes.POINTER(P)]
+    L.ara_yet_index_create.restype = i32
+    L.ara_yet_index_destroy.argtypes = [P]
+    L.ara_yet_index_destroy.restype = None
+    L.ara_adjoint_indexed.argtypes = [P, P, i32, P, P, P, d, P, P, P, P, P]
+    L.ara_adjoint_indexed.restype = i32
     L.ara_timing_enable.argtypes = [i32]
     L.ara_timing_enable.restype = None
     L.ara_timing_reset.restype = None
@@ -311,30 +317,46 @@ class Portfolio:
         return out
 
     def adjoint(self, offsets, event_ids, ylt, regimes, tvar_level: float = 0.99, layers=None,
-                stream=None):
+                stream=None, index: "YetIndex" = None):
         """Gradients of each selected layer's mean year loss (objective 0) and TVaR (objective 1)
-        from a forward run's YLT and regimes (ara_adjoint).  Returns a dict of device tensors:
-        'elt' [2, K, 2] (d/dR, d/dL per ELT slot), 'layer' [2, n_sel, 4] (OccR, OccL, AggR, AggL),
-        'loss' [2, M] (per record of each slot, creation order), and 'ties' (numpy int32)."""
+        from a forward run's YLT and regimes (ara_adjoint; with `index`, a YetIndex of the same
+        YET, ara_adjoint_indexed, and offsets / event_ids may be None).  Returns a dict of device
+        tensors: 'elt' [2, K, 2] (d/dR, d/dL per ELT slot), 'layer' [2, n_sel, 4] (OccR, OccL,
+        AggR, AggL), 'loss' [2, M] (per record of each slot, creation order), and 'ties' (numpy
+        int32)."""
         import torch
-        n_trials = offsets.numel() - 1
         n_sel, sel_p, n_out, sel = self._sel(layers)
         lay = list(range(self.n_layers)) if sel is None else [int(x) for x in sel]
         K = sum(len(self.layer_elts[l]) for l in lay)
         M = sum(self.elt_nnz[j] for l in lay for j in self.layer_elts[l])
-        dev = offsets.device
+        dev = ylt.device
         ge = torch.zeros((2, max(K, 1), 2), dtype=torch.float64, device=dev)
         gl = torch.zeros((2, n_out, 4), dtype=torch.float64, device=dev)
         gx = torch.zeros((2, max(M, 1)), dtype=torch.float64, device=dev)
         ties = np.zeros(n_out, dtype=np.int32)
-        st = lib().ara_adjoint(self._h, n_trials, _dev_ptr(offsets, torch.int64, "offsets"),
-                               event_ids.numel(), _dev_ptr(event_ids, torch.int32, "event_ids"),
-                               n_sel, sel_p, _dev_ptr(ylt, torch.float64, "ylt"),
-                               _dev_ptr(regimes, torch.uint8, "regimes"), float(tvar_level),
-                               _dev_ptr(ge, torch.float64, "g"), _dev_ptr(gl, torch.float64, "g"),
-                               _dev_ptr(gx, torch.float64, "g"), _np_ptr(ties), _stream_handle(stream))
-        _check(st, "ara_adjoint")
+        if index is not None:
+            st = lib().ara_adjoint_indexed(self._h, index._handle(), n_sel, sel_p,
+                                           _dev_ptr(ylt, torch.float64, "ylt"),
+                                           _dev_ptr(regimes, torch.uint8, "regimes"), float(tvar_level),
+                                           _dev_ptr(ge, torch.float64, "g"), _dev_ptr(gl, torch.float64, "g"),
+                                           _dev_ptr(gx, torch.float64, "g"), _np_ptr(ties),
+                                           _stream_handle(stream))
+            _check(st, "ara_adjoint_indexed")
+        else:
+            n_trials = offsets.numel() - 1
+            st = lib().ara_adjoint(self._h, n_trials, _dev_ptr(offsets, torch.int64, "offsets"),
+                                   event_ids.numel(), _dev_ptr(event_ids, torch.int32, "event_ids"),
+                                   n_sel, sel_p, _dev_ptr(ylt, torch.float64, "ylt"),
+                                   _dev_ptr(regimes, torch.uint8, "regimes"), float(tvar_level),
+                                   _dev_ptr(ge, torch.float64, "g"), _dev_ptr(gl, torch.float64, "g"),
+                                   _dev_ptr(gx, torch.float64, "g"), _np_ptr(ties), _stream_handle(stream))
+            _check(st, "ara_adjoint")
         return {"elt": ge[:, :K], "layer": gl, "loss": gx[:, :M], "ties": ties}
+
+    def yet_index(self, offsets, event_ids, stream=None) -> "YetIndex":
+        """Event-major index of a device YET for this portfolio's catalogue
+        (ara_yet_index_create), for adjoint(..., index=...) calls over the same YET."""
+        return YetIndex(self, offsets, event_ids, stream)
 
     def adjoint_accumulate(self, offsets, event_ids, ylt, regimes, weights, tvar_level: float = 0.99,
                            layers=None, out=None, stream=None):
@@ -382,6 +404,38 @@ class Portfolio:
 
     def check(self, stream=None):
         _check(lib().ara_check(self._h, _stream_handle(stream)), "ara_check")
+
+
+class YetIndex:
+    """An event-major index of a device YET (ara_yet_index_create).  It owns its device memory;
+    the YET may change or go afterwards."""
+
+    def __init__(self, portfolio: Portfolio, offsets, event_ids, stream=None):
+        import torch
+        self.n_trials = offsets.numel() - 1
+        h = ctypes.c_void_p()
+        st = lib().ara_yet_index_create(portfolio._h, self.n_trials,
+                                        _dev_ptr(offsets, torch.int64, "offsets"), event_ids.numel(),
+                                        _dev_ptr(event_ids, torch.int32, "event_ids"),
+                                        _stream_handle(stream), ctypes.byref(h))
+        _check(st, "ara_yet_index_create")
+        self._h = h
+
+    def _handle(self):
+        if not getattr(self, "_h", None):
+            raise AraError(ARA_EINVAL, "YetIndex is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ara_yet_index_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BatchedPlan:

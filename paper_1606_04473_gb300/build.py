@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libara.so")
 SOURCES = ["ara_api.cu", "ara_ylt.cu", "ara_select.cu", "ara_adjoint.cu", "ara_batched.cu",
-           "ara_server.cu"]
+           "ara_server.cu", "ara_yet_index.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -515,6 +515,156 @@ __global__ void __launch_bounds__(ADJB_WARPS * 32) k_adjb_hist(AdjbHistParams p)
   if (bad_off) atomicOr(p.err, DERR_OFFSETS);
 }
 
+// The same histograms from an event-major index of the YET (YetIndex).  Per group of up to 16
+// selected layers (slots [q0, q0 + nq)), each trial's classes are packed into one word, 2 bits
+// per slot: bit 0 the aggregate interior (class != 0), bit 1 at or above TVaR's threshold value
+// (class 2 or 3).  A trial equal to the threshold value for some slot of the group (class 3, a
+// handful of trials) instead has its slot-0 field set to 0b10, which no class gives; its
+// occurrences take an exact path that reads the classes from the byte table.  One launch per
+// block of trials: every CTA holds the block's class words in shared memory (the padding offset
+// YX_PAD reads a zero word), and each warp takes one group of 32 catalogue events, lane l the
+// event 32 g + l, as the index interleaves them.  A lane finds its row entries whose slots lie
+// in the layer group (rows hold slots in ascending order, so they form one run), then walks the
+// event's list of the block, 8 entries per 16-byte load: for each occurrence it reads the
+// trial's class word and adds, per entry, the word's 2-bit field (interior + 2 x above) and its
+// bit 1 (2 x above) into two registers, from which the interior and above counts follow.  Up
+// to ADJX_K entries per walk; a lane with more walks the list again for the next ADJX_K.  At the
+// end it adds its counts into the entry histograms, which no other lane writes in this launch
+// (launches follow one another on the stream; the exact path's atomics are the same lane's).
+// The counts are the integers the trial-major pass counts.
+constexpr int ADJX_LAYERS = 16;    // slots per class word (2 bits each)
+constexpr int ADJX_K = 5;          // entries counted per walk of a list
+constexpr int ADJX_SMEM = (int)(YX_PAD + 1) * 4;
+
+__global__ void __launch_bounds__(256)
+k_adjx_words(int64_t n_trials, int32_t n_sel, int32_t q0, int32_t nq,
+             const uint8_t* __restrict__ cls, uint32_t* __restrict__ words) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_trials;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t* c = cls + t * n_sel + q0;
+    uint32_t w = 0;
+    bool eq = false;
+    for (int i = 0; i < nq; ++i) {
+      const uint32_t ci = c[i];
+      w |= (ci != 0u ? 1u : 0u) << (2 * i);
+      w |= (ci >= 2u ? 2u : 0u) << (2 * i);
+      eq = eq || ci == 3u;
+    }
+    words[t] = eq ? (w & ~3u) | 2u : w;
+  }
+}
+
+struct AdjxHistParams {
+  const uint16_t* ent16;      // the index's entries
+  const int64_t* base;        // [groups] of this block
+  const uint32_t* len;        // [groups] of this block
+  int64_t groups, catalogue;
+  int64_t t0, nb;             // first trial of the block, trials in it
+  const uint32_t* words;      // [n_trials] class words of slots [q0, q0 + nq)
+  const uint8_t* cls;         // [n_trials][n_sel] classes, for the flagged trials
+  int32_t n_sel, q0, nq;
+  const uint64_t* rows;       // [catalogue] row descriptors (k_adjb_fill)
+  const uint8_t* ent;         // [cap] slot of every row entry
+  uint32_t cap;
+  uint32_t* h_mean;
+  uint32_t* h_gt;
+  uint32_t* h_eq;
+};
+
+__device__ __forceinline__ uint32_t adjx_slot(uint64_t rw, uint32_t first, uint32_t j, uint32_t cap,
+                                              const uint8_t* __restrict__ ent) {
+  if (j < 3) return (uint32_t)(rw >> (40 + 8 * j)) & 0xffu;
+  const uint32_t x = first + j;
+  return x < cap ? (uint32_t)ent[x] : 0xffu;
+}
+
+__global__ void __launch_bounds__(1024, 1) k_adjx_hist(AdjxHistParams p) {
+  extern __shared__ uint32_t cw[];   // [YX_PAD + 1] class words of the block's trials
+  for (int64_t i = threadIdx.x; i <= (int64_t)YX_PAD; i += blockDim.x)
+    cw[i] = i < p.nb ? __ldg(p.words + p.t0 + i) : 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t qlo = (uint32_t)p.q0, qhi = (uint32_t)(p.q0 + p.nq);
+  for (int64_t g = gw; g < p.groups; g += nw) {
+    const uint32_t L = __ldg(p.len + g);
+    if (L == 0) continue;                                   // uniform over the warp
+    const int64_t e = g * 32 + lane;
+    const uint64_t rw = e < p.catalogue ? __ldg(p.rows + e) : 0ull;
+    const uint32_t first = (uint32_t)rw, rl = (uint32_t)(rw >> 32) & 0xffu;
+    uint32_t j0 = 0, j1 = 0;                                // entries with slot < qlo, < qhi
+    for (uint32_t j = 0; j < rl; ++j) {
+      const uint32_t sl = adjx_slot(rw, first, j, p.cap, p.ent);
+      if (first + j >= p.cap) break;
+      j0 += sl < qlo ? 1u : 0u;
+      j1 += sl < qhi ? 1u : 0u;
+    }
+    const int n_in = (int)(j1 - j0);
+    const int walks = __reduce_max_sync(0xffffffffu, (uint32_t)((n_in + ADJX_K - 1) / ADJX_K));
+    const uint4* lst = reinterpret_cast<const uint4*>(p.ent16 + __ldg(p.base + g)) + lane;
+    const uint32_t steps = L / 8;                            // 8 entries per lane and load
+    for (int c = 0; c < walks; ++c) {
+      const int jb = (int)j0 + c * ADJX_K;
+      const int have = min(ADJX_K, (int)j1 - jb);           // entries counted by this walk
+      const int hv = __reduce_max_sync(0xffffffffu, (uint32_t)max(have, 0));
+      uint32_t sh[ADJX_K], m3[ADJX_K], ca[ADJX_K], cb[ADJX_K];
+#pragma unroll
+      for (int k = 0; k < ADJX_K; ++k) {
+        sh[k] = k < have ? 2u * (adjx_slot(rw, first, (uint32_t)(jb + k), p.cap, p.ent) - qlo) : 0u;
+        m3[k] = k < have ? 3u : 0u;                         // nothing for unused entries
+        ca[k] = cb[k] = 0u;
+      }
+      auto count = [&](uint32_t off) {
+        off = min(off, YX_PAD);
+        const uint32_t w = cw[off];
+        if ((w & 3u) == 2u) {                               // a trial equal to the threshold
+          const uint8_t* c = p.cls + (p.t0 + off) * p.n_sel + p.q0;
+#pragma unroll
+          for (int k = 0; k < ADJX_K; ++k)
+            if (k < have) {
+              const uint32_t x = first + (uint32_t)(jb + k), cl = c[sh[k] >> 1];
+              if (x < p.cap && cl != 0u) {
+                atomicAdd(p.h_mean + x, 1u);
+                if (cl == 2u) atomicAdd(p.h_gt + x, 1u);
+                if (cl == 3u) atomicAdd(p.h_eq + x, 1u);
+              }
+            }
+          return;
+        }
+#pragma unroll
+        for (int k = 0; k < ADJX_K; ++k)
+          if (k < hv) {                                     // uniform over the warp
+            const uint32_t f = (w >> sh[k]) & m3[k];
+            ca[k] += f;                                     // interior + 2 x above
+            cb[k] += f & 2u;                                // 2 x above
+          }
+      };
+#pragma unroll 2
+      for (uint32_t i = 0; i < steps; ++i) {
+        const uint4 v = __ldcs(lst + (int64_t)i * 32);
+        count(v.x & 0xffffu);
+        count(v.x >> 16);
+        count(v.y & 0xffffu);
+        count(v.y >> 16);
+        count(v.z & 0xffffu);
+        count(v.z >> 16);
+        count(v.w & 0xffffu);
+        count(v.w >> 16);
+      }
+#pragma unroll
+      for (int k = 0; k < ADJX_K; ++k)
+        if (k < have) {
+          const uint32_t x = first + (uint32_t)(jb + k);
+          if (x < p.cap) {
+            p.h_mean[x] += ca[k] - cb[k];
+            p.h_gt[x] += cb[k] >> 1;
+          }
+        }
+    }
+  }
+}
+
 // Sums over catalogue events of every slot's histograms, split by occurrence regime
 // (AdjCounts.occ of each slot), from the entry histograms.
 __global__ void __launch_bounds__(256)
@@ -673,10 +823,10 @@ __global__ void __launch_bounds__(256) k_adjb_finish(AdjbFinishParams p) {
 // caller then takes the per-layer path.
 static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, int64_t n_trials,
                                 const int64_t* d_offsets, int64_t n_events, const int32_t* d_ids,
-                                const double* d_ylt, const uint8_t* d_regimes, int64_t m,
-                                const SelectResult& sr, double* d_grad_elt, double* d_grad_layer,
-                                double* d_grad_loss, int64_t total_slots, int64_t total_loss,
-                                cudaStream_t s) {
+                                const YetIndex* yx, const double* d_ylt, const uint8_t* d_regimes,
+                                int64_t m, const SelectResult& sr, double* d_grad_elt,
+                                double* d_grad_layer, double* d_grad_loss, int64_t total_slots,
+                                int64_t total_loss, cudaStream_t s) {
   const int32_t n_sel = (int32_t)sel.size();
   const int64_t C = pf.catalogue, bmw = pf.bm_words;
   int64_t bound = 0;   // every entry is an event of one of the slot's ELTs
@@ -697,6 +847,7 @@ static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, 
   const size_t o_hm = take(4 * (size_t)bound), o_hg = take(4 * (size_t)bound), o_he = take(4 * (size_t)bound);
   const size_t o_acc = take(sizeof(AdjCounts) * (size_t)n_sel);
   const size_t o_slots = take(sizeof(SlotCounts) * (size_t)std::max<int64_t>(total_slots, 1));
+  const size_t o_words = yx ? take(sizeof(uint32_t) * (size_t)n_trials) : 0;
   char* scratch = nullptr;
   ARA_TRY(dmalloc_async((void**)&scratch, off, s));
   uint8_t* reg_all = (uint8_t*)(scratch + o_reg);
@@ -723,8 +874,14 @@ static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, 
   st = launch_fold_to(pf, n_sel, sel.data(), fo, s);
   if (st == ARA_OK && cudaMemsetAsync(scratch + o_hm, 0, off - o_hm, s) != cudaSuccess) st = ARA_ECUDA;
   const int n_rec_launches = (int)((total_slots + ADJ_MAX_SLOTS - 1) / ADJ_MAX_SLOTS);
+  const int n_qgroups = (n_sel + ADJX_LAYERS - 1) / ADJX_LAYERS;
+  const int n_hist_launches = yx ? n_qgroups * (1 + yx->n_blocks) : 1;
+  if (st == ARA_OK && yx &&
+      cudaFuncSetAttribute((const void*)k_adjx_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           ADJX_SMEM) != cudaSuccess)
+    st = ARA_ECUDA;
   if (st == ARA_OK) {
-    LaunchScope ls(ARA_K_ADJOINT, s, 7 + n_rec_launches);
+    LaunchScope ls(ARA_K_ADJOINT, s, 6 + n_hist_launches + n_rec_launches);
     // 2. event-major rows of the slots with a non-zero occurrence regime
     st = launch_event_scan(bits, bmw, n_sel, C, ptr, (uint32_t*)(scratch + o_bsum),
                            (uint32_t*)(scratch + o_tot), s);
@@ -735,7 +892,38 @@ static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, 
       const unsigned cb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_trials + 255) / 256, 64));
       k_adjb_class<<<dim3(cb, (unsigned)n_sel), 256, 0, s>>>(n_trials, n_sel, d_regimes, d_ylt,
                                                              sr.thr_key, sr.thr_stride, cls, acc);
-      // 4. one pass over the trials interior for any slot
+      // 4. the histograms: one pass over the trials interior for any slot, or over the
+      // event-major index
+      if (yx) {
+        uint32_t* words = (uint32_t*)(scratch + o_words);
+        AdjxHistParams xp{};
+        xp.ent16 = yx->d_ent;
+        xp.groups = yx->groups;
+        xp.catalogue = C;
+        xp.words = words;
+        xp.cls = cls;
+        xp.n_sel = n_sel;
+        xp.rows = rows;
+        xp.ent = ent;
+        xp.cap = cap;
+        xp.h_mean = hm;
+        xp.h_gt = hg;
+        xp.h_eq = he;
+        for (int32_t q0 = 0; q0 < n_sel; q0 += ADJX_LAYERS) {
+          const int32_t nq = std::min(ADJX_LAYERS, n_sel - q0);
+          k_adjx_words<<<(unsigned)std::min<int64_t>((n_trials + 255) / 256, 8 * pf.n_sms), 256, 0, s>>>(
+              n_trials, n_sel, q0, nq, cls, words);
+          xp.q0 = q0;
+          xp.nq = nq;
+          for (int32_t h = 0; h < yx->n_blocks; ++h) {
+            xp.base = yx->d_base + (int64_t)h * yx->groups;
+            xp.len = yx->d_len + (int64_t)h * yx->groups;
+            xp.t0 = (int64_t)h * yx->block;
+            xp.nb = std::min<int64_t>(yx->block, n_trials - xp.t0);
+            k_adjx_hist<<<(unsigned)pf.n_sms, 1024, ADJX_SMEM, s>>>(xp);
+          }
+        }
+      }
       AdjbHistParams hp{};
       hp.n_trials = n_trials;
       hp.offsets = d_offsets;
@@ -751,7 +939,7 @@ static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, 
       hp.h_gt = hg;
       hp.h_eq = he;
       hp.err = pf.d_err;
-      k_adjb_hist<<<(unsigned)(pf.n_sms * 2), ADJB_WARPS * 32, 0, s>>>(hp);
+      if (!yx) k_adjb_hist<<<(unsigned)(pf.n_sms * 2), ADJB_WARPS * 32, 0, s>>>(hp);
       // 5. per-slot sums of the histograms by occurrence regime
       k_adjb_events<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((C + 255) / 256, 4 * pf.n_sms)),
                       256, (size_t)6 * n_sel * sizeof(unsigned long long), s>>>(C, n_sel, cap, rows, ent,
@@ -830,15 +1018,17 @@ static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, 
 
 using namespace ara;
 
-extern "C" ara_status ara_adjoint(ara_portfolio* pf_, int64_t n_trials, const int64_t* d_offsets,
-                                  int64_t n_events, const int32_t* d_ids, int32_t n_sel_in,
-                                  const int32_t* layer_sel, const double* d_ylt,
-                                  const uint8_t* d_regimes, double tvar_level, double* d_grad_elt,
-                                  double* d_grad_layer, double* d_grad_loss, int32_t* h_ties,
-                                  void* stream) {
+// ara_adjoint over the trial-major YET (yx null) or over its event-major index (yx set: the
+// YET pointers are unused).
+static ara_status adjoint_common(ara_portfolio* pf_, const YetIndex* yx, int64_t n_trials,
+                                 const int64_t* d_offsets, int64_t n_events, const int32_t* d_ids,
+                                 int32_t n_sel_in, const int32_t* layer_sel, const double* d_ylt,
+                                 const uint8_t* d_regimes, double tvar_level, double* d_grad_elt,
+                                 double* d_grad_layer, double* d_grad_loss, int32_t* h_ties,
+                                 void* stream) {
   Portfolio* pf = static_cast<Portfolio*>(pf_);
-  if (!pf || n_trials < 1 || n_events < 0 || !d_offsets || !d_ylt || !d_regimes) return ARA_EINVAL;
-  if (n_events > 0 && !d_ids) return ARA_EINVAL;
+  if (!pf || n_trials < 1 || n_events < 0 || !d_ylt || !d_regimes) return ARA_EINVAL;
+  if (!yx && (!d_offsets || (n_events > 0 && !d_ids))) return ARA_EINVAL;
   if (!d_grad_elt || !d_grad_layer || !d_grad_loss) return ARA_EINVAL;
   std::vector<int32_t> sel;
   if (n_sel_in == 0 && layer_sel == nullptr) {
@@ -875,11 +1065,12 @@ extern "C" ara_status ara_adjoint(ara_portfolio* pf_, int64_t n_trials, const in
     }
   }
   // Several layers: one histogram pass for all of them (unless a test asks for the per-layer
-  // passes, or the layers' table exceeds 32-bit entry indices).
-  if (n_sel >= 2 && !adjoint_per_layer()) {
-    st = adjoint_multi(*pf, sel, n_trials, d_offsets, n_events, d_ids, d_ylt, d_regimes, m, sr,
+  // passes, or the layers' table exceeds 32-bit entry indices).  With an index, always that
+  // path: the per-layer passes read the trial-major YET.
+  if (yx || (n_sel >= 2 && !adjoint_per_layer())) {
+    st = adjoint_multi(*pf, sel, n_trials, d_offsets, n_events, d_ids, yx, d_ylt, d_regimes, m, sr,
                        d_grad_elt, d_grad_layer, d_grad_loss, total_slots, total_loss, s);
-    if (st != ARA_ERANGE) {
+    if (st != ARA_ERANGE || yx) {
       std::vector<unsigned long long> gt(n_sel), eq(n_sel);
       if (st == ARA_OK && h_ties) {
         if (cudaMemcpyAsync(gt.data(), sr.gt, 8 * n_sel, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1025,6 +1216,30 @@ extern "C" ara_status ara_adjoint(ara_portfolio* pf_, int64_t n_trials, const in
     for (int32_t i = 0; i < n_sel; ++i) h_ties[i] = (int64_t)(gt[i] + eq[i]) > m ? 1 : 0;
   if (out_st != ARA_OK) return out_st;
   return ara_check(pf_, stream);
+}
+
+extern "C" ara_status ara_adjoint(ara_portfolio* pf, int64_t n_trials, const int64_t* d_offsets,
+                                  int64_t n_events, const int32_t* d_ids, int32_t n_sel_in,
+                                  const int32_t* layer_sel, const double* d_ylt,
+                                  const uint8_t* d_regimes, double tvar_level, double* d_grad_elt,
+                                  double* d_grad_layer, double* d_grad_loss, int32_t* h_ties,
+                                  void* stream) {
+  return adjoint_common(pf, nullptr, n_trials, d_offsets, n_events, d_ids, n_sel_in, layer_sel,
+                        d_ylt, d_regimes, tvar_level, d_grad_elt, d_grad_layer, d_grad_loss,
+                        h_ties, stream);
+}
+
+extern "C" ara_status ara_adjoint_indexed(ara_portfolio* pf, const ara_yet_index* yx,
+                                          int32_t n_sel_in, const int32_t* layer_sel,
+                                          const double* d_ylt, const uint8_t* d_regimes,
+                                          double tvar_level, double* d_grad_elt,
+                                          double* d_grad_layer, double* d_grad_loss,
+                                          int32_t* h_ties, void* stream) {
+  if (!pf || !yx) return ARA_EINVAL;
+  if (yx->catalogue != pf->catalogue || yx->device != pf->device || !yx->d_ent) return ARA_EINVAL;
+  return adjoint_common(pf, yx, yx->n_trials, nullptr, yx->n_events, nullptr, n_sel_in, layer_sel,
+                        d_ylt, d_regimes, tvar_level, d_grad_elt, d_grad_layer, d_grad_loss,
+                        h_ties, stream);
 }
 
 extern "C" ara_status ara_adjoint_accumulate(ara_portfolio* pf_, int64_t n_trials,

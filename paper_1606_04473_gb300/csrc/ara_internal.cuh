@@ -255,10 +255,34 @@ ara_status risk_metrics_device(const double* d_ylt, int64_t n, int32_t n_layers,
                                const double* rps, int32_t n_tvar, const double* levels,
                                double* h_pml, double* h_tvar, double* h_mean, cudaStream_t s);
 
+// Event-major index of a device YET (ara_yet_index_create).  The trials are cut into blocks of
+// `block` trials and the catalogue into groups of 32 events.  For block h and group g, the
+// trials of the block in which each event of the group occurs are stored as 16-bit offsets
+// within the block, in runs of 8 per event interleaved 32 wide (one 16-byte load per lane gives
+// 8 entries of its event): entry k of event 32 g + l sits at
+// ent[base[h][g] + 256 (k / 8) + 8 l + k % 8] for k < len[h][g], a multiple of 8; lists shorter
+// than len[h][g] are padded with YX_PAD, an offset past every block's last trial.  An event
+// occurring several times in a trial appears that many times.  Within a list the order is
+// unspecified.
+constexpr uint32_t YX_PAD = 0xC0C0u;           // the padding offset: bytes 0xC0 0xC0
+constexpr int64_t YX_MAX_BLOCK = YX_PAD;       // trials per block at most (offsets < YX_PAD)
+struct YetIndex {
+  int device = 0;
+  int64_t n_trials = 0, n_events = 0, catalogue = 0;
+  int64_t block = 0;                 // trials per block
+  int32_t n_blocks = 0;
+  int64_t groups = 0;                // ceil(catalogue / 32)
+  int64_t n_ent = 0;                 // entries, padding included
+  uint16_t* d_ent = nullptr;         // [n_ent]
+  int64_t* d_base = nullptr;         // [n_blocks][groups]
+  uint32_t* d_len = nullptr;         // [n_blocks][groups] list length, a multiple of 8
+};
+
 }  // namespace ara
 
 // The opaque handle of the C ABI is the portfolio itself.
 struct ara_portfolio : public ara::Portfolio {};
+struct ara_yet_index : public ara::YetIndex {};
 
 namespace ara {
 

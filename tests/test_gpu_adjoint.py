@@ -317,3 +317,131 @@ def test_one_pass_for_all_layers_equals_per_layer_passes(mid, case_name):
     assert one["ties"].tolist() == per["ties"].tolist()
     assert torch.count_nonzero(one["loss"]).item() > 100
     g.close()
+
+
+def _both_ways(g, off, ids, sel, level=LEVEL, index=None):
+    """(trial-major adjoint, adjoint over an event-major index of the same YET)."""
+    n_sel = g.n_layers if sel is None else len(sel)
+    reg = torch.empty((n_sel, off.numel() - 1), dtype=torch.uint8, device="cuda")
+    y = g.run_ylt(off, ids, layers=sel, regimes=reg)
+    g.check()
+    a = g.adjoint(off, ids, y, reg, level, layers=sel)
+    yx = index if index is not None else g.yet_index(off, ids)
+    b = g.adjoint(None, None, y, reg, level, layers=sel, index=yx)
+    g.check()
+    return a, b
+
+
+def _assert_same(a, b):
+    for k in ("elt", "layer", "loss"):
+        assert torch.equal(a[k], b[k]), k
+    assert a["ties"].tolist() == b["ties"].tolist()
+
+
+@pytest.mark.parametrize("case_name", ["mid_all", "mid_one_layer", "adjoint_workload", "tie"])
+def test_indexed_adjoint_equals_trial_major(mid, case_name):
+    """ara_adjoint_indexed reads the YET through its event-major index: each event's list of
+    trials, with the trials' classes packed 2 bits per layer.  It counts the same integers as
+    the trial-major pass, so every gradient of both objectives and the reported ties are equal
+    bit for bit (and the trial-major pass is checked against the FP64 oracle above)."""
+    sel = None
+    if case_name.startswith("mid"):
+        pf, yet = mid
+        sel = [1] if case_name == "mid_one_layer" else None
+    elif case_name == "adjoint_workload":
+        pf = synth.adjoint_portfolio(0)
+        yet = synth.adjoint_yet(0, n_trials=3000)
+        sel = [0, 3, 7, 15]
+    else:
+        pf, yet = case(22, n_layers=2, n_trials=2000)
+        pf = pf.with_terms({**pf.terms_dict(), "agg_lim": list(np.asarray(pf.agg_lim) * 0.3)})
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    a, b = _both_ways(g, off, ids, sel)
+    _assert_same(a, b)
+    assert torch.count_nonzero(a["loss"]).item() > 100
+    if case_name == "tie":
+        assert a["ties"].tolist() == [1, 1]
+    g.close()
+
+
+def test_indexed_adjoint_several_trial_blocks_many_layers_long_rows():
+    """110,000 trials (three blocks of the index: offsets within a block are 16-bit), 20 layers
+    (two groups of 16 layers per class word) that all include ELT 0, so that events of ELT 0 sit
+    in the rows of most layers: rows longer than the 5 entries a walk counts, which walk their
+    lists several times.  Equal bit for bit to the trial-major pass."""
+    seed = 31
+    C, n_elts, n_layers = 50_000, 6, 20
+    ids_e, losses = synth.make_elts(seed, n_elts, 5000, C, 11.0, 2.0, f32=True)
+    r, l = synth.percentile_terms(losses)
+    rng = np.random.default_rng(seed)
+    layers = [sorted({0, *rng.choice(np.arange(1, n_elts), size=2, replace=False).tolist()})
+              for _ in range(n_layers)]
+    counts = synth.poisson_counts(seed, 20.0, 110_000)
+    counts[:2] = [0, 1]
+    yet = synth.make_yet(seed, counts, C, with_timestamps=False)
+    z = np.zeros(n_layers)
+    pf = synth.Portfolio(C, ids_e, losses, r, l, layers, z, z, z, z, losses_f32=True)
+    from oracle.derive_terms import derive
+    pf = pf.with_terms(derive(pf, synth.YET(yet.offsets[:2001], yet.event_ids[:int(yet.offsets[2000])]),
+                              20.0, 80.0))
+    rows = sum((_occurrence_regimes(pf, k) != 0).astype(np.int32) for k in range(n_layers))
+    assert rows.max() >= 13          # three walks in the first group of 16 layers
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    yx = g.yet_index(off, ids)
+    a, b = _both_ways(g, off, ids, None, index=yx)
+    _assert_same(a, b)
+    assert torch.count_nonzero(a["loss"]).item() > 1000
+    # one index serves any layers of the same catalogue: a subset, then changed terms
+    a, b = _both_ways(g, off, ids, [19, 2, 7], index=yx)
+    _assert_same(a, b)
+    g2 = ara.Portfolio.from_tables(pf.with_terms({**pf.terms_dict(),
+                                                  "occ_ret": list(np.asarray(pf.occ_ret) * 1.5)}))
+    a, b = _both_ways(g2, off, ids, None, index=yx)
+    _assert_same(a, b)
+    yx.close()
+    g.close()
+    g2.close()
+
+
+def test_yet_index_owns_its_memory_and_reports_bad_input(mid):
+    """The index keeps no reference to the YET (the YET's buffers may go); an event ID outside
+    the catalogue or decreasing offsets give ARA_EDATA and no index; a portfolio of another
+    catalogue size is refused; a closed index is refused."""
+    pf, yet = mid
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    reg = torch.empty((g.n_layers, yet.n_trials), dtype=torch.uint8, device="cuda")
+    y = g.run_ylt(off, ids, regimes=reg)
+    a = g.adjoint(off, ids, y, reg, LEVEL)
+    off2, ids2 = off.clone(), ids.clone()
+    yx = g.yet_index(off2, ids2)
+    del off2, ids2
+    torch.cuda.synchronize()
+    junk = torch.full((ids.numel(),), 7, dtype=torch.int32, device="cuda")   # reuse the memory
+    b = g.adjoint(None, None, y, reg, LEVEL, index=yx)
+    _assert_same(a, b)
+    del junk
+    bad = ids.clone()
+    bad[5] = pf.catalogue
+    with pytest.raises(ara.AraError) as ei:
+        g.yet_index(off, bad)
+    assert ei.value.status == ara.ARA_EDATA
+    off_bad = off.clone()
+    off_bad[10] = off_bad[12] + 1
+    with pytest.raises(ara.AraError) as ei:
+        g.yet_index(off_bad, ids)
+    assert ei.value.status == ara.ARA_EDATA
+    other = synth.Portfolio(pf.catalogue + 1, pf.elt_ids, pf.elt_losses, pf.elt_ret, pf.elt_lim,
+                            pf.layer_elts, pf.occ_ret, pf.occ_lim, pf.agg_ret, pf.agg_lim,
+                            losses_f32=True)
+    g3 = ara.Portfolio.from_tables(other)
+    with pytest.raises(ara.AraError) as ei:
+        g3.adjoint(None, None, y, reg, LEVEL, index=yx)
+    assert ei.value.status == ara.ARA_EINVAL
+    yx.close()
+    with pytest.raises(ara.AraError):
+        g.adjoint(None, None, y, reg, LEVEL, index=yx)
+    g3.close()
+    g.close()
