@@ -143,3 +143,16 @@ def test_timing_classes_of_the_host_pipeline_are_readable(L):
     for k in (ara.ARA_K_TRANSFER, ara.ARA_K_HOST_CHECK):
         assert L.ara_timing_read(k, ctypes.byref(ms), ctypes.byref(n)) == ara.ARA_OK
     assert L.ara_timing_read(7, ctypes.byref(ms), ctypes.byref(n)) == ara.ARA_EINVAL
+
+
+def test_yet_index_entry_points_reject_bad_arguments_on_host(L):
+    """The event-major YET index and the adjoint over it refuse missing handles and outputs
+    before touching a device, leave the output handle null, and accept destroying null."""
+    p = ctypes.c_void_p(256)          # never dereferenced: the argument checks fail first
+    out = ctypes.c_void_p(1234)
+    assert L.ara_yet_index_create(None, 10, p, 100, p, None, ctypes.byref(out)) == ara.ARA_EINVAL
+    assert out.value is None
+    assert L.ara_yet_index_create(p, 10, p, 100, p, None, None) == ara.ARA_EINVAL
+    L.ara_yet_index_destroy(None)
+    assert L.ara_adjoint_indexed(None, p, 0, None, p, p, 0.99, p, p, p, None, None) == ara.ARA_EINVAL
+    assert L.ara_adjoint_indexed(p, None, 0, None, p, p, 0.99, p, p, p, None, None) == ara.ARA_EINVAL
