@@ -445,3 +445,17 @@ def test_yet_index_owns_its_memory_and_reports_bad_input(mid):
         g.adjoint(None, None, y, reg, LEVEL, index=yx)
     g3.close()
     g.close()
+
+
+def test_indexed_adjoint_of_a_yet_without_occurrences(mid):
+    """Every trial empty: the index holds no entries, and the indexed adjoint equals the
+    trial-major one (no occurrence counts; only the aggregate terms' trial counts)."""
+    pf, _ = mid
+    n = 700
+    g = ara.Portfolio.from_tables(pf)
+    off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    ids = torch.zeros(1, dtype=torch.int32, device="cuda")[:0]
+    a, b = _both_ways(g, off, ids, None)
+    _assert_same(a, b)
+    assert torch.count_nonzero(a["loss"]).item() == 0
+    g.close()
