@@ -816,7 +816,9 @@ def measure_serving(rank: int, n_requests: int = 200, workers: int = 1, saturati
     per second, well above what any mode serves, so every makespan is set by the server and not
     by the last arrival), and compared with the same queries run one at a time (one worker, no
     merging; the batched path for requests of 4 or more layers, as in the served mode) and with
-    sequential plain runs (one at a time, every layer by the single-layer path).  Latencies are
+    sequential plain runs (one at a time, every layer by the single-layer path).  The server's
+    adjoint requests read an event-major index of the resident YET, built when each server is set
+    up, in every arm but the sequential plain runs and one served arm without it.  Latencies are
     then taken at 2x and 0.5x of the served mode's measured capacity.  Results must be identical
     in every mode."""
     import threading
@@ -843,8 +845,15 @@ def measure_serving(rank: int, n_requests: int = 200, workers: int = 1, saturati
                     want_adjoint=q["want_adjoint"], adjoint_level=0.99,
                     flags=ara.ARA_RUN_BATCHED if batched else 0, tenant=q["tenant"])
 
-    def serve(max_concurrent, merge, plain=False, stretch=1.0):
+    index_ms = []
+
+    def serve(max_concurrent, merge, plain=False, stretch=1.0, index=True):
         srv = ara.Server(pool, off, ev, max_concurrent=max_concurrent, max_merge=merge)
+        if index:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            srv.set_adjoint_index(True)
+            index_ms.append((time.perf_counter() - t0) * 1e3)
         srv.wait(srv.submit(**dict(query_args(trace[0], plain), trials=(0, 1000))))
         c0 = srv.counters()
         tickets = [None] * len(trace)
@@ -872,17 +881,19 @@ def measure_serving(rank: int, n_requests: int = 200, workers: int = 1, saturati
                "requests_per_s": len(trace) / makespan, "peak_running": stats["peak_running"],
                "passes": cnt["passes"] - c0["passes"],
                "merged_requests": cnt["merged_requests"] - c0["merged_requests"],
-               "head_passed": cnt["head_passed"] - c0["head_passed"]}
+               "head_passed": cnt["head_passed"] - c0["head_passed"],
+               "indexed_adjoints": cnt["indexed_adjoints"] - c0["indexed_adjoints"]}
         return res, arm
 
     sat = base_rate / saturating_rate
     res_s, served = serve(workers, 4, stretch=sat)
     res_2, served_2 = serve(2, 4, stretch=sat)
     res_1, one = serve(1, 1, stretch=sat)
-    res_p, plain = serve(1, 1, plain=True, stretch=sat)
+    res_p, plain = serve(1, 1, plain=True, stretch=sat, index=False)
+    res_n, served_noidx = serve(workers, 4, stretch=sat, index=False)
     capacity = served["requests_per_s"]
     loads = {}
-    others = [res_s, res_2, res_p]
+    others = [res_s, res_2, res_p, res_n]
     for name, factor in (("2x_capacity", 2.0), ("0.5x_capacity", 0.5)):
         rate = factor * capacity
         r_s, a_s = serve(workers, 4, stretch=base_rate / rate)
@@ -898,7 +909,13 @@ def measure_serving(rank: int, n_requests: int = 200, workers: int = 1, saturati
            "offered_load_saturating": f"{saturating_rate:g} requests/s (above every mode's capacity: "
                                       "makespans are set by the server)",
            "served": served, "served_2_workers": served_2, "one_at_a_time": one,
-           "sequential_plain": plain,
+           "sequential_plain": plain, "served_without_yet_index": served_noidx,
+           "yet_index": {"build_ms": round(float(np.median(index_ms)), 2) if index_ms else None,
+                         "what": "event-major index of the resident YET, built when the server "
+                                 "is set up (ara_server_set_adjoint_index); adjoint requests "
+                                 "whose slice covers at least half of the index blocks it "
+                                 "touches read it. Every arm but sequential_plain and "
+                                 "served_without_yet_index uses it"},
            "capacity_requests_per_s": {"served": round(capacity, 1),
                                        "one_at_a_time": round(one["requests_per_s"], 1),
                                        "sequential_plain": round(plain["requests_per_s"], 1)},

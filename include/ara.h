@@ -374,9 +374,21 @@ ARA_API ara_status ara_server_stats(ara_server* server, int32_t* queued_or_runni
 ARA_API ara_status ara_server_set_merging(ara_server* server, int32_t max_requests_per_pass,
                                           double min_overlap);
 /* Passes run so far (a pass serves one request or a merged group), requests that ran in a merged
- * group of two or more, and the times a blocked oldest request was passed by a later one. */
+ * group of two or more, the times a blocked oldest request was passed by a later one, and the
+ * adjoints computed over the server's YET index.  Each pointer may be NULL. */
 ARA_API ara_status ara_server_counters(ara_server* server, int64_t* passes,
-                                       int64_t* merged_requests, int64_t* head_passed);
+                                       int64_t* merged_requests, int64_t* head_passed,
+                                       int64_t* indexed_adjoints);
+/*
+ * Build (on != 0) or release (on == 0) an event-major index of the server's resident YET
+ * (ara_yet_index_create) for the adjoint requests.  While it exists, a request's adjoint reads
+ * the index instead of the YET when its trial slice covers at least half of the index blocks it
+ * touches (the indexed pass reads those blocks whole); results are bitwise the same either way.
+ * The index's device memory (about 3 bytes per occurrence) is held until released or the server
+ * is destroyed; admission sees it as memory in use.  Only while the server is idle: ARA_EBUSY
+ * when a request is queued or running.  Synchronous.  Errors as ara_yet_index_create.
+ */
+ARA_API ara_status ara_server_set_adjoint_index(ara_server* server, int32_t on);
 /* Finish every queued request, then stop the workers and release the server. */
 ARA_API void ara_server_destroy(ara_server* server);
 
@@ -463,14 +475,19 @@ ARA_API ara_status ara_yet_index_create(ara_portfolio* pf, int64_t n_trials,
 ARA_API void ara_yet_index_destroy(ara_yet_index* yx);
 
 /*
- * ara_adjoint over an indexed YET.  The arguments and results are those of ara_adjoint over
- * the YET the index was built from, with the YET replaced by the index; results are bitwise
- * equal.  pf must have the catalogue size the index was built for.  Synchronous.
- * Errors as ara_adjoint; also ARA_EINVAL for a catalogue mismatch, and ARA_ERANGE when the
- * selected layers' tables exceed 32-bit entry indices (ara_adjoint then takes one pass per
- * layer; with an index, call ara_adjoint).
+ * ara_adjoint over an indexed YET, for its trials [first_trial, first_trial + n_trials)
+ * (0 and 0: all of them).  The arguments and results are those of ara_adjoint over those
+ * trials of the YET the index was built from (d_ylt, d_regimes: [n_layer_sel][n_trials] of
+ * them), with the YET replaced by the index; results are bitwise equal.  The pass reads the
+ * index blocks the trials touch whole, so a slice much shorter than a block (49,344 trials at
+ * most) costs about as much as the block.  pf must have the catalogue size the index was built
+ * for.  Synchronous.
+ * Errors as ara_adjoint; also ARA_EINVAL for a catalogue mismatch or trials outside the index,
+ * and ARA_ERANGE when the selected layers' tables exceed 32-bit entry indices (ara_adjoint then
+ * takes one pass per layer; with an index, call ara_adjoint).
  */
 ARA_API ara_status ara_adjoint_indexed(ara_portfolio* pf, const ara_yet_index* yx,
+                                       int64_t first_trial, int64_t n_trials,
                                        int32_t n_layer_sel, const int32_t* layer_sel,
                                        const double* d_ylt, const uint8_t* d_regimes,
                                        double tvar_level, double* d_grad_elt, double* d_grad_layer,

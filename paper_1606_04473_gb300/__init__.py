@@ -116,7 +116,10 @@ def lib() -> ctypes.CDLL:
     L.ara_server_estimate_bytes.restype = i32
     L.ara_server_set_merging.argtypes = [P, i32, d]
     L.ara_server_set_merging.restype = i32
-    L.ara_server_counters.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.ara_server_counters.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i64)]
+    L.ara_server_set_adjoint_index.argtypes = [P, i32]
+    L.ara_server_set_adjoint_index.restype = i32
     L.ara_server_counters.restype = i32
     L.ara_server_destroy.argtypes = [P]
     L.ara_server_destroy.restype = None
@@ -128,7 +131,7 @@ def lib() -> ctypes.CDLL:
     L.ara_yet_index_create.restype = i32
     L.ara_yet_index_destroy.argtypes = [P]
     L.ara_yet_index_destroy.restype = None
-    L.ara_adjoint_indexed.argtypes = [P, P, i32, P, P, P, d, P, P, P, P, P]
+    L.ara_adjoint_indexed.argtypes = [P, P, i64, i64, i32, P, P, P, d, P, P, P, P, P]
     L.ara_adjoint_indexed.restype = i32
     L.ara_timing_enable.argtypes = [i32]
     L.ara_timing_enable.restype = None
@@ -317,10 +320,11 @@ class Portfolio:
         return out
 
     def adjoint(self, offsets, event_ids, ylt, regimes, tvar_level: float = 0.99, layers=None,
-                stream=None, index: "YetIndex" = None):
+                stream=None, index: "YetIndex" = None, first_trial: int = 0):
         """Gradients of each selected layer's mean year loss (objective 0) and TVaR (objective 1)
-        from a forward run's YLT and regimes (ara_adjoint; with `index`, a YetIndex of the same
-        YET, ara_adjoint_indexed, and offsets / event_ids may be None).  Returns a dict of device
+        from a forward run's YLT and regimes (ara_adjoint; with `index`, a YetIndex of a YET whose
+        trials [first_trial, first_trial + ylt columns) the forward ran over,
+        ara_adjoint_indexed, and offsets / event_ids may be None).  Returns a dict of device
         tensors: 'elt' [2, K, 2] (d/dR, d/dL per ELT slot), 'layer' [2, n_sel, 4] (OccR, OccL,
         AggR, AggL), 'loss' [2, M] (per record of each slot, creation order), and 'ties' (numpy
         int32)."""
@@ -335,7 +339,8 @@ class Portfolio:
         gx = torch.zeros((2, max(M, 1)), dtype=torch.float64, device=dev)
         ties = np.zeros(n_out, dtype=np.int32)
         if index is not None:
-            st = lib().ara_adjoint_indexed(self._h, index._handle(), n_sel, sel_p,
+            st = lib().ara_adjoint_indexed(self._h, index._handle(), int(first_trial),
+                                           int(ylt.shape[-1]), n_sel, sel_p,
                                            _dev_ptr(ylt, torch.float64, "ylt"),
                                            _dev_ptr(regimes, torch.uint8, "regimes"), float(tvar_level),
                                            _dev_ptr(ge, torch.float64, "g"), _dev_ptr(gl, torch.float64, "g"),
@@ -525,10 +530,16 @@ class Server:
                "ara_server_set_merging")
 
     def counters(self):
-        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-        _check(lib().ara_server_counters(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
-               "ara_server_counters")
-        return {"passes": a.value, "merged_requests": b.value, "head_passed": c.value}
+        a, b, c, x = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ara_server_counters(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                         ctypes.byref(x)), "ara_server_counters")
+        return {"passes": a.value, "merged_requests": b.value, "head_passed": c.value,
+                "indexed_adjoints": x.value}
+
+    def set_adjoint_index(self, on: bool = True):
+        """Build (or release) an event-major index of the resident YET for adjoint requests
+        (ara_server_set_adjoint_index; only while the server is idle)."""
+        _check(lib().ara_server_set_adjoint_index(self._h, 1 if on else 0), "ara_server_set_adjoint_index")
 
     @staticmethod
     def _query(layer_elts, occ_ret, occ_lim, agg_ret, agg_lim, trials, return_periods=(),

@@ -559,7 +559,9 @@ struct AdjxHistParams {
   const int64_t* base;        // [groups] of this block
   const uint32_t* len;        // [groups] of this block
   int64_t groups, catalogue;
-  int64_t t0, nb;             // first trial of the block, trials in it
+  int64_t t0, nb;             // the block's first trial as an index into words (< 0 when the
+                              // adjoint's trials start inside the block), trials in the block
+  int64_t n_words;            // the adjoint's trials (words and cls rows)
   const uint32_t* words;      // [n_trials] class words of slots [q0, q0 + nq)
   const uint8_t* cls;         // [n_trials][n_sel] classes, for the flagged trials
   int32_t n_sel, q0, nq;
@@ -581,7 +583,7 @@ __device__ __forceinline__ uint32_t adjx_slot(uint64_t rw, uint32_t first, uint3
 __global__ void __launch_bounds__(1024, 1) k_adjx_hist(AdjxHistParams p) {
   extern __shared__ uint32_t cw[];   // [YX_PAD + 1] class words of the block's trials
   for (int64_t i = threadIdx.x; i <= (int64_t)YX_PAD; i += blockDim.x)
-    cw[i] = i < p.nb ? __ldg(p.words + p.t0 + i) : 0u;
+    cw[i] = (i < p.nb && p.t0 + i >= 0 && p.t0 + i < p.n_words) ? __ldg(p.words + p.t0 + i) : 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -823,7 +825,8 @@ __global__ void __launch_bounds__(256) k_adjb_finish(AdjbFinishParams p) {
 // caller then takes the per-layer path.
 static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, int64_t n_trials,
                                 const int64_t* d_offsets, int64_t n_events, const int32_t* d_ids,
-                                const YetIndex* yx, const double* d_ylt, const uint8_t* d_regimes,
+                                const YetIndex* yx, int64_t first_trial, const double* d_ylt,
+                                const uint8_t* d_regimes,
                                 int64_t m, const SelectResult& sr, double* d_grad_elt,
                                 double* d_grad_layer, double* d_grad_loss, int64_t total_slots,
                                 int64_t total_loss, cudaStream_t s) {
@@ -875,7 +878,9 @@ static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, 
   if (st == ARA_OK && cudaMemsetAsync(scratch + o_hm, 0, off - o_hm, s) != cudaSuccess) st = ARA_ECUDA;
   const int n_rec_launches = (int)((total_slots + ADJ_MAX_SLOTS - 1) / ADJ_MAX_SLOTS);
   const int n_qgroups = (n_sel + ADJX_LAYERS - 1) / ADJX_LAYERS;
-  const int n_hist_launches = yx ? n_qgroups * (1 + yx->n_blocks) : 1;
+  const int64_t n_blocks_used =
+      yx ? (first_trial + n_trials - 1) / yx->block - first_trial / yx->block + 1 : 0;
+  const int n_hist_launches = yx ? n_qgroups * (int)(1 + n_blocks_used) : 1;
   if (st == ARA_OK && yx &&
       cudaFuncSetAttribute((const void*)k_adjx_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            ADJX_SMEM) != cudaSuccess)
@@ -915,11 +920,13 @@ static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, 
               n_trials, n_sel, q0, nq, cls, words);
           xp.q0 = q0;
           xp.nq = nq;
-          for (int32_t h = 0; h < yx->n_blocks; ++h) {
+          const int64_t h_lo = first_trial / yx->block, h_hi = (first_trial + n_trials - 1) / yx->block;
+          for (int64_t h = h_lo; h <= h_hi; ++h) {
             xp.base = yx->d_base + (int64_t)h * yx->groups;
             xp.len = yx->d_len + (int64_t)h * yx->groups;
-            xp.t0 = (int64_t)h * yx->block;
-            xp.nb = std::min<int64_t>(yx->block, n_trials - xp.t0);
+            xp.t0 = h * yx->block - first_trial;
+            xp.nb = std::min<int64_t>(yx->block, yx->n_trials - h * yx->block);
+            xp.n_words = n_trials;
             k_adjx_hist<<<(unsigned)pf.n_sms, 1024, ADJX_SMEM, s>>>(xp);
           }
         }
@@ -1019,9 +1026,10 @@ static ara_status adjoint_multi(Portfolio& pf, const std::vector<int32_t>& sel, 
 using namespace ara;
 
 // ara_adjoint over the trial-major YET (yx null) or over its event-major index (yx set: the
-// YET pointers are unused).
-static ara_status adjoint_common(ara_portfolio* pf_, const YetIndex* yx, int64_t n_trials,
-                                 const int64_t* d_offsets, int64_t n_events, const int32_t* d_ids,
+// trials [first_trial, first_trial + n_trials) of the indexed YET; the YET pointers are unused).
+static ara_status adjoint_common(ara_portfolio* pf_, const YetIndex* yx, int64_t first_trial,
+                                 int64_t n_trials, const int64_t* d_offsets, int64_t n_events,
+                                 const int32_t* d_ids,
                                  int32_t n_sel_in, const int32_t* layer_sel, const double* d_ylt,
                                  const uint8_t* d_regimes, double tvar_level, double* d_grad_elt,
                                  double* d_grad_layer, double* d_grad_loss, int32_t* h_ties,
@@ -1068,7 +1076,7 @@ static ara_status adjoint_common(ara_portfolio* pf_, const YetIndex* yx, int64_t
   // passes, or the layers' table exceeds 32-bit entry indices).  With an index, always that
   // path: the per-layer passes read the trial-major YET.
   if (yx || (n_sel >= 2 && !adjoint_per_layer())) {
-    st = adjoint_multi(*pf, sel, n_trials, d_offsets, n_events, d_ids, yx, d_ylt, d_regimes, m, sr,
+    st = adjoint_multi(*pf, sel, n_trials, d_offsets, n_events, d_ids, yx, first_trial, d_ylt, d_regimes, m, sr,
                        d_grad_elt, d_grad_layer, d_grad_loss, total_slots, total_loss, s);
     if (st != ARA_ERANGE || yx) {
       std::vector<unsigned long long> gt(n_sel), eq(n_sel);
@@ -1224,12 +1232,13 @@ extern "C" ara_status ara_adjoint(ara_portfolio* pf, int64_t n_trials, const int
                                   const uint8_t* d_regimes, double tvar_level, double* d_grad_elt,
                                   double* d_grad_layer, double* d_grad_loss, int32_t* h_ties,
                                   void* stream) {
-  return adjoint_common(pf, nullptr, n_trials, d_offsets, n_events, d_ids, n_sel_in, layer_sel,
+  return adjoint_common(pf, nullptr, 0, n_trials, d_offsets, n_events, d_ids, n_sel_in, layer_sel,
                         d_ylt, d_regimes, tvar_level, d_grad_elt, d_grad_layer, d_grad_loss,
                         h_ties, stream);
 }
 
 extern "C" ara_status ara_adjoint_indexed(ara_portfolio* pf, const ara_yet_index* yx,
+                                          int64_t first_trial, int64_t n_trials,
                                           int32_t n_sel_in, const int32_t* layer_sel,
                                           const double* d_ylt, const uint8_t* d_regimes,
                                           double tvar_level, double* d_grad_elt,
@@ -1237,7 +1246,9 @@ extern "C" ara_status ara_adjoint_indexed(ara_portfolio* pf, const ara_yet_index
                                           int32_t* h_ties, void* stream) {
   if (!pf || !yx) return ARA_EINVAL;
   if (yx->catalogue != pf->catalogue || yx->device != pf->device || !yx->d_ent) return ARA_EINVAL;
-  return adjoint_common(pf, yx, yx->n_trials, nullptr, yx->n_events, nullptr, n_sel_in, layer_sel,
+  if (n_trials == 0 && first_trial == 0) n_trials = yx->n_trials;
+  if (first_trial < 0 || n_trials < 1 || first_trial > yx->n_trials - n_trials) return ARA_EINVAL;
+  return adjoint_common(pf, yx, first_trial, n_trials, nullptr, yx->n_events, nullptr, n_sel_in, layer_sel,
                         d_ylt, d_regimes, tvar_level, d_grad_elt, d_grad_layer, d_grad_loss,
                         h_ties, stream);
 }

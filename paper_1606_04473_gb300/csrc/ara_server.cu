@@ -69,6 +69,11 @@ struct ara_server {
   // record of every layer's ELTs (an upper bound of the table's entries).
   int64_t max_table_bytes = 192ll << 20;
   int64_t n_passes = 0, n_merged = 0, n_head_passed = 0;
+  // Event-major index of the resident YET (ara_server_set_adjoint_index), or null: adjoint
+  // requests whose slice covers at least half of the index blocks it touches read it instead of
+  // the YET (the indexed pass reads those blocks whole).
+  ara_yet_index* yx = nullptr;
+  int64_t n_indexed = 0;
   // The YET passes (batched or single-layer streams, adjoint histograms) of different workers
   // run one after the other on the device: each waits for the previous one's completion event.
   // Concurrent passes each hold a large table in L2 and slow each other down; everything else
@@ -144,10 +149,23 @@ ara_status finish_request(ara_server& S, Request& r, ara_portfolio* ls, int32_t 
         dmalloc_async((void**)&gx, 8 * (size_t)std::max<int64_t>(2 * M, 1), s) != cudaSuccess) {
       st = ARA_ENOMEM;
     } else {
+      bool indexed = false;
+      if (S.yx) {
+        const int64_t B = S.yx->block;
+        const int64_t span = ((r.t1 - 1) / B - r.t0 / B + 1) * B;
+        indexed = 2 * n >= span;
+      }
       st = chained_pass(S, s, [&] {
+        if (indexed)
+          return ara_adjoint_indexed(ls, S.yx, r.t0, n, nl, sel.data(), ylt, reg, r.adjoint_level,
+                                     ge, gl, gx, nullptr, s);
         return ara_adjoint(ls, n, S.d_off + r.t0, S.n_events, S.d_ids, nl, sel.data(), ylt, reg,
                            r.adjoint_level, ge, gl, gx, nullptr, s);
       });
+      if (indexed) {
+        std::lock_guard<std::mutex> lk(S.mu);
+        ++S.n_indexed;
+      }
       if (st == ARA_OK) {
         r.grad_layer.assign((size_t)8 * nl, 0.0);
         if (cudaMemcpyAsync(r.grad_layer.data(), gl, 8 * (size_t)(8 * nl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -580,13 +598,34 @@ ara_status ara_server_set_merging(ara_server* S, int32_t max_requests_per_pass, 
   return ARA_OK;
 }
 
+ara_status ara_server_set_adjoint_index(ara_server* S, int32_t on) {
+  if (!S) return ARA_EINVAL;
+  // Held throughout: no worker can take a request (nor read S->yx) while the index changes.
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (!S->pending.empty() || S->running > 0) return ARA_EBUSY;
+  DeviceGuard g(S->pool->device);
+  if (!on) {
+    ara_yet_index_destroy(S->yx);
+    S->yx = nullptr;
+    return ARA_OK;
+  }
+  if (S->yx) return ARA_OK;
+  ara_yet_index* yx = nullptr;
+  const ara_status st = ara_yet_index_create(static_cast<ara_portfolio*>(S->pool), S->n_trials,
+                                             S->d_off, S->n_events, S->d_ids, nullptr, &yx);
+  if (st != ARA_OK) return st;
+  S->yx = yx;
+  return ARA_OK;
+}
+
 ara_status ara_server_counters(ara_server* S, int64_t* passes, int64_t* merged_requests,
-                               int64_t* head_passed) {
+                               int64_t* head_passed, int64_t* indexed_adjoints) {
   if (!S) return ARA_EINVAL;
   std::lock_guard<std::mutex> lk(S->mu);
   if (passes) *passes = S->n_passes;
   if (merged_requests) *merged_requests = S->n_merged;
   if (head_passed) *head_passed = S->n_head_passed;
+  if (indexed_adjoints) *indexed_adjoints = S->n_indexed;
   return ARA_OK;
 }
 
@@ -602,6 +641,7 @@ void ara_server_destroy(ara_server* S) {
     DeviceGuard g(S->pool->device);
     if (S->pass_done) cudaEventDestroy(S->pass_done);
   }
+  ara_yet_index_destroy(S->yx);
   delete S;
 }
 

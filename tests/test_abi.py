@@ -131,7 +131,9 @@ def test_new_entry_points_reject_null_handles_on_host(L):
     b = ctypes.c_int64()
     assert L.ara_server_estimate_bytes(None, None, ctypes.byref(b)) == ara.ARA_EINVAL
     n = ctypes.c_int64()
-    assert L.ara_server_counters(None, ctypes.byref(n), ctypes.byref(n), ctypes.byref(n)) == ara.ARA_EINVAL
+    assert L.ara_server_counters(None, ctypes.byref(n), ctypes.byref(n), ctypes.byref(n),
+                                 ctypes.byref(n)) == ara.ARA_EINVAL
+    assert L.ara_server_set_adjoint_index(None, 1) == ara.ARA_EINVAL
     assert L.ara_plan_table(None, None, ctypes.byref(n)) == ara.ARA_EINVAL
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
@@ -154,5 +156,5 @@ def test_yet_index_entry_points_reject_bad_arguments_on_host(L):
     assert out.value is None
     assert L.ara_yet_index_create(p, 10, p, 100, p, None, None) == ara.ARA_EINVAL
     L.ara_yet_index_destroy(None)
-    assert L.ara_adjoint_indexed(None, p, 0, None, p, p, 0.99, p, p, p, None, None) == ara.ARA_EINVAL
-    assert L.ara_adjoint_indexed(p, None, 0, None, p, p, 0.99, p, p, p, None, None) == ara.ARA_EINVAL
+    assert L.ara_adjoint_indexed(None, p, 0, 0, 0, None, p, p, 0.99, p, p, p, None, None) == ara.ARA_EINVAL
+    assert L.ara_adjoint_indexed(p, None, 0, 0, 0, None, p, p, 0.99, p, p, p, None, None) == ara.ARA_EINVAL

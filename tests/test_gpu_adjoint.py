@@ -365,11 +365,9 @@ def test_indexed_adjoint_equals_trial_major(mid, case_name):
     g.close()
 
 
-def test_indexed_adjoint_several_trial_blocks_many_layers_long_rows():
-    """110,000 trials (three blocks of the index: offsets within a block are 16-bit), 20 layers
-    (two groups of 16 layers per class word) that all include ELT 0, so that events of ELT 0 sit
-    in the rows of most layers: rows longer than the 5 entries a walk counts, which walk their
-    lists several times.  Equal bit for bit to the trial-major pass."""
+def _blocks_case():
+    """110,000 trials of Poisson(20) events over a 50,000-event catalogue (three blocks of the
+    index), 20 layers (two groups of 16 per class word) that all include ELT 0."""
     seed = 31
     C, n_elts, n_layers = 50_000, 6, 20
     ids_e, losses = synth.make_elts(seed, n_elts, 5000, C, 11.0, 2.0, f32=True)
@@ -385,6 +383,16 @@ def test_indexed_adjoint_several_trial_blocks_many_layers_long_rows():
     from oracle.derive_terms import derive
     pf = pf.with_terms(derive(pf, synth.YET(yet.offsets[:2001], yet.event_ids[:int(yet.offsets[2000])]),
                               20.0, 80.0))
+    return pf, yet
+
+
+def test_indexed_adjoint_several_trial_blocks_many_layers_long_rows():
+    """110,000 trials (three blocks of the index: offsets within a block are 16-bit), 20 layers
+    (two groups of 16 layers per class word) that all include ELT 0, so that events of ELT 0 sit
+    in the rows of most layers: rows longer than the 5 entries a walk counts, which walk their
+    lists several times.  Equal bit for bit to the trial-major pass."""
+    pf, yet = _blocks_case()
+    n_layers = pf.n_layers
     rows = sum((_occurrence_regimes(pf, k) != 0).astype(np.int32) for k in range(n_layers))
     assert rows.max() >= 13          # three walks in the first group of 16 layers
     g = ara.Portfolio.from_tables(pf)
@@ -458,4 +466,29 @@ def test_indexed_adjoint_of_a_yet_without_occurrences(mid):
     a, b = _both_ways(g, off, ids, None)
     _assert_same(a, b)
     assert torch.count_nonzero(a["loss"]).item() == 0
+    g.close()
+
+
+def test_indexed_adjoint_over_trial_slices():
+    """The adjoint of a forward run over a slice of the indexed YET's trials: inside one block,
+    across a block boundary, the last trials, and one trial.  The pass reads the blocks the slice
+    touches and counts only the slice's trials; equal bit for bit to the trial-major adjoint of
+    the same slice."""
+    pf, yet = _blocks_case()
+    g = ara.Portfolio.from_tables(pf)
+    off, ids = dev(yet)
+    yx = g.yet_index(off, ids)
+    sel = [0, 4, 17]
+    for t0, t1 in [(1_000, 9_000), (30_000, 80_000), (100_000, 110_000), (36_667, 36_668)]:
+        o = off[t0:t1 + 1]
+        reg = torch.empty((len(sel), t1 - t0), dtype=torch.uint8, device="cuda")
+        y = g.run_ylt(o, ids, layers=sel, regimes=reg)
+        g.check()
+        a = g.adjoint(o, ids, y, reg, LEVEL, layers=sel)
+        b = g.adjoint(None, None, y, reg, LEVEL, layers=sel, index=yx, first_trial=t0)
+        g.check()
+        _assert_same(a, b)
+    with pytest.raises(ara.AraError):      # trials past the end of the index
+        g.adjoint(None, None, y, reg, LEVEL, layers=sel, index=yx, first_trial=110_000)
+    yx.close()
     g.close()

@@ -214,3 +214,37 @@ def test_blocked_request_is_passed_by_smaller_ones_a_bounded_number_of_times(wor
         for k in ("pml", "tvar", "mean", "grad_layer"):
             assert (a[k] is None and m[k] is None) or np.array_equal(a[k], m[k]), k
     alone.close()
+
+
+def test_server_adjoints_over_the_yet_index_are_identical(world):
+    """With the server's index of its resident YET, adjoint requests whose slice covers at least
+    half of the index blocks it touches read the index; every result equals the same request on
+    a server without the index, bit for bit.  The index can change only while the server is
+    idle."""
+    pool_tables, yet, pool, off, ev = world
+    rng = np.random.default_rng(23)
+    qs = random_queries(12, 29, yet.n_trials)
+    for k, q in enumerate(qs):
+        q["want_adjoint"] = True
+        if k % 3:                                     # long slices read the index
+            t0 = int(rng.integers(0, 1000))
+            q["trials"] = (t0, int(rng.integers(4000, yet.n_trials + 1)))
+    plain = ara.Server(pool, off, ev, max_concurrent=1, max_merge=4)
+    want = [plain.wait(t) for t in [plain.submit(**q) for q in qs]]
+    assert plain.counters()["indexed_adjoints"] == 0
+    plain.close()
+    srv = ara.Server(pool, off, ev, max_concurrent=1, max_merge=4)
+    srv.set_adjoint_index(True)
+    got = [srv.wait(t) for t in [srv.submit(**q) for q in qs]]
+    cnt = srv.counters()
+    assert 0 < cnt["indexed_adjoints"] < len(qs)
+    for a, b in zip(want, got):
+        for k in ("pml", "tvar", "mean", "grad_layer"):
+            assert np.array_equal(a[k], b[k]), k
+    tickets = [srv.submit(**q) for q in qs]
+    with pytest.raises(ara.AraError) as ei:          # requests queued: refused
+        srv.set_adjoint_index(False)
+    assert ei.value.status == ara.ARA_EBUSY
+    for t in tickets:
+        srv.wait(t)
+    srv.close()
