@@ -119,7 +119,6 @@ extern "C" ara_status ara_yet_index_create(ara_portfolio* pf_, int64_t n_trials,
   yx->groups = G;
   uint32_t* d_cnt = nullptr;
   uint32_t* d_err = nullptr;
-  ara_status st = ARA_OK;
   auto fail = [&](ara_status e) {
     if (d_cnt) cudaFreeAsync(d_cnt, s);
     if (d_err) cudaFreeAsync(d_err, s);
@@ -179,7 +178,7 @@ extern "C" ara_status ara_yet_index_create(ara_portfolio* pf_, int64_t n_trials,
   d_err = nullptr;
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(ARA_ECUDA);
   *out = yx;
-  return st;
+  return ARA_OK;
 }
 
 extern "C" void ara_yet_index_destroy(ara_yet_index* yx) {
