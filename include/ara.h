@@ -331,7 +331,7 @@ typedef struct ara_query {
  * next 31 queued requests that fits runs ahead of it (at most 4 times per blocked request).  A
  * request larger than the budget runs alone.  Into the admitted request the worker merges up to
  * three more queued requests (of the next 32) whose trial slices overlap the group's (by at
- * least 30 % of their union, see ara_server_set_merging), best overlap first, while their
+ * least 60 % of their union by default, see ara_server_set_merging), best overlap first, while their
  * memory fits: the group's layers run in one batched pass over the union of the slices, each
  * trial walking only the table entries of the requests that cover it, so the requests share the
  * reading of the YET (a group's table is kept near L2 size).  The workers' YET passes (batched
@@ -370,7 +370,7 @@ ARA_API ara_status ara_server_stats(ara_server* server, int32_t* queued_or_runni
 /* Merging of queued requests into one pass: at most max_requests_per_pass (1..4; 1 = every
  * request runs its own pass) requests per pass, a request joining a group when its slice
  * overlaps the group's by at least min_overlap (0 < min_overlap <= 1) of their union.  Applies
- * to groups formed after the call.  Default 4 and 0.3.  Errors: ARA_EINVAL. */
+ * to groups formed after the call.  Default 4 and 0.6.  Errors: ARA_EINVAL. */
 ARA_API ara_status ara_server_set_merging(ara_server* server, int32_t max_requests_per_pass,
                                           double min_overlap);
 /* Passes run so far (a pass serves one request or a merged group), requests that ran in a merged

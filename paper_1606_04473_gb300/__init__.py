@@ -510,7 +510,7 @@ class Server:
     (ara_server_*).  submit() queues a query and returns a ticket; wait() returns its results."""
 
     def __init__(self, pool: Portfolio, offsets, event_ids, max_concurrent: int = 4,
-                 memory_budget: int = 0, max_merge: int = 4, min_overlap: float = 0.3):
+                 memory_budget: int = 0, max_merge: int = 4, min_overlap: float = 0.6):
         import torch
         self._keep = (pool, offsets, event_ids)
         self.n_trials = offsets.numel() - 1
@@ -523,7 +523,7 @@ class Server:
         self._shapes = {}
         self.set_merging(max_merge, min_overlap)
 
-    def set_merging(self, max_merge: int, min_overlap: float = 0.3):
+    def set_merging(self, max_merge: int, min_overlap: float = 0.6):
         """Merge up to max_merge queued requests with overlapping slices into one pass
         (ara_server_set_merging; 1 = no merging)."""
         _check(lib().ara_server_set_merging(self._h, int(max_merge), float(min_overlap)),

@@ -61,7 +61,7 @@ struct ara_server {
   // merging: at most max_merge requests per pass; a queued request joins a group when its
   // slice's overlap with the group's slice is at least min_overlap of their union
   int32_t max_merge = 4;
-  double min_overlap = 0.3;
+  double min_overlap = 0.6;
   int32_t window = 32;        // queued requests examined for a group or to pass a blocked head
   int32_t max_passed = 4;     // a blocked head is passed at most this many times
   // A group's event-major table is kept near L2 size: merged passes whose table far exceeds it
