@@ -362,6 +362,13 @@ def test_indexed_adjoint_equals_trial_major(mid, case_name):
     assert torch.count_nonzero(a["loss"]).item() > 100
     if case_name == "tie":
         assert a["ties"].tolist() == [1, 1]
+    if case_name == "mid_all":                      # and directly against the FP64 chain rule
+        for obj, name in ((0, "mean"), (1, "tvar")):
+            ref = oracle.adjoint(pf, yet, name, LEVEL)
+            scale = max(1.0, float(np.abs(ref["loss"]).max()))
+            close(b["elt"][obj].cpu().numpy(), ref["elt"], 1.0)
+            close(b["layer"][obj].cpu().numpy(), ref["layer"], 1.0)
+            close(b["loss"][obj].cpu().numpy(), ref["loss"], scale)
     g.close()
 
 
