@@ -450,8 +450,8 @@ ARA_API ara_status ara_adjoint_accumulate(ara_portfolio* pf, int64_t n_trials,
                                           double* d_g_loss, void* stream);
 
 /*
- * Event-major index of a device YET, for adjoint passes over the same YET (Section IV-B's
- * trial-major table, transposed).  The adjoint's histograms count, per catalogue event and
+ * Event-major index of a device YET, for adjoint passes over the same YET (the trial-major
+ * table of Eq. 1, transposed).  The adjoint's histograms count, per catalogue event and
  * layer, the occurrences of the event in trials whose aggregate loss is interior for the layer.
  * Read trial by trial, every occurrence scatters into the histograms.  Read event by event, an
  * event's counts stay in one thread.  The index depends on the YET alone (not on the layers or
