@@ -201,25 +201,30 @@ struct BtStream {
   uint32_t* err;
 };
 
-__device__ __forceinline__ void smem_add_u128(unsigned long long* lo, unsigned long long* hi, uint64_t q) {
-  const unsigned long long old = atomicAdd(lo, (unsigned long long)q);
-  if (old + q < old) atomicAdd(hi, 1ull);
+// Non-returning 64-bit shared-memory add.  A segment of at most BT_SEG occurrences adds at most
+// one value below 2^55 per occurrence to a slot's word (a row holds each slot once), so the word
+// cannot wrap: BT_SEG * 2^55 <= 2^64.
+constexpr int BT_SEG = 512;
+__device__ __forceinline__ void smem_red_u64(unsigned long long* a, uint64_t q) {
+  asm volatile("red.shared.add.u64 [%0], %1;" :: "r"((uint32_t)__cvta_generic_to_shared(a)), "l"(q) : "memory");
 }
 
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_bt_stream(BtStream p) {
-  extern __shared__ __align__(16) unsigned long long bt_acc[];   // [WARPS][copies][2][n_sel]
+  // [WARPS][copies + 2][n_sel]: per copy the 64-bit sums of the current segment, then the
+  // trial's exact 128-bit totals (low and high words) of the finished segments
+  extern __shared__ __align__(16) unsigned long long bt_acc[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = p.n_sel;
   // Each group of 32 / copies lanes has its own copy of the warp's accumulators, so that lanes
   // of different groups never add to the same word; the copies are summed exactly at the end of
   // a trial.
   const int nc = p.copies;
-  unsigned long long* const acc0 = bt_acc + (int64_t)wid * 2 * nc * ns;
-  unsigned long long* const lo = acc0 + (int64_t)(lane / (32 / nc)) * 2 * ns;
-  unsigned long long* const hi = lo + ns;
-  for (int i = lane; i < 2 * nc * ns; i += 32) acc0[i] = 0ull;
+  unsigned long long* const acc0 = bt_acc + (int64_t)wid * (nc + 2) * ns;
+  unsigned long long* const lo = acc0 + (int64_t)(lane / (32 / nc)) * ns;
+  unsigned long long* const tot = acc0 + (int64_t)nc * ns;   // [2][n_sel]
+  for (int i = lane; i < (nc + 2) * ns; i += 32) acc0[i] = 0ull;
   __syncwarp();
   bool bad_id = false, bad_off = false;
   while (true) {
@@ -261,6 +266,21 @@ k_bt_stream(BtStream p) {
       };
       uint64_t ri_cur = load_row(load_id(beg + lane));
       int64_t e_nxt = load_id(beg + 32 + lane);
+      // Adds the segment sums of every copy into the trial's totals and clears them.
+      auto flush = [&]() {
+        __syncwarp();
+        for (int i = lane; i < ns; i += 32) {
+          U128 S{tot[i], tot[ns + i]};
+          for (int c = 0; c < nc; ++c) {
+            add_u64(S, acc0[(int64_t)c * ns + i]);
+            acc0[(int64_t)c * ns + i] = 0ull;
+          }
+          tot[i] = S.lo;
+          tot[ns + i] = S.hi;
+        }
+        __syncwarp();
+      };
+      int rounds = 0;
       for (int64_t i0 = beg; i0 < end; i0 += 32) {
         const uint64_t ri_nxt = load_row(e_nxt);
         e_nxt = load_id(i0 + 64 + lane);
@@ -290,20 +310,23 @@ k_bt_stream(BtStream p) {
           if (x < total) {
             const uint64_t v = __ldg(p.entries + (uint32_t)(b + x));
             const int s = (int)(v >> 56);
-            if ((uint32_t)s - skip_lo >= skip_n)
-              smem_add_u128(&lo[s], &hi[s], v & ((1ull << 56) - 1));
+            if ((uint32_t)s - skip_lo >= skip_n) smem_red_u64(&lo[s], v & ((1ull << 56) - 1));
           }
+        }
+        if (++rounds == BT_SEG / 32) {
+          flush();
+          rounds = 0;
         }
       }
       __syncwarp();
       // aggregate terms of every layer on the exact sums; reset the accumulators
       for (int i = lane; i < ns; i += 32) {
-        U128 S{0ull, 0ull};
+        U128 S{tot[i], tot[ns + i]};
+        tot[i] = 0ull;
+        tot[ns + i] = 0ull;
         for (int c = 0; c < nc; ++c) {
-          unsigned long long* const a = acc0 + (int64_t)c * 2 * ns;
-          add_u128(S, a[i], a[ns + i]);
-          a[i] = 0ull;
-          a[ns + i] = 0ull;
+          add_u64(S, acc0[(int64_t)c * ns + i]);
+          acc0[(int64_t)c * ns + i] = 0ull;
         }
         const uint32_t r = bt_req_of_slot(p.rs, i);
         if (!((amask >> r) & 1u)) continue;
@@ -397,7 +420,7 @@ ara_status bt_prep(ara_plan& P, cudaStream_t s, bool fill, int* n_kernels) {
 
 template <int W>
 ara_status bt_launch_w(ara_plan& P, const BtStream& bs, cudaStream_t s) {
-  const int smem = W * 2 * P.copies * (int)P.sel.size() * 8;
+  const int smem = W * (P.copies + 2) * (int)P.sel.size() * 8;
   const auto fn = k_bt_stream<W>;
   if (smem > 48 * 1024)
     ARA_TRY(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -626,7 +649,7 @@ ara_status ara_plan_batched(ara_portfolio* pf_, int64_t n_trials, const int64_t*
       for (int c : cand_c)
         for (int t : cand_t)
           for (int k : cand_k) {
-          const int64_t smem = (int64_t)w * 2 * k * (int64_t)P->sel.size() * 8;
+          const int64_t smem = (int64_t)w * (k + 2) * (int64_t)P->sel.size() * 8;
           if (smem * c > (int64_t)pf->max_smem_block || w * 32 * c > 2048) continue;
           P->warps = w;
           P->ctas_per_sm = c;
