@@ -17,7 +17,7 @@
 
 namespace ara {
 
-constexpr int FOLD_THREADS = 256;
+constexpr int FOLD_THREADS = 128;
 constexpr int YLT_THREADS = 1024;
 constexpr int MAX_SEL = 256;
 
@@ -47,10 +47,10 @@ struct FoldOut {
 };
 
 constexpr int FOLD_GROUP = 32;     // ELTs whose record ranges are searched together
-constexpr int FOLD_REC = 2048;     // records staged in shared memory per batch
+constexpr int FOLD_REC = 512;      // records staged in shared memory per window
 
 template <typename LossT>
-__global__ void __launch_bounds__(FOLD_THREADS)
+__global__ void __launch_bounds__(FOLD_THREADS, 7)
 k_fold(int64_t catalogue, const int64_t* __restrict__ tile_rec, int64_t n_tiles,
        const int32_t* __restrict__ rec_ids,
        const LossT* __restrict__ rec_loss, const double* __restrict__ elt_ret,
@@ -65,7 +65,6 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ tile_rec, int64_t n_tiles,
   __shared__ int64_t lo[FOLD_GROUP];
   __shared__ double eR[FOLD_GROUP], eL[FOLD_GROUP];
   __shared__ int32_t cnt_off[FOLD_GROUP + 1];
-  __shared__ int32_t n_batch;
   __shared__ int32_t n_list;
   const int layer = sel.idx[blockIdx.y];
   const int64_t slot = out.by_slot ? blockIdx.y : layer;
@@ -80,14 +79,14 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ tile_rec, int64_t n_tiles,
     for (int i = threadIdx.x; i < FOLD_TILE; i += FOLD_THREADS) reg[i] = 0;
   int n_touched = 0;   // kept by warp 0
   if (threadIdx.x == 0) n_list = 0;
-  // The layer's ELTs in order, in batches: warp 0 reads the record ranges of up to FOLD_GROUP
-  // ELTs within this tile from the portfolio's tile index, and the batch is the longest prefix
-  // of them whose records fit FOLD_REC.  All threads stage the batch's records with their ELT
-  // terms applied (one record per thread, so that the FP64 instructions run on full warps);
-  // then warp 0 adds them into the tile one ELT after the other, which keeps the FP64 sum in
-  // the layer's ELT order (IDs are unique within an ELT, so the lanes never collide within one
-  // ELT).
-  for (int k0 = lc.elt_begin; k0 < lc.elt_end;) {
+  // The layer's ELTs in order, in groups of up to FOLD_GROUP: warp 0 reads the group's record
+  // ranges within this tile from the portfolio's tile index.  The group's records, taken ELT
+  // after ELT, are then handled in windows of FOLD_REC (an ELT may straddle two windows): all
+  // threads stage a window's records with their ELT terms applied (one record per thread, so
+  // that the FP64 instructions run on full warps), then warp 0 adds them into the tile in that
+  // order, which keeps every event's FP64 sum in the layer's ELT order (IDs are unique within an
+  // ELT, so the lanes never collide within one ELT).
+  for (int k0 = lc.elt_begin; k0 < lc.elt_end; k0 += FOLD_GROUP) {
     const int G = min(FOLD_GROUP, lc.elt_end - k0);
     if (warp == 0) {
       int32_t c = 0;
@@ -108,48 +107,56 @@ k_fold(int64_t catalogue, const int64_t* __restrict__ tile_rec, int64_t n_tiles,
       }
       cnt_off[lane + 1] = incl;
       if (lane == 0) cnt_off[0] = 0;
-      const unsigned fit = __ballot_sync(FULL, lane < G && incl <= FOLD_REC);
-      if (lane == 0) n_batch = fit ? 32 - __clz((int)fit) : 1;  // one ELT always fits a tile
     }
     __syncthreads();
-    const int nb = n_batch;
-    const int32_t total = cnt_off[nb];
-    for (int i = threadIdx.x; i < total; i += FOLD_THREADS) {
-      int g = 0;   // the batch ELT of staged record i: the last g < nb with cnt_off[g] <= i
+    const int32_t total = cnt_off[G];
+    if (total == 0) {   // no window: every thread reads total before warp 0 rewrites the ranges
+      __syncthreads();
+      continue;
+    }
+    for (int32_t w0 = 0; w0 < total; w0 += FOLD_REC) {
+      // Between two windows of a group: warp 0 is done adding the previous window before it
+      // is restaged.  (Before a group's first window, the group's barrier above does this.)
+      if (w0 > 0) __syncthreads();
+      const int32_t wn = min(FOLD_REC, total - w0);
+      for (int i = threadIdx.x; i < wn; i += FOLD_THREADS) {
+        const int32_t x = w0 + i;
+        int g = 0;   // the group ELT of record x: the last g < G with cnt_off[g] <= x
 #pragma unroll
-      for (int step = FOLD_GROUP / 2; step > 0; step >>= 1)
-        if (g + step < nb && cnt_off[g + step] <= i) g += step;
-      const int64_t r = lo[g] + (i - cnt_off[g]);
-      rev[i] = (uint16_t)(rec_ids[r] - t0);
-      rx[i] = clamp_terms_bits(to_f64(rec_loss[r]), eR[g], eL[g]);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      for (int g = 0; g < nb; ++g) {
-        const int32_t b1 = cnt_off[g + 1];
-        for (int i = cnt_off[g] + lane; i - lane < b1; i += 32) {
-          bool first = false;
-          int e = 0;
-          if (i < b1) {
-            e = rev[i];
-            const double old = s[e], x = rx[i];
-            s[e] = __dadd_rn(old, x);
-            // Sums only grow (the ELT terms give x >= 0), so an event turns non-zero exactly
-            // once: when a zero sum meets a non-zero x (tested on the bits, off the add's path).
-            first = ((uint64_t)__double_as_longlong(old) << 1) == 0ull &&
-                    ((uint64_t)__double_as_longlong(x) << 1) != 0ull;
-          }
-          const unsigned m = __ballot_sync(FULL, first);
-          if (first) touched[n_touched + __popc(m & ((1u << lane) - 1u))] = (uint16_t)e;
-          n_touched += __popc(m);
-        }
-        __syncwarp();
+        for (int step = FOLD_GROUP / 2; step > 0; step >>= 1)
+          if (g + step < G && cnt_off[g + step] <= x) g += step;
+        const int64_t r = lo[g] + (x - cnt_off[g]);
+        rev[i] = (uint16_t)(rec_ids[r] - t0);
+        rx[i] = clamp_terms_bits(to_f64(rec_loss[r]), eR[g], eL[g]);
       }
-      if (lane == 0) n_list = n_touched;
+      __syncthreads();
+      if (warp == 0) {
+        const int32_t w1 = w0 + wn;
+        for (int g = 0; g < G; ++g) {
+          const int32_t a = max(cnt_off[g], w0) - w0, b1 = min(cnt_off[g + 1], w1) - w0;
+          for (int i = a + lane; i - lane < b1; i += 32) {
+            bool first = false;
+            int e = 0;
+            if (i < b1) {
+              e = rev[i];
+              const double old = s[e], x = rx[i];
+              s[e] = __dadd_rn(old, x);
+              // Sums only grow (the ELT terms give x >= 0), so an event turns non-zero exactly
+              // once: when a zero sum meets a non-zero x (tested on the bits, off the add's path).
+              first = ((uint64_t)__double_as_longlong(old) << 1) == 0ull &&
+                      ((uint64_t)__double_as_longlong(x) << 1) != 0ull;
+            }
+            const unsigned m = __ballot_sync(FULL, first);
+            if (first) touched[n_touched + __popc(m & ((1u << lane) - 1u))] = (uint16_t)e;
+            n_touched += __popc(m);
+          }
+          __syncwarp();
+        }
+        if (lane == 0) n_list = n_touched;
+      }
     }
-    // No barrier here: the next batch's first barrier keeps the other warps' staging away from
-    // the records warp 0 is still adding.
-    k0 += nb;
+    // No barrier here: the next group's barrier keeps the other warps' staging away from the
+    // records warp 0 is still adding, and warp 0 rewrites the ranges only after its adds.
   }
   __syncthreads();
   const int n_nz = n_list;
