@@ -258,10 +258,12 @@ ARA_API ara_status ara_plan_batched(ara_portfolio* pf, int64_t n_trials,
                                     int32_t flags, void* stream, ara_plan** out);
 /* Replay the plan's graph on `stream` (asynchronous; data errors via ara_check). */
 ARA_API ara_status ara_plan_launch(ara_plan* plan, void* stream);
-/* The schedule in use: warps per block, blocks per SM, trials per queue grab, and the tuned
- * time of one stream kernel in ms (0 without ARA_PLAN_AUTOTUNE). */
+/* The schedule in use: warps per block, blocks per SM, trials per queue grab, the tuned time
+ * of one stream kernel in ms (0 without ARA_PLAN_AUTOTUNE), and the copies of each warp's
+ * per-layer accumulators in shared memory (1, 2 or 4; a copy per group of 32 / copies lanes).
+ * Any output pointer may be NULL.  Errors: ARA_EINVAL (NULL plan). */
 ARA_API ara_status ara_plan_info(ara_plan* plan, int32_t* warps, int32_t* blocks_per_sm,
-                                 int32_t* trials_per_grab, double* tuned_ms);
+                                 int32_t* trials_per_grab, double* tuned_ms, int32_t* copies);
 /* The plan's event-major table, for measurement: d_rows receives its device array of row
  * descriptors [catalogue] (bits 0..31: the event's first table entry; byte 4: the number of its
  * entries, one per selected layer whose occurrence loss for the event is non-zero), valid until

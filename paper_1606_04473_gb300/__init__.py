@@ -89,7 +89,7 @@ def lib() -> ctypes.CDLL:
     L.ara_plan_launch.argtypes = [P, P]
     L.ara_plan_launch.restype = i32
     L.ara_plan_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
-                                ctypes.POINTER(d)]
+                                ctypes.POINTER(d), ctypes.POINTER(i32)]
     L.ara_plan_info.restype = i32
     L.ara_plan_table.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(i64)]
     L.ara_plan_table.restype = i32
@@ -472,10 +472,11 @@ class BatchedPlan:
 
     def info(self):
         w, c, t, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        k = ctypes.c_int32()
         _check(lib().ara_plan_info(self._h, ctypes.byref(w), ctypes.byref(c), ctypes.byref(t),
-                                   ctypes.byref(ms)), "ara_plan_info")
+                                   ctypes.byref(ms), ctypes.byref(k)), "ara_plan_info")
         return {"warps": w.value, "blocks_per_sm": c.value, "trials_per_grab": t.value,
-                "tuned_ms": ms.value}
+                "accumulator_copies": k.value, "tuned_ms": ms.value}
 
     def table(self):
         """(row descriptors, entries): the plan's event-major table for measurement

@@ -746,12 +746,14 @@ ara_status ara_plan_launch(ara_plan* P, void* stream) {
   return ARA_OK;
 }
 
-ara_status ara_plan_info(ara_plan* P, int32_t* warps, int32_t* bpsm, int32_t* tpg, double* ms) {
+ara_status ara_plan_info(ara_plan* P, int32_t* warps, int32_t* bpsm, int32_t* tpg, double* ms,
+                         int32_t* copies) {
   if (!P) return ARA_EINVAL;
   if (warps) *warps = P->warps;
   if (bpsm) *bpsm = P->ctas_per_sm;
   if (tpg) *tpg = P->tpg;
   if (ms) *ms = P->tuned_ms;
+  if (copies) *copies = P->copies;
   return ARA_OK;
 }
 

@@ -135,6 +135,7 @@ def test_new_entry_points_reject_null_handles_on_host(L):
                                  ctypes.byref(n)) == ara.ARA_EINVAL
     assert L.ara_server_set_adjoint_index(None, 1) == ara.ARA_EINVAL
     assert L.ara_plan_table(None, None, ctypes.byref(n)) == ara.ARA_EINVAL
+    assert L.ara_plan_info(None, None, None, None, None, None) == ara.ARA_EINVAL
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         assert L.ara_release_memory() == ara.ARA_OK

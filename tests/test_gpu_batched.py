@@ -66,6 +66,7 @@ def test_plan_equals_single_layer_path_and_oracle(case, autotune):
     assert np.all(err <= 1e-6 * np.abs(ref) + 1e-12 * np.abs(agg))
     info = plan.info()
     assert info["warps"] in (8, 16, 32) and info["blocks_per_sm"] in (1, 2, 4)
+    assert info["accumulator_copies"] in (1, 2, 4) and info["trials_per_grab"] in (1, 2, 4)
     if autotune:
         assert info["tuned_ms"] > 0
     plan.close()
