@@ -199,6 +199,39 @@ def test_per_elt_path_many_elts_and_fp64_losses():
     assert np.all(ref[2] == 0.0)
 
 
+def test_fold_windows_dense_elts_and_empty_groups():
+    """The fold stages a tile's records in windows of a few hundred: dense ELTs (70 % of a
+    6,000-event catalogue, about 1,400 records per ELT and tile) straddle several windows each,
+    and a second group of ELTs (a layer of 40 ELTs, searched 32 at a time) has records only in
+    the first tile, so the other tiles meet groups without records.  The folded YLT equals the
+    literal per-ELT path (Algorithm 3's lookups, the same ELT order) bit for bit, and the FP64
+    oracle within tolerance; per-ELT, occurrence and aggregate retentions all bind."""
+    catalogue = 6000
+    dense_ids, dense_losses = synth.make_elts(21, 32, 4200, catalogue, 11.0, 2.0, f32=True)
+    sparse_ids, sparse_losses = synth.make_elts(22, 8, 100, 500, 11.0, 2.0, f32=True)
+    ids, losses = dense_ids + sparse_ids, dense_losses + sparse_losses
+    r, l = synth.percentile_terms(losses)
+    layers = [list(range(40)), [5], [33, 0, 39, 12], list(range(32, 40))]
+    n = len(layers)
+    counts = synth.poisson_counts(23, 200.0, 600)
+    counts[:3] = [0, 1, 2]
+    yet = synth.make_yet(23, counts, catalogue, with_timestamps=False)
+    pf = synth.Portfolio(catalogue, ids, losses, r, l, layers, np.zeros(n), np.zeros(n),
+                         np.zeros(n), np.zeros(n), losses_f32=True)
+    from oracle.derive_terms import derive
+    pf = pf.with_terms(derive(pf, yet, 20.0, 70.0))
+    ref, agg = oracle.ylt(pf, yet, return_agg=True)
+    g = ara.Portfolio.from_tables(pf, dense_tables=True)
+    off, ev = dev(yet)
+    a = g.run_ylt(off, ev, flags=ara.ARA_RUN_PER_ELT)
+    b = g.run_ylt(off, ev)
+    g.check()
+    assert torch.equal(a, b)
+    assert_ylt_close(b.cpu().numpy(), ref, agg)
+    for k in range(n):   # the aggregate clamp is exercised in every layer
+        assert np.any(ref[k] == 0.0) and np.any(ref[k] > 0.0)
+
+
 def test_identity_terms_give_raw_loss_sums():
     pf, yet = mid_case(4, n_layers=2, n_trials=900)
     pf = pf.with_terms({**pf.terms_dict(), "elt_ret": [0.0] * pf.n_elts, "elt_lim": [INF] * pf.n_elts,
