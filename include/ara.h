@@ -533,6 +533,12 @@ ARA_API ara_status ara_risk_metrics(const double* d_ylt, int64_t n_trials, int32
  *                in when a device-side wait runs out (the other outputs are then undefined)
  * Scratch comes from the library's memory pool in stream order and is released in stream order.  Argument
  * errors are returned at once (ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA) and nothing is queued.
+ * Scheduling: the selection's blocks, like those of the default stream kernel, each fill an SM's
+ * registers, and the selection starts only once every SM is free.  When it runs on another
+ * stream than the next ara_run_ylt, order it before that run's stream kernel, e.g.
+ * ara_prepare_ylt on the run's stream, a wait on an event recorded after this call, then
+ * ara_run_ylt with ARA_RUN_PREPARED: otherwise the next stream kernel may take every SM first and
+ * hold the selection back for a whole run.
  */
 #define ARA_DEVICE_TIMEOUT 4u
 ARA_API ara_status ara_risk_metrics_async(const double* d_ylt, int64_t n_trials, int32_t n_layers,
