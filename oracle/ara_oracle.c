@@ -38,7 +38,7 @@ static double clamp_terms(double x, double R, double Lim) {
     return excess;
 }
 
-/* Regime of the clamp at x, judged on the same excess x - R as clamp_terms:
+/* Regime of the clamp at x, decided on the same excess x - R as clamp_terms:
  * 1 when 0 < x - R < Lim (slope 1 in x, -1 in R), 2 when x - R > Lim (slope 1 in Lim), else 0. */
 static int clamp_regime(double x, double R, double Lim) {
     double excess = x - R;
