@@ -328,11 +328,11 @@ def run_ours(args, rank, ws, local):
     # results and device status are copied to pinned host slots without a host wait, so the
     # host queues step k+1 while step k runs (one synchronisation at the end).  The selection
     # runs on a second stream behind an event.  Its blocks, like the stream kernel's, fill an SM's
-    # registers and it is cooperative, so it starts once every SM is free; the next step's fold
-    # (the first thing its ara_run_ylt queues) starts on each SM as the stream kernel's block
-    # there exits, and the selection then runs before that step's stream kernel.  The YLT is
-    # double-buffered so that the next step's stream kernel does not overwrite the row the
-    # selection is reading.
+    # registers and it is cooperative, so it starts once every SM is free: the next step's fold
+    # (the first thing its ara_run_ylt queues, right behind the stream kernel) runs first and
+    # hides the event's latency, and the selection then runs before that step's stream kernel.
+    # The YLT is double-buffered so that the next step's stream kernel does not overwrite the
+    # row the selection is reading.
     n_slots = max(args.steps, args.warmup, 3)
     ylts = [ylt, torch.empty_like(ylt)]
     pml_d = [torch.empty((1, len(RPS)), dtype=torch.float64, device="cuda") for _ in range(2)]
@@ -521,9 +521,9 @@ def run_ours(args, rank, ws, local):
                            "parallelism": f"replicas x{ws}",
                            "step": "YLT + PML/TVaR queued stream-ordered (ara_run_ylt, then "
                                    "ara_risk_metrics_async on a second stream after an event, YLT "
-                                   "double-buffered; the next fold starts in the stream "
-                                   "kernel's tail, then the cooperative selection runs before the "
-                                   "next stream kernel), each step's results copied to pinned host memory; "
+                                   "double-buffered; the next fold runs right behind the stream "
+                                   "kernel, then the cooperative selection before the next stream "
+                                   "kernel), each step's results copied to pinned host memory; "
                                    "one host synchronisation after the last step"},
                 "lookups_per_step": lookups_per_step,
                 "kernel_ms": {"fold_and_coarsen_per_step": round(fold_ms / max(args.steps, 1), 4),
